@@ -1,0 +1,147 @@
+"""Python access to the CPU oracle (oracle.c): test infrastructure only.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module.  It shares nothing with the CUDA library
+and the CUDA library never calls it.  Every function here is IEEE double
+precision on the host.
+
+Citations are to the paper's sections and equations:
+  * ``op_periodic``  -- Eq. 2 on a periodic uniform line + linear interpolation
+    to the LES nodes (the discretization operator of Sec. 3);
+  * ``op_wall``      -- Eq. 2 on the wall-normal line extended by Eq. 7 (or
+    Eq. 9, or truncated at the walls) + linear interpolation;
+  * ``subfilter_stress`` -- the four steps of Sec. 2.1 / Eq. 6, separable
+    evaluation of the product kernel;
+  * ``direct3d_points`` -- the same quantities by direct three-dimensional
+    summation of Eq. 2 at selected LES points;
+  * ``mlp_*`` (oracle/mlp.py) -- the learned closure of Sec. 2.1 / Sec. 5.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+EXT_EVEN_ODD = 0   # Eq. 7
+EXT_ODD_EVEN = 1   # Eq. 9
+EXT_NONE = 2       # filter support cut at the walls
+
+PAIRS = ((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc into oracle/_build/liboracle.so."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-ffp-contract=off",
+                               "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            d, i, p = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+            lib.or_op_periodic.argtypes = [i, d, i, d, p]
+            lib.or_op_wall.argtypes = [i, p, i, p, d, i, i, p]
+            lib.or_apply_separable.argtypes = [i, i, i, i, i, i, p, p, p, p, p, i, i]
+            lib.or_subfilter_stress.argtypes = [i, i, i, d, d, p, i, i, i, p, d, i, p, p, p, i, i]
+            lib.or_direct3d_points.argtypes = [i, i, i, d, d, p, i, i, i, p, d, i, p, i, p, p, p]
+            lib.or_num_threads.restype = i
+            lib.or_set_threads.argtypes = [i]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return _load().or_num_threads()
+
+
+def set_threads(n: int) -> None:
+    _load().or_set_threads(int(n))
+
+
+def op_periodic(n: int, L: float, nl: int, delta: float) -> np.ndarray:
+    A = np.zeros((nl, n))
+    rc = _load().or_op_periodic(n, float(L), nl, float(delta), _ptr(A))
+    if rc:
+        raise ValueError(f"or_op_periodic failed ({rc})")
+    return A
+
+
+def op_wall(y, Y, delta: float, parity: int, truncated: bool = False) -> np.ndarray:
+    y, Y = _f64(y), _f64(Y)
+    A = np.zeros((Y.size, y.size))
+    rc = _load().or_op_wall(y.size, _ptr(y), Y.size, _ptr(Y), float(delta),
+                            1 if truncated else 0, int(parity), _ptr(A))
+    if rc:
+        raise ValueError(f"or_op_wall failed ({rc})")
+    return A
+
+
+def apply_separable(f, Ax, Ay, Az, J0: int = 0, J1: int = 0) -> np.ndarray:
+    f = _f64(f)
+    ny, nz, nx = f.shape
+    Ax, Ay, Az = _f64(Ax), _f64(Ay), _f64(Az)
+    out = np.zeros((Ay.shape[0], Az.shape[0], Ax.shape[0]))
+    rc = _load().or_apply_separable(nx, ny, nz, Ax.shape[0], Ay.shape[0], Az.shape[0],
+                                    _ptr(Ax), _ptr(Ay), _ptr(Az), _ptr(f), _ptr(out), J0, J1)
+    if rc:
+        raise ValueError(f"or_apply_separable failed ({rc})")
+    return out
+
+
+def subfilter_stress(dns, les, delta: float, u, ext: int = EXT_EVEN_ODD,
+                     J0: int = 0, J1: int = 0):
+    """(ubar[3][nly][nlz][nlx], tau[6][nly][nlz][nlx]) for the whole snapshot
+    (or LES rows J0 <= J < J1; other rows are zero)."""
+    u = _f64(u)
+    assert u.shape == (3, dns.ny, dns.nz, dns.nx)
+    y, Y = _f64(dns.y), _f64(les.y)
+    ubar = np.zeros((3, les.ny, les.nz, les.nx))
+    tau = np.zeros((6, les.ny, les.nz, les.nx))
+    rc = _load().or_subfilter_stress(dns.nx, dns.ny, dns.nz, dns.Lx, dns.Lz, _ptr(y),
+                                     les.nx, les.ny, les.nz, _ptr(Y), float(delta), int(ext),
+                                     _ptr(u), _ptr(ubar), _ptr(tau), J0, J1)
+    if rc:
+        raise ValueError(f"or_subfilter_stress failed ({rc})")
+    return ubar, tau
+
+
+def direct3d_points(dns, les, delta: float, u, pts, ext: int = EXT_EVEN_ODD):
+    """(ubar[npts][3], tau[npts][6]) by direct 3-D summation at LES points
+    pts[npts][3] = (I, J, K)."""
+    u = _f64(u)
+    pts = np.ascontiguousarray(pts, dtype=np.int32)
+    n = pts.shape[0]
+    y, Y = _f64(dns.y), _f64(les.y)
+    ub = np.zeros((n, 3))
+    tau = np.zeros((n, 6))
+    rc = _load().or_direct3d_points(dns.nx, dns.ny, dns.nz, dns.Lx, dns.Lz, _ptr(y),
+                                    les.nx, les.ny, les.nz, _ptr(Y), float(delta), int(ext),
+                                    _ptr(u), n, _ptr(pts), _ptr(ub), _ptr(tau))
+    if rc:
+        raise ValueError(f"or_direct3d_points failed ({rc})")
+    return ub, tau
