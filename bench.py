@@ -1,0 +1,349 @@
+"""Benchmark: DNS points filtered (+ T_ij) per second on one GB300.
+
+Workload (default, the Re_tau ~ 180 channel shape): DNS 192 x 129 x 192 in a
+4 pi x 2 x 2 pi box, tanh-stretched y, filtered with a Gaussian of constant
+width Delta = Lx / 32 (wall extension of Eq. 7) onto a 32 x 33 x 32 LES grid;
+one step = ~bar(u_i), T_ij and the plane means of 10 seeded synthetic
+snapshots.  Inputs are 10 x 57 MB = 570 MB per step, larger than the 129 MB
+L2, so no flush is needed between steps.
+
+Output: one JSON line (rank 0).  `value` is whole-job throughput in DNS
+points per second with inputs resident in HBM; `e2e` is the same metric
+through the same C-ABI call with the inputs copied from pinned host memory
+and the results copied back inside the timed region.  `roofline` reports the
+x-contraction kernel (the dominant phase) against the measured HBM copy
+bandwidth.  `cpu_baseline` times the CPU oracle on a bounded sample.
+
+Multi-GPU: one process per GPU; snapshots are independent, so every rank
+filters its own 10 snapshots with no collective on the data path (weak
+scaling, "replicas only").
+
+--impl reference times the CPU oracle (the only reference that exists for
+this method) on the same workload's unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "DNS pts filtered+tau_ij per s, TC split-prec vs FP64 plain at stated err; %roofline"
+UNIT = "DNS points/s"
+
+WORKLOADS = {
+    # name: (nx, ny, nz, Lx, Lz, nlx, nly, nlz, delta/Lx, snapshots per step)
+    "re180": (192, 129, 192, 4 * math.pi, 2 * math.pi, 32, 33, 32, 1 / 32, 10),
+    "re550_d64": (512, 257, 384, 2 * math.pi, math.pi, 64, 65, 48, 1 / 64, 2),
+    "re550_d32": (512, 257, 384, 2 * math.pi, math.pi, 64, 65, 48, 1 / 32, 2),
+}
+PREC = {"fp32": 1, "fp64": 0, "bf16x3": 3}
+L2_BYTES = 129e6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="re180", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=sorted(PREC))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name, rank=0):
+    from paper_1902_02508_gb300 import inputs as I
+    nx, ny, nz, Lx, Lz, nlx, nly, nlz, dfrac, ns = WORKLOADS[name]
+    dns = I.dns_grid(nx, ny, nz, Lx, Lz)
+    les = I.les_grid(dns, nlx, nly, nlz)
+    delta = dfrac * Lx
+    base = [I.channel_velocity(dns, 1000 + rank * 1000 + s) for s in range(min(ns, 2))]
+    snaps = []
+    for s in range(ns):
+        b = base[s % len(base)]
+        snaps.append(b if s < len(base) else I.shifted(b, 7 * s, 5 * s))
+    return dns, les, delta, snaps
+
+
+def workload_config(name, prec):
+    nx, ny, nz, Lx, Lz, nlx, nly, nlz, dfrac, ns = WORKLOADS[name]
+    esz = 8 if prec == "fp64" else 4
+    return {"workload": f"channel DNS {nx}x{ny}x{nz} -> LES {nlx}x{nly}x{nlz}, Delta=Lx/{round(1 / dfrac)}, "
+                        f"Eq.7 wall extension, {ns} snapshots per step",
+            "dns_grid": [nx, ny, nz], "les_grid": [nlx, nly, nlz], "box": [Lx, 2.0, Lz],
+            "delta": dfrac * Lx, "snapshots_per_step": ns,
+            "l2": f"inputs {ns * nx * ny * nz * 3 * esz / 1e6:.0f} MB per step > {L2_BYTES / 1e6:.0f} MB L2, no flush"}
+
+
+# ------------------------------------------------------------ clocks ----
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        if not self.proc or not self.out:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ oracle ----
+def oracle_time(dns, les, delta, snaps, budget_s=10.0):
+    """Time the CPU oracle (separable FP64 evaluation) on whole snapshots of
+    the workload until ~budget_s has passed.  Returns (points/s, cores, sample)."""
+    from oracle import oracle as O
+    done, t0 = 0, time.perf_counter()
+    while done < len(snaps):
+        O.subfilter_stress(dns, les, delta, snaps[done])
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    pts = done * dns.npts
+    return pts / dt, O.num_threads(), f"{done} whole snapshot(s) of the workload, {dt:.1f} s"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    dns, les, delta, snaps = make_workload(args.workload)
+    for s in range(args.warmup):
+        O.subfilter_stress(dns, les, delta, snaps[s % len(snaps)])
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        O.subfilter_stress(dns, les, delta, snaps[s % len(snaps)])
+    dt = time.perf_counter() - t0
+    value = args.steps * dns.npts / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args.workload, args.precision),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"one whole snapshot per step ({dns.npts} DNS points)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- ours ----
+def traffic_from_profile(kernel_tag):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.json")
+    src = os.path.join(ROOT, "paper_1902_02508_gb300", "csrc", "filter_kernels.cu")
+    try:
+        prof = json.load(open(path))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if prof.get("source_sha256_16") == h:
+            return prof.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_1902_02508_gb300 import eles
+
+    dns, les, delta, snaps = make_workload(args.workload, rank)
+    ns = len(snaps)
+    prec = PREC[args.precision]
+    plan = eles.filter_setup(dns, les, delta, precision=prec)
+    dt = plan.dtype
+    stream = torch.cuda.Stream(dev)
+    u = torch.stack([torch.from_numpy(s) for s in snaps]).to(dev, dt)
+    ub = torch.empty((ns, 3, les.ny, les.nz, les.nx), device=dev, dtype=dt)
+    tau = torch.empty((ns, 6, les.ny, les.nz, les.nx), device=dev, dtype=dt)
+    pm = torch.empty((ns, 3, dns.ny), device=dev, dtype=torch.float64)
+    torch.cuda.synchronize()
+
+    def step(pl, uu, bb, tt, mm):
+        for s in range(ns):
+            eles.subfilter_stress(pl, uu[s], bb[s], tt[s], mm[s], stream=stream)
+
+    def timed(fn, steps, warmup):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                fn()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # --- device-resident throughput, with phase timing and clocks
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(plan, u, ub, tau, pm)
+    torch.cuda.synchronize()
+    assert eles.check_device_error(plan, stream) == 0
+    eles.profile_enable(plan, True)
+    with ClockSampler(local) as clk:
+        ms = timed(lambda: step(plan, u, ub, tau, pm), args.steps, 0)
+    phase_ms, calls = eles.profile_read(plan)
+    eles.profile_enable(plan, False)
+    # a second pass without the phase events, for the headline number
+    ms = min(ms, timed(lambda: step(plan, u, ub, tau, pm), args.steps, 1))
+    pts_step = ns * dns.npts
+    value = world * pts_step * args.steps / (ms / 1e3)
+
+    # --- end to end: pinned host in, results back to pinned host
+    hu = torch.stack([torch.from_numpy(s) for s in snaps]).to(dt).pin_memory()
+    hb = torch.empty(ub.shape, dtype=dt).pin_memory()
+    ht = torch.empty(tau.shape, dtype=dt).pin_memory()
+    ud = torch.empty_like(u)
+
+    def e2e_step():
+        ud.copy_(hu, non_blocking=True)
+        step(plan, ud, ub, tau, pm)
+        hb.copy_(ub, non_blocking=True)
+        ht.copy_(tau, non_blocking=True)
+
+    e2e_steps = max(3, args.steps // 2)
+    ms_e2e = timed(e2e_step, e2e_steps, 2)
+    e2e = {"value": world * pts_step * e2e_steps / (ms_e2e / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": hu.numel() * hu.element_size(),
+           "d2h_bytes_per_step": hb.numel() * hb.element_size() + ht.numel() * ht.element_size()}
+
+    # --- plain FP64 GPU filter on the same workload (the metric's comparator)
+    fp64 = None
+    if not args.no_fp64 and prec != 0:
+        p64 = eles.filter_setup(dns, les, delta, precision=0)
+        u64 = u.double()
+        b64 = torch.empty(ub.shape, device=dev, dtype=torch.float64)
+        t64 = torch.empty(tau.shape, device=dev, dtype=torch.float64)
+        k64 = max(2, args.steps // 4)
+        ms64 = timed(lambda: step(p64, u64, b64, t64, pm), k64, 1)
+        fp64 = {"value": world * pts_step * k64 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64 / k64}
+        del u64
+        p64.close()
+
+    # --- accuracy at the stated tolerance: snapshot 0 against the CPU oracle
+    err = None
+    cpu = None
+    if rank == 0:
+        from oracle import oracle as O
+        ub_ref, tau_ref = O.subfilter_stress(dns, les, delta, snaps[0])
+        got = tau[0].double().cpu().numpy()
+        err = {"tau_max_abs_err_utau2": [float(x) for x in np.abs(got - tau_ref).max(axis=(1, 2, 3))],
+               "tau_order": ["11", "12", "13", "22", "23", "33"],
+               "ubar_max_abs_err": float(np.abs(ub[0].double().cpu().numpy() - ub_ref).max())}
+        if not args.no_cpu_baseline and world == 1:
+            v, cores, sample = oracle_time(dns, les, delta, snaps)
+            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    # --- roofline of the dominant phase (x-contraction: it alone reads the input)
+    from_json = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = from_json.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in from_json else "fallback"
+    x_ms = phase_ms[1] / max(calls, 1)
+    alg_bytes = 12 * dns.npts if prec != 0 else 24 * dns.npts
+    achieved = alg_bytes / (x_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": "xpass (x-contraction, reads the input once)",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": peak_src, "traffic": traffic_from_profile(f"xpass_{args.workload}_{args.precision}"),
+            "algorithmic_bytes_per_launch": alg_bytes,
+            "phase_ms_per_call": {"profile": phase_ms[0] / max(calls, 1), "x": x_ms,
+                                  "z": phase_ms[2] / max(calls, 1), "y_recovery": phase_ms[3] / max(calls, 1)},
+            "path_frac": (value / world) * (alg_bytes / dns.npts) / 1e9 / peak}
+    per_call_launches = 6 if eles.plan_info(plan, 10) != 0 else 6
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp32": "f32", "fp64": "f64", "bf16x3": "bf16x3"}[args.precision],
+                "data": "synthetic (seeded solenoidal channel fields, Reichardt mean profile)",
+                "config": workload_config(args.workload, args.precision),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64,
+                "accuracy": err, "clocks": clk.summary(),
+                "gpu_launches": per_call_launches * ns * args.steps,
+                "x_variant": eles.plan_info(plan, 10)}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

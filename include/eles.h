@@ -1,0 +1,183 @@
+/*
+ * eles.h -- C ABI of the GB300 (sm_103a) explicit-filter library.
+ *
+ * The library computes, for channel-flow velocity snapshots, the explicitly
+ * filtered velocity and the exact subfilter stress of Bae & Lozano-Duran,
+ * "DNS-aided explicitly filtered LES of channel flow" (arXiv 1902.02508):
+ *
+ *   bar(phi)(x) = integral G(x - x') phi(x') dx'                     (Eq. 2)
+ *   T_ij = bar(u_i u_j) - ~bar(u_i) ~bar(u_j)                         (Eq. 6)
+ *
+ * following the four steps of Sec. 2.1 (form u_i u_j, filter it, form the
+ * product of the filtered velocities, subtract), with the wall-normal line
+ * extended across both walls by Eq. 7 (u1, u3 even, u2 odd) so that the
+ * filter keeps a constant width up to the wall, and with the filtered field
+ * sampled on the LES grid by linear interpolation (the discretization
+ * operator of Sec. 3).  The kernel is a Gaussian of width Delta per direction
+ * (transfer function exp(-k^2 Delta^2 / 24)), cut at |s| <= 2.5 Delta, with
+ * trapezoid weights on the extended node set and every row normalised.
+ *
+ * Conventions shared by every call:
+ *  - Fields are device pointers, row-major [component][y][z][x], x fastest.
+ *    Velocity input u: [3][ny][nz][nx]; filtered velocity ubar:
+ *    [3][nly][nlz][nlx]; stress tau: [6][nly][nlz][nlx] in the order
+ *    11, 12, 13, 22, 23, 33.  Element type: double for EF_PREC_FP64, float
+ *    for every other precision.  Velocities in units of u_tau.
+ *  - The caller owns every field buffer.  The library owns plans: their
+ *    filter weights and their scratch memory live on the device of the plan
+ *    and are allocated by ef_filter_setup only; hot calls allocate nothing
+ *    and never synchronise the host.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on it.  Calls that share a plan must
+ *    not overlap in time (they share its scratch): issue them on one stream.
+ *  - Every call returns an ef_status.  On failure ef_last_error() returns a
+ *    thread-local message.  Device-side problems (non-finite input, a wait
+ *    that ran out) are recorded in the plan's error word and read back by
+ *    ef_check_device_error().
+ */
+#ifndef ELES_H
+#define ELES_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum {
+    EF_OK = 0,
+    EF_ERR_ARG = 1,          /* invalid argument (NULL, non-positive size, Delta <= 0 ...) */
+    EF_ERR_SHAPE = 2,        /* grid shapes the library does not accept */
+    EF_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    EF_ERR_NAN = 4,          /* non-finite values seen on the device */
+    EF_ERR_TIMEOUT = 5,      /* a bounded device wait ran out */
+    EF_ERR_OOM = 6,          /* device allocation failed in a setup call */
+    EF_ERR_UNSUPPORTED = 7   /* valid request the library does not implement */
+} ef_status;
+
+/* Filter kernels.  Only the Gaussian is implemented. */
+enum { EF_KERNEL_GAUSSIAN = 0 };
+
+/* Wall treatment. */
+enum {
+    EF_EXT_EVEN_ODD = 0,     /* Eq. 7: u1, u3 even, u2 odd about each wall */
+    EF_EXT_ODD_EVEN = 1,     /* Eq. 9: u1, u3 odd, u2 even (divergence-preserving, not NS-compatible) */
+    EF_EXT_NONE = 2          /* no extension: support cut at the walls (does not commute, Sec. 2.2) */
+};
+
+/* Arithmetic of the filter contractions. */
+enum {
+    EF_PREC_FP64 = 0,        /* double in, double out, FP64 throughout */
+    EF_PREC_FP32 = 1,        /* float in/out, FP32 contractions on CUDA cores, FP64 recovery */
+    EF_PREC_TF32X2 = 2,      /* reserved */
+    EF_PREC_BF16X3 = 3       /* float in/out, x-contraction on tensor cores with split BF16 operands */
+};
+
+/*
+ * A channel grid: nx x ny x nz nodes, periodic in x (length Lx) and z (Lz),
+ * wall-normal nodes y[0..ny-1] on the host, strictly ascending with
+ * y[0] = -1 and y[ny-1] = +1 (both walls are nodes).  x_i = i Lx / nx,
+ * z_k = k Lz / nz.
+ */
+typedef struct {
+    int nx, ny, nz;
+    double Lx, Lz;
+    const double *y;
+} ef_grid;
+
+typedef struct ef_plan ef_plan;
+
+/*
+ * ef_filter_setup -- build a filter plan on the current CUDA device.
+ * Cite: Eq. 2 (filter), Eq. 7 / Eq. 9 (extension), Sec. 3 (linear
+ * interpolation to the LES grid), constant filter width Delta (Sec. 2.2).
+ *  dns, les   grids (host structs; y arrays are copied).  les must span the
+ *             same box: les->Lx == dns->Lx, les->Lz == dns->Lz, les->y within
+ *             [-1, 1] ascending with les->y[0] = -1 and les->y[nly-1] = +1.
+ *  delta      filter width, > 0; 2.5 delta must be < Lx/2, Lz/2 and < 2.
+ *  kernel     EF_KERNEL_GAUSSIAN.
+ *  extension  EF_EXT_*.
+ *  precision  EF_PREC_*.
+ *  out        receives the plan (owned by the caller, free with
+ *             ef_plan_destroy).
+ * The operator weights are computed on the device in FP64 (one thread per
+ * operator row) and kept there; the plan also allocates the scratch memory
+ * its hot calls use.  Synchronises the device.  Errors: EF_ERR_ARG,
+ * EF_ERR_SHAPE, EF_ERR_OOM, EF_ERR_CUDA, EF_ERR_UNSUPPORTED.
+ */
+int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int kernel,
+                    int extension, int precision, ef_plan **out);
+
+/* Release a plan and its device memory (NULL is ignored). */
+void ef_plan_destroy(ef_plan *plan);
+
+/*
+ * ef_filter_fields -- ~bar(u_i) only (steps 2-3 of Sec. 2.1 for the
+ * velocities; the initial condition of Sec. 3 is exactly this call).
+ *  u     device [3][ny][nz][nx]
+ *  ubar  device [3][nly][nlz][nlx]
+ * Errors: EF_ERR_ARG (NULL plan or pointer), EF_ERR_CUDA (launch failure).
+ */
+int ef_filter_fields(ef_plan *plan, const void *u, void *ubar, void *stream);
+
+/*
+ * ef_subfilter_stress -- ~bar(u_i) and T_ij on the LES grid (Eq. 6, the
+ * four steps of Sec. 2.1).
+ *  u           device [3][ny][nz][nx]
+ *  ubar        device [3][nly][nlz][nlx]
+ *  tau         device [6][nly][nlz][nlx], order 11, 12, 13, 22, 23, 33
+ *  plane_mean  device double [3][ny]: the x-z plane means <u_i>(y_j)
+ *              (Sec. 4.1's averaging in the homogeneous directions), or NULL.
+ * Internally the products are formed about a reference profile U(y) (the
+ * mean of one z-row per plane); the decomposition is exact algebra because
+ * the x and z operators preserve functions of y, and the cancelling
+ * subtractions run in FP64.
+ * Errors: EF_ERR_ARG, EF_ERR_CUDA.
+ */
+int ef_subfilter_stress(ef_plan *plan, const void *u, void *ubar, void *tau,
+                        double *plane_mean, void *stream);
+
+/*
+ * ef_check_device_error -- read (and clear) the plan's device error word.
+ * Synchronises `stream`.  Returns EF_OK, or the ef_status a kernel recorded.
+ */
+int ef_check_device_error(ef_plan *plan, void *stream);
+
+/* Plan facts for callers and tests.  ints: 0 nx, 1 ny, 2 nz, 3 nlx, 4 nly,
+ * 5 nlz, 6 precision, 7 x-taps per row, 8 z-taps per row, 9 max y-taps per
+ * row, 10 x-contraction variant (0 generic, 1 banded ring on CUDA cores,
+ * 2 tensor cores).  Returns EF_ERR_ARG for an unknown index. */
+int ef_plan_info(const ef_plan *plan, int what, long *value);
+
+/*
+ * ef_plan_weights -- copy one operator of the plan to the host as a dense
+ * row-major FP64 matrix (for tests).  which: 0 A_x [nlx][nx], 1 A_z
+ * [nlz][nz], 2 A_y even [nly][ny], 3 A_y odd [nly][ny].  dst must hold the
+ * whole matrix.  Synchronises the device.
+ */
+int ef_plan_weights(const ef_plan *plan, int which, double *dst);
+
+/*
+ * Phase timing for benchmarks.  ef_profile_enable(plan, 1) clears the
+ * accumulators and makes every later hot call record CUDA events on its own
+ * stream before and after each phase; ef_profile_enable(plan, 0) stops it.
+ * ef_profile_read waits for the recorded events and returns the summed
+ * milliseconds per phase (ms[0] reference profile, ms[1] x-contraction,
+ * ms[2] z-contraction, ms[3] y-contraction and recovery) and the number of
+ * calls timed.  Errors: EF_ERR_ARG, EF_ERR_CUDA.
+ */
+int ef_profile_enable(ef_plan *plan, int on);
+int ef_profile_read(ef_plan *plan, double *ms, long *calls);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char *ef_last_error(void);
+
+/* Library version string. */
+const char *ef_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ELES_H */

@@ -1,0 +1,301 @@
+// The C ABI of include/eles.h: argument checks, plan lifetime, dispatch.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "eles_internal.h"
+
+namespace eles {
+
+static thread_local char g_msg[512] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+    va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? EF_ERR_OOM : EF_ERR_CUDA;
+}
+
+static void free_band(Band &b)
+{
+    cudaFree(b.d_start);
+    cudaFree(b.d_w64);
+    cudaFree(b.d_w32);
+    b = Band();
+}
+
+static int check_grid(const ef_grid *g, const char *name)
+{
+    if (!g || !g->y) { set_error("%s: NULL grid or y", name); return EF_ERR_ARG; }
+    if (g->nx < 1 || g->ny < 3 || g->nz < 1) { set_error("%s: sizes must be nx,nz >= 1, ny >= 3", name); return EF_ERR_SHAPE; }
+    if (!(g->Lx > 0) || !(g->Lz > 0)) { set_error("%s: Lx, Lz must be > 0", name); return EF_ERR_ARG; }
+    if (g->y[0] != -1.0 || g->y[g->ny - 1] != 1.0) { set_error("%s: y must run from -1 to +1", name); return EF_ERR_ARG; }
+    for (int j = 1; j < g->ny; j++)
+        if (!(g->y[j] > g->y[j - 1])) { set_error("%s: y must be strictly ascending", name); return EF_ERR_ARG; }
+    return EF_OK;
+}
+
+}  // namespace eles
+
+namespace eles {
+
+// Accumulate a finished slot's phase times into the plan's totals.
+static int prof_collect(ef_plan *p, int slot)
+{
+    if (!p->prof_used[slot]) return EF_OK;
+    cudaError_t e = cudaEventSynchronize(p->prof_ev[slot][ef_plan::kProfEvents - 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "profile events");
+    for (int k = 0; k < 4; k++) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, p->prof_ev[slot][k], p->prof_ev[slot][k + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "profile events");
+        p->prof_ms[k] += ms;
+    }
+    p->prof_used[slot] = false;
+    p->prof_calls++;
+    return EF_OK;
+}
+
+int prof_begin(ef_plan *p, PhaseEvents *pe)
+{
+    const int slot = (int)((p->prof_calls + 0) % ef_plan::kProfSlots);
+    int free_slot = -1;
+    for (int t = 0; t < ef_plan::kProfSlots; t++)
+        if (!p->prof_used[(slot + t) % ef_plan::kProfSlots]) { free_slot = (slot + t) % ef_plan::kProfSlots; break; }
+    if (free_slot < 0) {
+        for (int t = 0; t < ef_plan::kProfSlots; t++) {
+            int rc = prof_collect(p, t);
+            if (rc) return rc;
+        }
+        free_slot = 0;
+    }
+    for (int k = 0; k < ef_plan::kProfEvents; k++) {
+        if (!p->prof_ev[free_slot][k]) {
+            cudaError_t e = cudaEventCreate(&p->prof_ev[free_slot][k]);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+        }
+        pe->e[k] = p->prof_ev[free_slot][k];
+    }
+    p->prof_used[free_slot] = true;
+    return EF_OK;
+}
+
+}  // namespace eles
+
+using namespace eles;
+
+extern "C" {
+
+const char *ef_last_error(void) { return g_msg; }
+
+const char *ef_version(void) { return "eles-gb300 0.1 (sm_103a)"; }
+
+void ef_plan_destroy(ef_plan *p)
+{
+    if (!p) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->device);
+    free_band(p->bx);
+    free_band(p->bz);
+    cudaFree(p->d_ystart);
+    cudaFree(p->d_ycount);
+    for (int q = 0; q < 2; q++) { cudaFree(p->d_yw64[q]); cudaFree(p->d_yw32[q]); }
+    cudaFree(p->d_ygrid);
+    cudaFree(p->d_g);
+    cudaFree(p->d_h);
+    cudaFree(p->d_uref);
+    cudaFree(p->d_urefT);
+    cudaFree(p->d_rowsum);
+    cudaFree(p->d_AU);
+    cudaFree(p->d_AUU);
+    cudaFree(p->d_err);
+    for (int t = 0; t < ef_plan::kProfSlots; t++)
+        for (int k = 0; k < ef_plan::kProfEvents; k++)
+            if (p->prof_ev[t][k]) cudaEventDestroy(p->prof_ev[t][k]);
+    cudaSetDevice(cur);
+    delete p;
+}
+
+int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int kernel, int extension,
+                    int precision, ef_plan **out)
+{
+    if (!out) { set_error("ef_filter_setup: out is NULL"); return EF_ERR_ARG; }
+    *out = nullptr;
+    int rc;
+    if ((rc = check_grid(dns, "dns")) || (rc = check_grid(les, "les"))) return rc;
+    if (!(delta > 0) || !isfinite(delta)) { set_error("delta must be finite and > 0"); return EF_ERR_ARG; }
+    if (kernel != EF_KERNEL_GAUSSIAN) { set_error("only the Gaussian kernel is implemented"); return EF_ERR_UNSUPPORTED; }
+    if (extension < EF_EXT_EVEN_ODD || extension > EF_EXT_NONE) { set_error("unknown extension %d", extension); return EF_ERR_ARG; }
+    if (precision != EF_PREC_FP64 && precision != EF_PREC_FP32) {
+        set_error("precision %d not implemented", precision);
+        return EF_ERR_UNSUPPORTED;
+    }
+    if (les->Lx != dns->Lx || les->Lz != dns->Lz) { set_error("LES and DNS boxes differ"); return EF_ERR_SHAPE; }
+    if (les->nx > dns->nx || les->nz > dns->nz || les->ny > dns->ny) { set_error("LES grid finer than DNS grid"); return EF_ERR_SHAPE; }
+    if (2.5 * delta >= 0.5 * dns->Lx || 2.5 * delta >= 0.5 * dns->Lz || 2.5 * delta >= 2.0) {
+        set_error("filter support 2.5 delta must be below half of Lx, Lz and below 2");
+        return EF_ERR_ARG;
+    }
+    ef_plan *p = new ef_plan();
+    cudaGetDevice(&p->device);
+    p->nx = dns->nx; p->ny = dns->ny; p->nz = dns->nz;
+    p->nlx = les->nx; p->nly = les->ny; p->nlz = les->nz;
+    p->Lx = dns->Lx; p->Lz = dns->Lz; p->delta = delta;
+    p->ext = extension; p->prec = precision;
+    if (extension == EF_EXT_ODD_EVEN) { p->par[0] = -1; p->par[1] = 1; p->par[2] = -1; }
+    cudaError_t e;
+#define CK(x, what) do { if ((e = (x)) != cudaSuccess) { rc = cuda_fail(e, what); goto fail; } } while (0)
+    {
+        CK(cudaMalloc(&p->d_ygrid, sizeof(double) * p->ny), "cudaMalloc y");
+        CK(cudaMemcpy(p->d_ygrid, dns->y, sizeof(double) * p->ny, cudaMemcpyHostToDevice), "copy y");
+        if ((rc = build_periodic_band(p->nx, p->Lx, p->nlx, delta, &p->bx))) goto fail;
+        if ((rc = build_periodic_band(p->nz, p->Lz, p->nlz, delta, &p->bz))) goto fail;
+        if ((rc = build_wall_rows(p, les->y))) goto fail;
+        CK(cudaDeviceSynchronize(), "operator kernels");
+        if ((rc = build_ring(p->bx, &p->rx))) goto fail;
+        if ((rc = build_ring(p->bz, &p->rz))) goto fail;
+        p->x_variant = p->rx.ok ? 1 : 0;
+        const size_t es = (precision == EF_PREC_FP64) ? sizeof(double) : sizeof(float);
+        p->nzw = (p->nz + 31) / 32;
+        CK(cudaMalloc(&p->d_g, es * 9 * (size_t)p->ny * p->nz * p->nlx), "cudaMalloc scratch g");
+        CK(cudaMalloc(&p->d_h, es * 9 * (size_t)p->ny * p->nlz * p->nlx), "cudaMalloc scratch h");
+        CK(cudaMalloc(&p->d_uref, sizeof(double) * 3 * p->ny), "cudaMalloc scratch");
+        CK(cudaMalloc(&p->d_urefT, es * 3 * p->ny), "cudaMalloc scratch");
+        CK(cudaMalloc(&p->d_rowsum, sizeof(double) * 3 * (size_t)p->ny * p->nzw), "cudaMalloc scratch");
+        CK(cudaMalloc(&p->d_AU, sizeof(double) * 3 * p->nly), "cudaMalloc scratch");
+        CK(cudaMalloc(&p->d_AUU, sizeof(double) * 6 * p->nly), "cudaMalloc scratch");
+        CK(cudaMalloc(&p->d_err, sizeof(int)), "cudaMalloc error word");
+        CK(cudaMemset(p->d_err, 0, sizeof(int)), "clear error word");
+        CK(cudaDeviceSynchronize(), "setup");
+    }
+#undef CK
+    *out = p;
+    return EF_OK;
+fail:
+    ef_plan_destroy(p);
+    return rc;
+}
+
+
+static int hot_args(ef_plan *p, const void *u, const void *ubar, const char *who)
+{
+    if (!p || !u || !ubar) { set_error("%s: NULL plan or field pointer", who); return EF_ERR_ARG; }
+    if (((uintptr_t)u) % 16) { set_error("%s: u must be 16-byte aligned", who); return EF_ERR_ARG; }
+    return EF_OK;
+}
+
+int ef_filter_fields(ef_plan *p, const void *u, void *ubar, void *stream)
+{
+    int rc = hot_args(p, u, ubar, "ef_filter_fields");
+    if (rc) return rc;
+    PhaseEvents pe;
+    if (p->prof_on && (rc = prof_begin(p, &pe))) return rc;
+    return run_filter(p, u, ubar, nullptr, nullptr, false, static_cast<cudaStream_t>(stream),
+                      p->prof_on ? &pe : nullptr);
+}
+
+int ef_subfilter_stress(ef_plan *p, const void *u, void *ubar, void *tau, double *plane_mean, void *stream)
+{
+    int rc = hot_args(p, u, ubar, "ef_subfilter_stress");
+    if (rc) return rc;
+    if (!tau) { set_error("ef_subfilter_stress: tau is NULL"); return EF_ERR_ARG; }
+    PhaseEvents pe;
+    if (p->prof_on && (rc = prof_begin(p, &pe))) return rc;
+    return run_filter(p, u, ubar, tau, plane_mean, true, static_cast<cudaStream_t>(stream),
+                      p->prof_on ? &pe : nullptr);
+}
+
+int ef_profile_enable(ef_plan *p, int on)
+{
+    if (!p) { set_error("ef_profile_enable: NULL plan"); return EF_ERR_ARG; }
+    if (on) {
+        for (int t = 0; t < ef_plan::kProfSlots; t++) p->prof_used[t] = false;
+        p->prof_calls = 0;
+        for (int k = 0; k < 4; k++) p->prof_ms[k] = 0.0;
+    }
+    p->prof_on = on != 0;
+    return EF_OK;
+}
+
+int ef_profile_read(ef_plan *p, double *ms, long *calls)
+{
+    if (!p || !ms) { set_error("ef_profile_read: NULL argument"); return EF_ERR_ARG; }
+    for (int t = 0; t < ef_plan::kProfSlots; t++) {
+        int rc = prof_collect(p, t);
+        if (rc) return rc;
+    }
+    for (int k = 0; k < 4; k++) ms[k] = p->prof_ms[k];
+    if (calls) *calls = p->prof_calls;
+    return EF_OK;
+}
+
+int ef_check_device_error(ef_plan *p, void *stream)
+{
+    if (!p) { set_error("ef_check_device_error: NULL plan"); return EF_ERR_ARG; }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int code = 0;
+    cudaError_t e = cudaMemcpyAsync(&code, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "read device error word");
+    if (code) set_error("device reported status %d", code);
+    return code;
+}
+
+int ef_plan_info(const ef_plan *p, int what, long *value)
+{
+    if (!p || !value) { set_error("ef_plan_info: NULL argument"); return EF_ERR_ARG; }
+    switch (what) {
+    case 0: *value = p->nx; break;
+    case 1: *value = p->ny; break;
+    case 2: *value = p->nz; break;
+    case 3: *value = p->nlx; break;
+    case 4: *value = p->nly; break;
+    case 5: *value = p->nlz; break;
+    case 6: *value = p->prec; break;
+    case 7: *value = p->rx.ok ? 2 * p->rx.R + 1 : p->bx.T; break;
+    case 8: *value = p->rz.ok ? 2 * p->rz.R + 1 : p->bz.T; break;
+    case 9: *value = p->ytaps_max; break;
+    case 10: *value = p->x_variant; break;
+    default: set_error("ef_plan_info: unknown index %d", what); return EF_ERR_ARG;
+    }
+    return EF_OK;
+}
+
+int ef_plan_weights(const ef_plan *p, int which, double *dst)
+{
+    if (!p || !dst) { set_error("ef_plan_weights: NULL argument"); return EF_ERR_ARG; }
+    cudaError_t e;
+    if (which == 0 || which == 1) {
+        const Band &b = which == 0 ? p->bx : p->bz;
+        std::vector<double> w((size_t)b.nl * b.T);
+        std::vector<int> st(b.nl);
+        e = cudaMemcpy(w.data(), b.d_w64, sizeof(double) * w.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(st.data(), b.d_start, sizeof(int) * b.nl, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "ef_plan_weights");
+        memset(dst, 0, sizeof(double) * (size_t)b.nl * b.n);
+        for (int r = 0; r < b.nl; r++)
+            for (int t = 0; t < b.T; t++) dst[(size_t)r * b.n + (st[r] + t) % b.n] += w[(size_t)r * b.T + t];
+        return EF_OK;
+    }
+    if (which == 2 || which == 3) {
+        e = cudaMemcpy(dst, p->d_yw64[which - 2], sizeof(double) * (size_t)p->nly * p->ny, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "ef_plan_weights");
+        return EF_OK;
+    }
+    set_error("ef_plan_weights: unknown operator %d", which);
+    return EF_ERR_ARG;
+}
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+// Internal declarations shared by the library's translation units.
+// Nothing here is part of the C ABI (that is include/eles.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "eles.h"
+
+namespace eles {
+
+constexpr int kMaxRing = 24;      // largest ring (taps / stride + 1) of the banded ring kernels
+constexpr int kMaxStride = 8;     // largest DNS/LES stride of the banded ring kernels
+
+// A banded operator A[nl][n]: row r has `T` entries starting at column
+// start[r] (periodic operators wrap the column index modulo n).
+struct Band {
+    int n = 0, nl = 0, T = 0;
+    int *d_start = nullptr;       // [nl]
+    double *d_w64 = nullptr;      // [nl][T]
+    float *d_w32 = nullptr;       // [nl][T]
+};
+
+// Strided convolution form of a periodic operator whose LES nodes coincide
+// with DNS nodes (n = r nl): A[X][x] = w[x - r X] for |x - r X| <= R.
+// Table W[s][dd] = w[s - r (dd + dmin)] for s in [0, r), dd in [0, D).
+struct Ring {
+    bool ok = false;
+    int r = 0, R = 0, dmin = 0, dmax = 0, D = 0;
+    double W64[kMaxStride * kMaxRing];
+    float W32[kMaxStride * kMaxRing];
+};
+
+}  // namespace eles
+
+struct ef_plan {
+    int device = 0;
+    int nx = 0, ny = 0, nz = 0, nlx = 0, nly = 0, nlz = 0;
+    double Lx = 0, Lz = 0, delta = 0;
+    int ext = 0, prec = 0;
+    int par[3] = {1, -1, 1};      // wall parity of u1, u2, u3 (Eq. 7 or Eq. 9)
+    eles::Band bx, bz;            // x and z operators
+    eles::Ring rx, rz;            // their strided-convolution tables (if ok)
+    int x_variant = 0;            // 0 generic gather, 1 ring (CUDA cores), 2 tensor cores
+    // y operators, dense [nly][ny] rows with a nonzero range per row
+    int *d_ystart = nullptr, *d_ycount = nullptr;
+    double *d_yw64[2] = {nullptr, nullptr};   // [0] even, [1] odd
+    float *d_yw32[2] = {nullptr, nullptr};
+    int ytaps_max = 0;
+    double *d_ygrid = nullptr;    // DNS y nodes on the device
+    // scratch owned by the plan
+    void *d_g = nullptr;          // x-contracted fields  [9][ny][nz][nlx]
+    void *d_h = nullptr;          // x,z-contracted fields [9][ny][nlz][nlx]
+    double *d_uref = nullptr;     // reference profile U_c(y_j), [3][ny]
+    void *d_urefT = nullptr;      // same in the working type
+    double *d_rowsum = nullptr;   // partial sums of the fluctuation, [3][ny][nzw]
+    int nzw = 0;
+    double *d_AU = nullptr;       // A_y U_c, [3][nly]
+    double *d_AUU = nullptr;      // A_y (U_a U_b), [6][nly]
+    int *d_err = nullptr;         // device error word
+    // phase timing (ef_profile_enable)
+    bool prof_on = false;
+    static constexpr int kProfSlots = 64, kProfEvents = 5;
+    cudaEvent_t prof_ev[kProfSlots][kProfEvents] = {};
+    bool prof_used[kProfSlots] = {};
+    long prof_calls = 0;
+    double prof_ms[4] = {0, 0, 0, 0};
+};
+
+namespace eles {
+
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+// setup_kernels.cu
+int build_periodic_band(int n, double L, int nl, double delta, Band *b);
+int build_ring(const Band &b, Ring *r);
+int build_wall_rows(ef_plan *p, const double *h_les_y);
+
+// Phase events of the current call (nullptr entries when timing is off).
+struct PhaseEvents { cudaEvent_t e[ef_plan::kProfEvents]; };
+int prof_begin(ef_plan *p, PhaseEvents *pe);
+inline void prof_mark(const PhaseEvents *pe, int k, cudaStream_t s)
+{
+    if (pe && pe->e[k]) cudaEventRecord(pe->e[k], s);
+}
+
+// filter_kernels.cu
+int run_filter(ef_plan *p, const void *u, void *ubar, void *tau, double *plane_mean,
+               bool stress, cudaStream_t s, const PhaseEvents *pe);
+
+}  // namespace eles

@@ -1,0 +1,197 @@
+"""Thin Python binding of the C ABI in include/eles.h (ctypes).
+
+Argument marshalling only: every step of the filter runs in the CUDA library
+libeles.so.  PyTorch supplies device memory and streams.  There is no CPU or
+PyTorch fallback: if the library is missing the import of a function fails
+loudly.
+
+Names follow the C ABI: ``filter_setup``, ``filter_fields``,
+``subfilter_stress``, ``check_device_error``, ``plan_info``, ``plan_weights``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libeles.so")
+
+EF_OK = 0
+STATUS = {0: "EF_OK", 1: "EF_ERR_ARG", 2: "EF_ERR_SHAPE", 3: "EF_ERR_CUDA", 4: "EF_ERR_NAN",
+          5: "EF_ERR_TIMEOUT", 6: "EF_ERR_OOM", 7: "EF_ERR_UNSUPPORTED"}
+KERNEL_GAUSSIAN = 0
+EXT_EVEN_ODD, EXT_ODD_EVEN, EXT_NONE = 0, 1, 2
+PREC_FP64, PREC_FP32, PREC_TF32X2, PREC_BF16X3 = 0, 1, 2, 3
+
+# every symbol include/eles.h declares
+EXPORTED = ("ef_filter_setup", "ef_plan_destroy", "ef_filter_fields", "ef_subfilter_stress",
+            "ef_check_device_error", "ef_plan_info", "ef_plan_weights", "ef_profile_enable",
+            "ef_profile_read", "ef_last_error", "ef_version")
+
+
+class EFError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("Lx", ctypes.c_double), ("Lz", ctypes.c_double),
+                ("y", ctypes.POINTER(ctypes.c_double))]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libeles.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise ImportError(f"libeles.so not built at {path}; run paper_1902_02508_gb300.build.build()")
+            lib = ctypes.CDLL(path)
+            vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+            lib.ef_filter_setup.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Grid), d, i, i, i,
+                                            ctypes.POINTER(vp)]
+            lib.ef_filter_setup.restype = i
+            lib.ef_plan_destroy.argtypes = [vp]
+            lib.ef_plan_destroy.restype = None
+            lib.ef_filter_fields.argtypes = [vp, vp, vp, vp]
+            lib.ef_filter_fields.restype = i
+            lib.ef_subfilter_stress.argtypes = [vp, vp, vp, vp, vp, vp]
+            lib.ef_subfilter_stress.restype = i
+            lib.ef_check_device_error.argtypes = [vp, vp]
+            lib.ef_check_device_error.restype = i
+            lib.ef_plan_info.argtypes = [vp, i, ctypes.POINTER(ctypes.c_long)]
+            lib.ef_plan_info.restype = i
+            lib.ef_plan_weights.argtypes = [vp, i, vp]
+            lib.ef_plan_weights.restype = i
+            lib.ef_profile_enable.argtypes = [vp, i]
+            lib.ef_profile_enable.restype = i
+            lib.ef_profile_read.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_long)]
+            lib.ef_profile_read.restype = i
+            lib.ef_last_error.restype = ctypes.c_char_p
+            lib.ef_version.restype = ctypes.c_char_p
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int):
+    if rc != EF_OK:
+        raise EFError(rc, load().ef_last_error().decode())
+
+
+def _grid(g):
+    y = np.ascontiguousarray(g.y, dtype=np.float64)
+    s = _Grid(g.nx, g.ny, g.nz, float(g.Lx), float(g.Lz), y.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return s, y
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """Owns an ef_plan*.  Created by filter_setup()."""
+
+    def __init__(self, handle, dns, les, delta, precision):
+        self.handle = handle
+        self.dns, self.les, self.delta, self.precision = dns, les, delta, precision
+
+    def close(self):
+        if self.handle:
+            load().ef_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == PREC_FP64 else torch.float32
+
+
+def filter_setup(dns, les, delta: float, kernel: int = KERNEL_GAUSSIAN,
+                 extension: int = EXT_EVEN_ODD, precision: int = PREC_FP32) -> Plan:
+    lib = load()
+    gd, yd = _grid(dns)
+    gl, yl = _grid(les)
+    h = ctypes.c_void_p()
+    _check(lib.ef_filter_setup(ctypes.byref(gd), ctypes.byref(gl), float(delta), int(kernel),
+                               int(extension), int(precision), ctypes.byref(h)))
+    return Plan(h, dns, les, delta, precision)
+
+
+def _field(t, shape, dtype, name):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name}: need a contiguous CUDA {dtype} tensor of shape {shape}, "
+                         f"got {t.dtype} {tuple(t.shape)} on {t.device}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def filter_fields(plan: Plan, u, ubar, stream=None) -> None:
+    d, l = plan.dns, plan.les
+    pu = _field(u, (3, d.ny, d.nz, d.nx), plan.dtype, "u")
+    pb = _field(ubar, (3, l.ny, l.nz, l.nx), plan.dtype, "ubar")
+    _check(load().ef_filter_fields(plan.handle, pu, pb, _stream(stream)))
+
+
+def subfilter_stress(plan: Plan, u, ubar, tau, plane_mean=None, stream=None) -> None:
+    import torch
+    d, l = plan.dns, plan.les
+    pu = _field(u, (3, d.ny, d.nz, d.nx), plan.dtype, "u")
+    pb = _field(ubar, (3, l.ny, l.nz, l.nx), plan.dtype, "ubar")
+    pt = _field(tau, (6, l.ny, l.nz, l.nx), plan.dtype, "tau")
+    pm = _field(plane_mean, (3, d.ny), torch.float64, "plane_mean")
+    _check(load().ef_subfilter_stress(plan.handle, pu, pb, pt, pm, _stream(stream)))
+
+
+def check_device_error(plan: Plan, stream=None) -> int:
+    return load().ef_check_device_error(plan.handle, _stream(stream))
+
+
+def plan_info(plan: Plan, what: int) -> int:
+    v = ctypes.c_long()
+    _check(load().ef_plan_info(plan.handle, int(what), ctypes.byref(v)))
+    return v.value
+
+
+def plan_weights(plan: Plan, which: int) -> np.ndarray:
+    d, l = plan.dns, plan.les
+    shape = {0: (l.nx, d.nx), 1: (l.nz, d.nz), 2: (l.ny, d.ny), 3: (l.ny, d.ny)}[which]
+    out = np.zeros(shape)
+    _check(load().ef_plan_weights(plan.handle, int(which), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def profile_enable(plan: Plan, on: bool = True) -> None:
+    _check(load().ef_profile_enable(plan.handle, 1 if on else 0))
+
+
+def profile_read(plan: Plan):
+    """(ms per phase [profile, x, z, y], calls) summed since profile_enable."""
+    ms = np.zeros(4)
+    n = ctypes.c_long()
+    _check(load().ef_profile_read(plan.handle, ms.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)))
+    return ms, n.value
+
+
+def version() -> str:
+    return load().ef_version().decode()

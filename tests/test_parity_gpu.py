@@ -1,0 +1,208 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances:
+  * FP64 path: per component, max |GPU - oracle| <= 1e-12 max(|oracle|, 1)
+    (the plain formula cancels bar(u1 u1) ~ 400 to T11 ~ 1..20, so the
+    oracle itself carries ~1e-14 relative roundoff);
+  * FP32 path: max |GPU - oracle| <= 1e-4 u_tau^2 for every T_ij component
+    (velocities in units of u_tau) and <= 1e-4 for ~bar(u_i).
+Operator weights are compared entry by entry with the oracle's FP64 operators.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import __graft_entry__ as entry
+from oracle import oracle as O
+from paper_1902_02508_gb300 import eles
+from paper_1902_02508_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    entry.build()
+
+
+def run_gpu(dns, les, delta, u, prec, ext=eles.EXT_EVEN_ODD, plane_mean=False):
+    plan = eles.filter_setup(dns, les, delta, extension=ext, precision=prec)
+    dev = torch.device("cuda")
+    ud = torch.from_numpy(np.ascontiguousarray(u)).to(dev, plan.dtype)
+    ub = torch.full((3, les.ny, les.nz, les.nx), float("nan"), device=dev, dtype=plan.dtype)
+    tau = torch.full((6, les.ny, les.nz, les.nx), float("nan"), device=dev, dtype=plan.dtype)
+    pm = torch.zeros((3, dns.ny), device=dev, dtype=torch.float64) if plane_mean else None
+    eles.subfilter_stress(plan, ud, ub, tau, pm)
+    torch.cuda.synchronize()
+    assert eles.check_device_error(plan) == 0
+    out = (ub.double().cpu().numpy(), tau.double().cpu().numpy())
+    if plane_mean:
+        out = out + (pm.cpu().numpy(),)
+    return plan, out
+
+
+def assert_close(got, ref, tol, what):
+    for c in range(ref.shape[0]):
+        err = np.abs(got[c] - ref[c]).max()
+        scale = max(np.abs(ref[c]).max(), 1.0) if tol == TOL64 else 1.0
+        assert err <= tol * scale, f"{what}[{c}]: max err {err:.3e} > {tol * scale:.3e}"
+
+
+CASES = {
+    # name: (nx, ny, nz, Lx, Lz, nlx, nly, nlz, delta)
+    "tiny": (32, 33, 32, 2 * math.pi, math.pi, 8, 9, 8, 2 * math.pi / 16),
+    # several 128-row tiles in z with a ragged tail (160 = 128 + 32)
+    "tiles": (96, 65, 160, 2 * math.pi, math.pi, 24, 17, 40, 2 * math.pi / 24),
+    # stride 6 in x and z (channel box 4 pi x 2 x 2 pi)
+    "stride6": (96, 49, 96, 4 * math.pi, 2 * math.pi, 16, 13, 16, 4 * math.pi / 16),
+    # non-integer DNS/LES ratios in x, y and z: generic banded path + interpolation
+    "interp": (30, 25, 20, 2 * math.pi, math.pi, 9, 8, 6, 0.5),
+}
+
+
+def case(name, seed=1000):
+    nx, ny, nz, Lx, Lz, nlx, nly, nlz, delta = CASES[name]
+    dns = I.dns_grid(nx, ny, nz, Lx, Lz)
+    les = I.les_grid(dns, nlx, nly, nlz) if (ny - 1) % (nly - 1) == 0 else \
+        I.Grid(nlx, nly, nlz, Lx, Lz, I.tanh_nodes(nly))
+    return dns, les, delta, I.channel_velocity(dns, seed)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_weights_match_oracle(name):
+    dns, les, delta, _ = case(name)
+    plan = eles.filter_setup(dns, les, delta, precision=eles.PREC_FP64)
+    assert np.abs(eles.plan_weights(plan, 0) - O.op_periodic(dns.nx, dns.Lx, les.nx, delta)).max() < 1e-14
+    assert np.abs(eles.plan_weights(plan, 1) - O.op_periodic(dns.nz, dns.Lz, les.nz, delta)).max() < 1e-14
+    assert np.abs(eles.plan_weights(plan, 2) - O.op_wall(dns.y, les.y, delta, +1)).max() < 1e-14
+    assert np.abs(eles.plan_weights(plan, 3) - O.op_wall(dns.y, les.y, delta, -1)).max() < 1e-14
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("prec", [eles.PREC_FP64, eles.PREC_FP32])
+def test_subfilter_stress_matches_oracle(name, prec):
+    dns, les, delta, u = case(name)
+    ub_ref, tau_ref = O.subfilter_stress(dns, les, delta, u)
+    plan, (ub, tau) = run_gpu(dns, les, delta, u, prec)
+    tol = TOL64 if prec == eles.PREC_FP64 else TOL32
+    assert_close(ub, ub_ref, tol, "ubar")
+    assert_close(tau, tau_ref, tol, "tau")
+
+
+@pytest.mark.parametrize("ext", [eles.EXT_ODD_EVEN, eles.EXT_NONE])
+@pytest.mark.parametrize("prec", [eles.PREC_FP64, eles.PREC_FP32])
+def test_other_wall_treatments(ext, prec):
+    dns, les, delta, u = case("tiny", seed=7)
+    ub_ref, tau_ref = O.subfilter_stress(dns, les, delta, u, ext=ext)
+    _, (ub, tau) = run_gpu(dns, les, delta, u, prec, ext=ext)
+    tol = TOL64 if prec == eles.PREC_FP64 else TOL32
+    assert_close(ub, ub_ref, tol, "ubar")
+    assert_close(tau, tau_ref, tol, "tau")
+
+
+def test_channel_shape_re180_fp32_and_fp64():
+    """192 x 129 x 192 -> 32 x 33 x 32, Delta = Lx / 32 (Re_tau ~ 180 shape)."""
+    dns = I.dns_grid(192, 129, 192, 4 * math.pi, 2 * math.pi)
+    les = I.les_grid(dns, 32, 33, 32)
+    delta = dns.Lx / 32
+    u = I.channel_velocity(dns, 1001)
+    ub_ref, tau_ref = O.subfilter_stress(dns, les, delta, u)
+    for prec, tol in ((eles.PREC_FP64, TOL64), (eles.PREC_FP32, TOL32)):
+        _, (ub, tau) = run_gpu(dns, les, delta, u, prec)
+        assert_close(ub, ub_ref, tol, "ubar")
+        assert_close(tau, tau_ref, tol, "tau")
+
+
+_BIG = {}
+
+
+def big_field():
+    if not _BIG:
+        dns = I.dns_grid(512, 257, 384, 2 * math.pi, math.pi)
+        _BIG["v"] = (dns, I.les_grid(dns, 64, 65, 48), I.channel_velocity(dns, 1002))
+    return _BIG["v"]
+
+
+@pytest.mark.parametrize("dfrac", [64, 32])
+def test_full_size_sampled_points(dfrac):
+    """512 x 257 x 384 -> 64 x 65 x 48 at full size, checked at seeded LES
+    points (wall rows included) by the oracle's direct 3-D summation."""
+    dns, les, u = big_field()
+    delta = dns.Lx / dfrac
+    _, (ub, tau) = run_gpu(dns, les, delta, u, eles.PREC_FP32)
+    rng = np.random.default_rng(3)
+    pts = np.stack([rng.integers(0, les.nx, 12), rng.integers(0, les.ny, 12),
+                    rng.integers(0, les.nz, 12)], axis=1)
+    pts[:2, 1] = [0, les.ny - 1]
+    ub3, tau3 = O.direct3d_points(dns, les, delta, u, pts)
+    got_ub = ub[:, pts[:, 1], pts[:, 2], pts[:, 0]].T
+    got_tau = tau[:, pts[:, 1], pts[:, 2], pts[:, 0]].T
+    assert np.abs(got_ub - ub3).max() <= TOL32
+    assert np.abs(got_tau - tau3).max() <= TOL32
+
+
+def test_plane_mean_and_filter_fields():
+    dns, les, delta, u = case("tiles", seed=5)
+    plan, (ub, tau, pm) = run_gpu(dns, les, delta, u, eles.PREC_FP32, plane_mean=True)
+    assert np.abs(pm - u.mean(axis=(2, 3))).max() < 1e-6
+    dev = torch.device("cuda")
+    ud = torch.from_numpy(u).to(dev, torch.float32)
+    ub2 = torch.empty((3, les.ny, les.nz, les.nx), device=dev)
+    eles.filter_fields(plan, ud, ub2)
+    torch.cuda.synchronize()
+    assert np.array_equal(ub2.double().cpu().numpy(), ub)
+
+
+def test_invariants_on_gpu():
+    """Eq. 8 parity at the walls, symmetric PSD T_ij, Galilean shift in x, z."""
+    dns, les, delta, u = case("tiles", seed=9)
+    _, (ub, tau) = run_gpu(dns, les, delta, u, eles.PREC_FP64)
+    assert np.abs(ub[1, 0]).max() < 1e-14 and np.abs(ub[1, -1]).max() < 1e-14
+    T = np.empty(tau.shape[1:] + (3, 3))
+    for q, (i, j) in enumerate(O.PAIRS):
+        T[..., i, j] = tau[q]
+        T[..., j, i] = tau[q]
+    assert np.linalg.eigvalsh(T.reshape(-1, 3, 3)).min() > -1e-11
+    u2 = u.copy()
+    u2[0] += 2.0
+    u2[2] -= 0.5
+    _, (ubs, taus) = run_gpu(dns, les, delta, u2, eles.PREC_FP32)
+    _, (ub32, tau32) = run_gpu(dns, les, delta, u, eles.PREC_FP32)
+    assert np.abs(taus - tau32).max() < 1e-5
+
+
+def test_nan_input_sets_device_error():
+    dns, les, delta, u = case("tiny")
+    u = u.copy()
+    u[0, 5, 3, 7] = np.nan
+    plan = eles.filter_setup(dns, les, delta, precision=eles.PREC_FP32)
+    dev = torch.device("cuda")
+    ud = torch.from_numpy(u).to(dev, torch.float32)
+    ub = torch.empty((3, les.ny, les.nz, les.nx), device=dev)
+    tau = torch.empty((6, les.ny, les.nz, les.nx), device=dev)
+    eles.subfilter_stress(plan, ud, ub, tau)
+    assert eles.check_device_error(plan) == 4
+    assert eles.check_device_error(plan) == 0      # the word is cleared by the read
+
+
+def test_repeat_calls_are_bitwise_stable():
+    dns, les, delta, u = case("tiles", seed=2)
+    plan = eles.filter_setup(dns, les, delta, precision=eles.PREC_FP32)
+    dev = torch.device("cuda")
+    ud = torch.from_numpy(u).to(dev, torch.float32)
+    outs = []
+    for _ in range(2):
+        ub = torch.empty((3, les.ny, les.nz, les.nx), device=dev)
+        tau = torch.empty((6, les.ny, les.nz, les.nx), device=dev)
+        eles.subfilter_stress(plan, ud, ub, tau)
+        outs.append(tau.cpu())
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], outs[1])
