@@ -139,6 +139,25 @@ int ef_subfilter_stress(ef_plan *plan, const void *u, void *ubar, void *tau,
                         double *plane_mean, void *stream);
 
 /*
+ * ef_subfilter_stress_batch -- the same for nsnap snapshots that share the
+ * plan's grids and filter, stored back to back: u [nsnap][3][ny][nz][nx],
+ * ubar [nsnap][3][..], tau [nsnap][6][..], plane_mean [nsnap][3][ny] or NULL.
+ * Snapshots are independent; up to the plan's reserved count (see
+ * ef_plan_reserve) run in one launch per phase, larger batches in groups.
+ * Errors: EF_ERR_ARG, EF_ERR_CUDA.
+ */
+int ef_subfilter_stress_batch(ef_plan *plan, int nsnap, const void *u, void *ubar, void *tau,
+                              double *plane_mean, void *stream);
+
+/*
+ * ef_plan_reserve -- size the plan's scratch for batches of up to
+ * max_snapshots snapshots per launch (setup-time call: it allocates, and
+ * synchronises the device; never call it while the plan is in use).  A new
+ * plan reserves 1.  Errors: EF_ERR_ARG, EF_ERR_OOM.
+ */
+int ef_plan_reserve(ef_plan *plan, int max_snapshots);
+
+/*
  * ef_check_device_error -- read (and clear) the plan's device error word.
  * Synchronises `stream`.  Returns EF_OK, or the ef_status a kernel recorded.
  */
@@ -147,7 +166,8 @@ int ef_check_device_error(ef_plan *plan, void *stream);
 /* Plan facts for callers and tests.  ints: 0 nx, 1 ny, 2 nz, 3 nlx, 4 nly,
  * 5 nlz, 6 precision, 7 x-taps per row, 8 z-taps per row, 9 max y-taps per
  * row, 10 x-contraction variant (0 generic, 1 banded ring on CUDA cores,
- * 2 tensor cores).  Returns EF_ERR_ARG for an unknown index. */
+ * 2 tensor cores), 11 x and z fused in one kernel (0/1), 12 reserved
+ * snapshots.  Returns EF_ERR_ARG for an unknown index. */
 int ef_plan_info(const ef_plan *plan, int what, long *value);
 
 /*
@@ -163,9 +183,11 @@ int ef_plan_weights(const ef_plan *plan, int which, double *dst);
  * accumulators and makes every later hot call record CUDA events on its own
  * stream before and after each phase; ef_profile_enable(plan, 0) stops it.
  * ef_profile_read waits for the recorded events and returns the summed
- * milliseconds per phase (ms[0] reference profile, ms[1] x-contraction,
- * ms[2] z-contraction, ms[3] y-contraction and recovery) and the number of
- * calls timed.  Errors: EF_ERR_ARG, EF_ERR_CUDA.
+ * milliseconds per phase (ms[0] reference profile with the x- and
+ * z-contractions, ms[1] reserved (0), ms[2] y-contraction and recovery,
+ * ms[3] reserved (0)) and the number of calls timed.  A batch larger than
+ * the reserved count is timed over its last group only.
+ * Errors: EF_ERR_ARG, EF_ERR_CUDA.
  */
 int ef_profile_enable(ef_plan *plan, int on);
 int ef_profile_read(ef_plan *plan, double *ms, long *calls);

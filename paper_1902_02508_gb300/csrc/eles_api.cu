@@ -90,6 +90,40 @@ int prof_begin(ef_plan *p, PhaseEvents *pe)
     return EF_OK;
 }
 
+// (Re)allocate the plan's scratch for batches of up to nsnap snapshots.
+int plan_reserve(ef_plan *p, int nsnap)
+{
+    if (nsnap < 1) { set_error("reserve: nsnap must be >= 1"); return EF_ERR_ARG; }
+    if (nsnap <= p->reserve) return EF_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "reserve");
+    cudaFree(p->d_g); cudaFree(p->d_h); cudaFree(p->d_uref); cudaFree(p->d_urefT); cudaFree(p->d_rowsum);
+    cudaFree(p->d_AU); cudaFree(p->d_AUU); cudaFree(p->d_wy); cudaFree(p->d_ytmp);
+    p->d_g = p->d_h = p->d_urefT = p->d_wy = p->d_ytmp = nullptr;
+    p->d_uref = p->d_rowsum = p->d_AU = p->d_AUU = nullptr;
+    p->reserve = 0;
+    const size_t es = (p->prec == EF_PREC_FP64) ? sizeof(double) : sizeof(float);
+    const size_t S = (size_t)nsnap;
+    struct { void **ptr; size_t bytes; } req[] = {
+        {&p->d_g, p->fused ? 0 : es * 9 * (size_t)p->ny * p->nz * p->nlx},
+        {&p->d_h, es * 9 * S * p->ny * p->nlz * p->nlx},
+        {(void **)&p->d_uref, sizeof(double) * 3 * S * p->ny},
+        {&p->d_urefT, es * 3 * (size_t)p->ny},
+        {(void **)&p->d_rowsum, sizeof(double) * 3 * (size_t)p->ny * p->nzw},
+        {(void **)&p->d_AU, sizeof(double) * 3 * S * p->nly},
+        {(void **)&p->d_AUU, sizeof(double) * 6 * S * p->nly},
+        {&p->d_wy, es * 8 * S * p->nly * p->ny},
+        {&p->d_ytmp, es * 12 * S * p->nly * p->nlz * p->nlx},
+    };
+    for (auto &r : req) {
+        if (!r.bytes) continue;
+        e = cudaMalloc(r.ptr, r.bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc scratch");
+    }
+    p->reserve = nsnap;
+    return EF_OK;
+}
+
 }  // namespace eles
 
 using namespace eles;
@@ -119,6 +153,8 @@ void ef_plan_destroy(ef_plan *p)
     cudaFree(p->d_rowsum);
     cudaFree(p->d_AU);
     cudaFree(p->d_AUU);
+    cudaFree(p->d_wy);
+    cudaFree(p->d_ytmp);
     cudaFree(p->d_err);
     for (int t = 0; t < ef_plan::kProfSlots; t++)
         for (int k = 0; k < ef_plan::kProfEvents; k++)
@@ -166,15 +202,27 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
         if ((rc = build_ring(p->bx, &p->rx))) goto fail;
         if ((rc = build_ring(p->bz, &p->rz))) goto fail;
         p->x_variant = p->rx.ok ? 1 : 0;
-        const size_t es = (precision == EF_PREC_FP64) ? sizeof(double) : sizeof(float);
+        // FP32 plans use the fused x-z kernel when its ring sizes are instantiated
+        if (precision == EF_PREC_FP32 && p->rx.ok && p->rz.ok && p->nz <= kFusedMaxRows && p->nz % 32 == 0 &&
+            fused_supported(p->rx.r, p->rx.D, p->rz.r, p->rz.D) && p->nlx % fused_stage_blocks(p->rx.r) == 0) {
+            const int SB = fused_stage_blocks(p->rx.r);
+            p->P = 8;
+            while (p->P > 1 && fused_smem_bytes(p->rx.r, p->P, p->nz) > 222 * 1024) p->P /= 2;
+            if (fused_smem_bytes(p->rx.r, p->P, p->nz) <= 222 * 1024) {
+                p->fused = true;
+                p->NQ = 1;
+                for (int q = p->nz / (9 * p->P); q > 1; q--)
+                    if (p->nlz % q == 0) { p->NQ = q; break; }
+                p->ZQs = p->nlz / p->NQ;
+                // stream start: dmax rounded up to whole stages, so no stage wraps and
+                // every stage starts on a 16-byte boundary
+                p->bshift = (p->rx.dmax + SB - 1) / SB * SB;
+                const int need = p->nlx - p->rx.dmin + p->bshift;
+                p->nblk_x = (need + SB - 1) / SB * SB;
+            }
+        }
         p->nzw = (p->nz + 31) / 32;
-        CK(cudaMalloc(&p->d_g, es * 9 * (size_t)p->ny * p->nz * p->nlx), "cudaMalloc scratch g");
-        CK(cudaMalloc(&p->d_h, es * 9 * (size_t)p->ny * p->nlz * p->nlx), "cudaMalloc scratch h");
-        CK(cudaMalloc(&p->d_uref, sizeof(double) * 3 * p->ny), "cudaMalloc scratch");
-        CK(cudaMalloc(&p->d_urefT, es * 3 * p->ny), "cudaMalloc scratch");
-        CK(cudaMalloc(&p->d_rowsum, sizeof(double) * 3 * (size_t)p->ny * p->nzw), "cudaMalloc scratch");
-        CK(cudaMalloc(&p->d_AU, sizeof(double) * 3 * p->nly), "cudaMalloc scratch");
-        CK(cudaMalloc(&p->d_AUU, sizeof(double) * 6 * p->nly), "cudaMalloc scratch");
+        if ((rc = plan_reserve(p, 1))) goto fail;
         CK(cudaMalloc(&p->d_err, sizeof(int)), "cudaMalloc error word");
         CK(cudaMemset(p->d_err, 0, sizeof(int)), "clear error word");
         CK(cudaDeviceSynchronize(), "setup");
@@ -195,25 +243,43 @@ static int hot_args(ef_plan *p, const void *u, const void *ubar, const char *who
     return EF_OK;
 }
 
+int ef_plan_reserve(ef_plan *p, int max_snapshots)
+{
+    if (!p) { set_error("ef_plan_reserve: NULL plan"); return EF_ERR_ARG; }
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->device);
+    int rc = plan_reserve(p, max_snapshots);
+    cudaSetDevice(cur);
+    return rc;
+}
+
 int ef_filter_fields(ef_plan *p, const void *u, void *ubar, void *stream)
 {
     int rc = hot_args(p, u, ubar, "ef_filter_fields");
     if (rc) return rc;
     PhaseEvents pe;
     if (p->prof_on && (rc = prof_begin(p, &pe))) return rc;
-    return run_filter(p, u, ubar, nullptr, nullptr, false, static_cast<cudaStream_t>(stream),
+    return run_filter(p, 1, u, ubar, nullptr, nullptr, false, static_cast<cudaStream_t>(stream),
+                      p->prof_on ? &pe : nullptr);
+}
+
+int ef_subfilter_stress_batch(ef_plan *p, int nsnap, const void *u, void *ubar, void *tau, double *plane_mean,
+                              void *stream)
+{
+    int rc = hot_args(p, u, ubar, "ef_subfilter_stress");
+    if (rc) return rc;
+    if (!tau) { set_error("ef_subfilter_stress: tau is NULL"); return EF_ERR_ARG; }
+    if (nsnap < 1) { set_error("ef_subfilter_stress_batch: nsnap must be >= 1"); return EF_ERR_ARG; }
+    PhaseEvents pe;
+    if (p->prof_on && (rc = prof_begin(p, &pe))) return rc;
+    return run_filter(p, nsnap, u, ubar, tau, plane_mean, true, static_cast<cudaStream_t>(stream),
                       p->prof_on ? &pe : nullptr);
 }
 
 int ef_subfilter_stress(ef_plan *p, const void *u, void *ubar, void *tau, double *plane_mean, void *stream)
 {
-    int rc = hot_args(p, u, ubar, "ef_subfilter_stress");
-    if (rc) return rc;
-    if (!tau) { set_error("ef_subfilter_stress: tau is NULL"); return EF_ERR_ARG; }
-    PhaseEvents pe;
-    if (p->prof_on && (rc = prof_begin(p, &pe))) return rc;
-    return run_filter(p, u, ubar, tau, plane_mean, true, static_cast<cudaStream_t>(stream),
-                      p->prof_on ? &pe : nullptr);
+    return ef_subfilter_stress_batch(p, 1, u, ubar, tau, plane_mean, stream);
 }
 
 int ef_profile_enable(ef_plan *p, int on)
@@ -268,6 +334,8 @@ int ef_plan_info(const ef_plan *p, int what, long *value)
     case 8: *value = p->rz.ok ? 2 * p->rz.R + 1 : p->bz.T; break;
     case 9: *value = p->ytaps_max; break;
     case 10: *value = p->x_variant; break;
+    case 11: *value = p->fused ? 1 : 0; break;
+    case 12: *value = p->reserve; break;
     default: set_error("ef_plan_info: unknown index %d", what); return EF_ERR_ARG;
     }
     return EF_OK;

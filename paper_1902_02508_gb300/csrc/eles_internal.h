@@ -31,6 +31,51 @@ struct Ring {
     float W32[kMaxStride * kMaxRing];
 };
 
+constexpr int kFusedMaxRows = 384;   // largest nz of the fused x-z kernel (one thread per z-row)
+
+// Parameters of the fused x-z kernel (FP32).
+struct FusedArgs {
+    const float *u;       // [S][3][ny][nz][nx]
+    float *h;             // [S][9][ny][nlz][nlx]
+    double *uref;         // [S][3][ny]
+    double *plane_mean;   // [S][3][ny] or nullptr
+    int nx, ny, nz, nlx, nlz;
+    int nblk_x;           // x ring: blocks streamed per row (a multiple of the stage blocks)
+    int bshift, dmin_x;   // stream block bi is row block bi - bshift (mod nlx); it completes X = bi - bshift + dmin
+    int dmax_z, ZQs, NQ;  // z ring: dmax, Z outputs per work item, items per column
+    int P, lP;            // completed columns parked per z phase (a power of two), log2 P
+    int nf;               // fields to contract in z (9, or 3 for the velocities only)
+    float WX[kMaxStride * kMaxRing];
+    float WZ[kMaxStride * kMaxRing];
+};
+
+bool fused_supported(int rx, int dx, int rz, int dz);
+int fused_stage_blocks(int rx);
+size_t fused_smem_bytes(int rx, int P, int nz);
+cudaError_t launch_fused(int rx, int dx, int rz, int dz, const FusedArgs &a, int nsnap, cudaStream_t st);
+
+// Parameters of the y-contraction and recovery (any precision).
+template <typename T>
+struct YArgs {
+    const T *h;            // [S][9][ny][nlz][nlx]
+    const T *wy;           // [S][nly][ny][8]: w+, w-, U1 w+, U1 w-, U2 w+, U2 w-, U3 w+, U3 w-
+    const double *AU;      // [S][3][nly]
+    const double *AUU;     // [S][6][nly]
+    const int *ystart, *ycount;
+    T *ubar, *tau;         // [S][3][..], [S][6][..]
+    T *tmp;                // [S][12][nly][nlz][nlx]: q_a and C_ab between the two passes
+    int ny, nly, nlz, nlx;
+    int stress, flip;      // flip: Eq. 9 parities
+    int *err;
+};
+
+template <typename T>
+cudaError_t launch_yprofile(const double *uref, const int *ystart, const int *ycount, const double *we,
+                            const double *wo, int ny, int nly, int flip, int nsnap, double *AU, double *AUU,
+                            T *wy, cudaStream_t st);
+template <typename T>
+cudaError_t launch_ypass(const YArgs<T> &a, int nsnap, cudaStream_t st);
+
 }  // namespace eles
 
 struct ef_plan {
@@ -48,15 +93,21 @@ struct ef_plan {
     float *d_yw32[2] = {nullptr, nullptr};
     int ytaps_max = 0;
     double *d_ygrid = nullptr;    // DNS y nodes on the device
-    // scratch owned by the plan
-    void *d_g = nullptr;          // x-contracted fields  [9][ny][nz][nlx]
-    void *d_h = nullptr;          // x,z-contracted fields [9][ny][nlz][nlx]
-    double *d_uref = nullptr;     // reference profile U_c(y_j), [3][ny]
-    void *d_urefT = nullptr;      // same in the working type
-    double *d_rowsum = nullptr;   // partial sums of the fluctuation, [3][ny][nzw]
+    bool fused = false;           // FP32 fused x-z kernel available for this plan
+    int NQ = 1, ZQs = 0, P = 8;   // its z work split and columns per z phase
+    int bshift = 0, nblk_x = 0;   // its x stream
+    // scratch owned by the plan, sized for `reserve` snapshots per launch
+    int reserve = 0;
+    void *d_g = nullptr;          // x-contracted fields of one snapshot [9][ny][nz][nlx] (unfused path)
+    void *d_h = nullptr;          // x,z-contracted fields [S][9][ny][nlz][nlx]
+    double *d_uref = nullptr;     // reference profile U_c(y_j), [S][3][ny]
+    void *d_urefT = nullptr;      // same in the working type, one snapshot
+    double *d_rowsum = nullptr;   // partial sums of the fluctuation, [3][ny][nzw], one snapshot
     int nzw = 0;
-    double *d_AU = nullptr;       // A_y U_c, [3][nly]
-    double *d_AUU = nullptr;      // A_y (U_a U_b), [6][nly]
+    double *d_AU = nullptr;       // A_y U_c, [S][3][nly]
+    double *d_AUU = nullptr;      // A_y (U_a U_b), [S][6][nly]
+    void *d_wy = nullptr;         // y weights with U folded in, [S][nly][ny][8]
+    void *d_ytmp = nullptr;       // q_a, C_ab between the y passes, [S][12][nly][nlz][nlx]
     int *d_err = nullptr;         // device error word
     // phase timing (ef_profile_enable)
     bool prof_on = false;
@@ -86,7 +137,8 @@ inline void prof_mark(const PhaseEvents *pe, int k, cudaStream_t s)
 }
 
 // filter_kernels.cu
-int run_filter(ef_plan *p, const void *u, void *ubar, void *tau, double *plane_mean,
+int run_filter(ef_plan *p, int nsnap, const void *u, void *ubar, void *tau, double *plane_mean,
                bool stress, cudaStream_t s, const PhaseEvents *pe);
+int plan_reserve(ef_plan *p, int nsnap);
 
 }  // namespace eles

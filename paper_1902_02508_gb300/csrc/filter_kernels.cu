@@ -50,8 +50,9 @@ __global__ void uref_kernel(const T *__restrict__ u, int nx, int ny, int nz, dou
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[w];
         t /= nx;
-        uref[c * ny + j] = t;
-        urefT[c * ny + j] = (T)t;
+        const T tt = (T)t;             // the value subtracted is the one the recovery uses
+        uref[c * ny + j] = (double)tt;
+        urefT[c * ny + j] = tt;
     }
 }
 
@@ -296,116 +297,7 @@ __global__ void zpass_gather(const T *__restrict__ g, T *__restrict__ h, const i
     h[(fj * nlz + Z) * nlx + X] = acc;
 }
 
-// ----------------------------------------------------------------- step 4 --
-// A_y U_a and A_y (U_a U_b) per LES row, FP64.
-__global__ void yprofile_kernel(const double *uref, const int *ystart, const int *ycount,
-                                const double *we, const double *wo, int ny, int nly,
-                                int p0, int p1, int p2, double *AU, double *AUU)
-{
-    int J = blockIdx.x * blockDim.x + threadIdx.x;
-    if (J >= nly) return;
-    const int par[3] = {p0, p1, p2};
-    const int PI[6] = {0, 0, 0, 1, 1, 2}, PJ[6] = {0, 1, 2, 1, 2, 2};
-    double au[3] = {0, 0, 0}, auu[6] = {0, 0, 0, 0, 0, 0};
-    for (int t = 0; t < ycount[J]; t++) {
-        int j = ystart[J] + t;
-        double wev = we[(size_t)J * ny + j], wod = wo[(size_t)J * ny + j];
-        double U[3] = {uref[j], uref[ny + j], uref[2 * ny + j]};
-        for (int c = 0; c < 3; c++) au[c] += (par[c] > 0 ? wev : wod) * U[c];
-        for (int k = 0; k < 6; k++)
-            auu[k] += (par[PI[k]] * par[PJ[k]] > 0 ? wev : wod) * U[PI[k]] * U[PJ[k]];
-    }
-    for (int c = 0; c < 3; c++) AU[c * nly + J] = au[c];
-    for (int k = 0; k < 6; k++) AUU[k * nly + J] = auu[k];
-}
-
-// One thread per LES point (J, Z, X); the CTA shares J, so the y-weights are
-// broadcast loads.  q_f = A_y h_f for the nine fields, C_ab = A_y(U_a h_b).
-template <typename T, typename TO>
-__global__ void __launch_bounds__(YT) ypass_tau(const T *__restrict__ h, const T *__restrict__ urefT,
-                                                const double *__restrict__ AU, const double *__restrict__ AUU,
-                                                const int *__restrict__ ystart, const int *__restrict__ ycount,
-                                                const T *__restrict__ we, const T *__restrict__ wo,
-                                                TO *__restrict__ ubar, TO *__restrict__ tau,
-                                                int ny, int nly, int nlz, int nlx, int p0, int p1, int p2,
-                                                int stress, int *err)
-{
-    const int J = blockIdx.y;
-    const int pidx = blockIdx.x * YT + threadIdx.x;
-    const int nplane = nlz * nlx;
-    if (pidx >= nplane) return;
-    const size_t nl = (size_t)nly * nplane;
-    const int par[3] = {p0, p1, p2};
-    const int PI[6] = {0, 0, 0, 1, 1, 2}, PJ[6] = {0, 1, 2, 1, 2, 2};
-    const int nf = stress ? 9 : 3;
-    T q[9];
-    T C[3][3];
-#pragma unroll
-    for (int f = 0; f < 9; f++) q[f] = T(0);
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-        for (int b = 0; b < 3; b++) C[a][b] = T(0);
-    const int st = ystart[J], cnt = ycount[J];
-    const T *hp = h + pidx;
-    for (int t = 0; t < cnt; t++) {
-        const int j = st + t;
-        const T wev = we[(size_t)J * ny + j], wod = wo[(size_t)J * ny + j];
-        T hv[9];
-#pragma unroll
-        for (int f = 0; f < 9; f++) hv[f] = f < nf ? __ldg(hp + ((size_t)f * ny + j) * nplane) : T(0);
-#pragma unroll
-        for (int c = 0; c < 3; c++) q[c] = fma(par[c] > 0 ? wev : wod, hv[c], q[c]);
-        if (stress) {
-#pragma unroll
-            for (int k = 0; k < 6; k++)
-                q[3 + k] = fma(par[PI[k]] * par[PJ[k]] > 0 ? wev : wod, hv[3 + k], q[3 + k]);
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                const T Ua = urefT[a * ny + j];
-#pragma unroll
-                for (int b = 0; b < 3; b++) {
-                    const T wab = par[a] * par[b] > 0 ? wev : wod;
-                    C[a][b] = fma(wab * Ua, hv[b], C[a][b]);
-                }
-            }
-        }
-    }
-    double ub[3];
-    bool bad = false;
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        ub[c] = AU[c * nly + J] + (double)q[c];
-        bad |= !isfinite(ub[c]);
-        ubar[c * nl + (size_t)J * nplane + pidx] = (TO)ub[c];
-    }
-    if (stress) {
-#pragma unroll
-        for (int k = 0; k < 6; k++) {
-            const int a = PI[k], b = PJ[k];
-            const double Aa = AU[a * nly + J], Ab = AU[b * nly + J];
-            const double qa = (double)q[a], qb = (double)q[b];
-            const double t = (AUU[k * nly + J] - Aa * Ab) + ((double)C[a][b] - Aa * qb)
-                           + ((double)C[b][a] - Ab * qa) + ((double)q[3 + k] - qa * qb);
-            bad |= !isfinite(t);
-            tau[k * nl + (size_t)J * nplane + pidx] = (TO)t;
-        }
-    }
-    if (bad) flag_error(err, EF_ERR_NAN);
-}
-
-// <u_c>(y_j) = U_c(y_j) + (sum of the fluctuation over the plane) / (nx nz)
-__global__ void plane_mean_finalize(const double *uref, const double *rowsum, int ny, int nzw,
-                                    double inv, double *out)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 3 * ny) return;
-    double s = 0.0;
-    for (int w = 0; w < nzw; w++) s += rowsum[(size_t)i * nzw + w];
-    out[i] = uref[i] + s * inv;
-}
-
-// Plane means by a plain reduction (used when the x-contraction has no ring).
+// Plane means by a plain reduction (unfused path).
 template <typename T>
 __global__ void plane_mean_direct(const T *__restrict__ u, const double *uref, int nx, int ny, int nz, double *out)
 {
@@ -488,24 +380,19 @@ bool dispatch_z(const Ring &rg, const ZArgs<T> &a, cudaStream_t s)
     return false;
 }
 
+// Unfused x and z contractions of one snapshot into h (FP64 path, and any
+// grid without a fused instantiation).
 template <typename T>
-int run_typed(ef_plan *p, const T *u, T *ubar, T *tau, double *plane_mean, bool stress, cudaStream_t s,
-              const PhaseEvents *pe)
+void xz_unfused(ef_plan *p, const T *u, T *h, double *uref, double *plane_mean, int nf, cudaStream_t s)
 {
-    const int nf = stress ? 9 : 3;
     T *g = static_cast<T *>(p->d_g);
-    T *h = static_cast<T *>(p->d_h);
     T *urefT = static_cast<T *>(p->d_urefT);
-
-    prof_mark(pe, 0, s);
-    uref_kernel<T><<<dim3(p->ny, 3), 256, 0, s>>>(u, p->nx, p->ny, p->nz, p->d_uref, urefT);
-    prof_mark(pe, 1, s);
-
+    uref_kernel<T><<<dim3(p->ny, 3), 256, 0, s>>>(u, p->nx, p->ny, p->nz, uref, urefT);
     bool ring_x = false;
-    if (p->x_variant == 1) {
+    if (p->rx.ok) {
         XArgs<T> a;
         a.u = u; a.uref = urefT; a.g = g;
-        a.rowsum = plane_mean ? p->d_rowsum : nullptr;
+        a.rowsum = nullptr;
         a.nx = p->nx; a.ny = p->ny; a.nz = p->nz; a.nlx = p->nlx; a.nzw = p->nzw;
         a.nblk = p->nlx + p->rx.D - 1;
         a.dmax = p->rx.dmax;
@@ -516,15 +403,13 @@ int run_typed(ef_plan *p, const T *u, T *ubar, T *tau, double *plane_mean, bool 
     if (!ring_x) {
         const size_t total = (size_t)p->ny * p->nz * p->nlx;
         const unsigned grid = (unsigned)((total + 127) / 128);
-        if (stress)
+        if (nf == 9)
             xpass_gather<T, 9><<<grid, 128, 0, s>>>(u, urefT, g, p->bx.d_start, band_w<T>(p->bx),
                                                     p->bx.T, p->nx, p->ny, p->nz, p->nlx);
         else
             xpass_gather<T, 3><<<grid, 128, 0, s>>>(u, urefT, g, p->bx.d_start, band_w<T>(p->bx),
                                                     p->bx.T, p->nx, p->ny, p->nz, p->nlx);
     }
-
-    prof_mark(pe, 2, s);
     bool ring_z = false;
     if (p->rz.ok) {
         ZArgs<T> a;
@@ -540,40 +425,85 @@ int run_typed(ef_plan *p, const T *u, T *ubar, T *tau, double *plane_mean, bool 
         zpass_gather<T><<<(unsigned)((total + 127) / 128), 128, 0, s>>>(
             g, h, p->bz.d_start, band_w<T>(p->bz), p->bz.T, nf, p->ny, p->nz, p->nlz, p->nlx);
     }
+    if (plane_mean)
+        plane_mean_direct<T><<<dim3(p->ny, 3), 256, 0, s>>>(u, uref, p->nx, p->ny, p->nz, plane_mean);
+}
 
-    prof_mark(pe, 3, s);
-    yprofile_kernel<<<(p->nly + 63) / 64, 64, 0, s>>>(p->d_uref, p->d_ystart, p->d_ycount, p->d_yw64[0],
-                                                      p->d_yw64[1], p->ny, p->nly, p->par[0], p->par[1],
-                                                      p->par[2], p->d_AU, p->d_AUU);
-    const T *we, *wo;
-    if constexpr (sizeof(T) == 4) { we = p->d_yw32[0]; wo = p->d_yw32[1]; }
-    else { we = p->d_yw64[0]; wo = p->d_yw64[1]; }
-    dim3 yg((p->nlz * p->nlx + YT - 1) / YT, p->nly);
-    ypass_tau<T, T><<<yg, YT, 0, s>>>(h, urefT, p->d_AU, p->d_AUU, p->d_ystart, p->d_ycount, we, wo,
-                                      ubar, tau, p->ny, p->nly, p->nlz, p->nlx, p->par[0], p->par[1],
-                                      p->par[2], stress ? 1 : 0, p->d_err);
-    prof_mark(pe, 4, s);
-    if (plane_mean) {
-        if (ring_x)
-            plane_mean_finalize<<<(3 * p->ny + 127) / 128, 128, 0, s>>>(
-                p->d_uref, p->d_rowsum, p->ny, p->nzw, 1.0 / ((double)p->nx * p->nz), plane_mean);
-        else
-            plane_mean_direct<T><<<dim3(p->ny, 3), 256, 0, s>>>(u, p->d_uref, p->nx, p->ny, p->nz, plane_mean);
+template <typename T>
+int run_group(ef_plan *p, int ns, const T *u, T *ubar, T *tau, double *plane_mean, bool stress,
+              cudaStream_t s, const PhaseEvents *pe)
+{
+    const int nf = stress ? 9 : 3;
+    const size_t np = (size_t)p->nx * p->ny * p->nz;
+    const size_t nh = (size_t)9 * p->ny * p->nlz * p->nlx;
+    T *h = static_cast<T *>(p->d_h);
+    cudaError_t e = cudaSuccess;
+    prof_mark(pe, 0, s);
+    if constexpr (sizeof(T) == 4) {
+        if (p->fused) {
+            FusedArgs a;
+            a.u = u; a.h = h; a.uref = p->d_uref; a.plane_mean = plane_mean;
+            a.nx = p->nx; a.ny = p->ny; a.nz = p->nz; a.nlx = p->nlx; a.nlz = p->nlz;
+            a.nblk_x = p->nblk_x; a.bshift = p->bshift; a.dmin_x = p->rx.dmin;
+            a.dmax_z = p->rz.dmax; a.ZQs = p->ZQs; a.NQ = p->NQ; a.P = p->P; a.nf = nf;
+            a.lP = 0;
+            while ((1 << a.lP) < a.P) a.lP++;
+            for (int i = 0; i < p->rx.r * p->rx.D; i++) a.WX[i] = p->rx.W32[i];
+            for (int i = 0; i < p->rz.r * p->rz.D; i++) a.WZ[i] = p->rz.W32[i];
+            e = launch_fused(p->rx.r, p->rx.D, p->rz.r, p->rz.D, a, ns, s);
+            if (e != cudaSuccess) return cuda_fail(e, "xz_fused launch");
+        }
     }
-    cudaError_t e = cudaGetLastError();
+    if (!p->fused) {
+        for (int k = 0; k < ns; k++)
+            xz_unfused<T>(p, u + k * 3 * np, h + k * nh, p->d_uref + (size_t)k * 3 * p->ny,
+                          plane_mean ? plane_mean + (size_t)k * 3 * p->ny : nullptr, nf, s);
+    }
+    prof_mark(pe, 1, s);
+    prof_mark(pe, 2, s);
+    T *wy = static_cast<T *>(p->d_wy);
+    e = launch_yprofile<T>(p->d_uref, p->d_ystart, p->d_ycount, p->d_yw64[0], p->d_yw64[1], p->ny, p->nly,
+                           p->ext == EF_EXT_ODD_EVEN, ns, p->d_AU, p->d_AUU, wy, s);
+    if (e != cudaSuccess) return cuda_fail(e, "yprofile launch");
+    YArgs<T> y;
+    y.h = h; y.wy = wy; y.AU = p->d_AU; y.AUU = p->d_AUU; y.ystart = p->d_ystart; y.ycount = p->d_ycount;
+    y.ubar = ubar; y.tau = tau; y.tmp = static_cast<T *>(p->d_ytmp); y.ny = p->ny; y.nly = p->nly; y.nlz = p->nlz; y.nlx = p->nlx;
+    y.stress = stress ? 1 : 0; y.flip = p->ext == EF_EXT_ODD_EVEN; y.err = p->d_err;
+    e = launch_ypass<T>(y, ns, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ypass launch");
+    prof_mark(pe, 3, s);
+    prof_mark(pe, 4, s);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "filter launch");
+    return EF_OK;
+}
+
+template <typename T>
+int run_typed(ef_plan *p, int nsnap, const T *u, T *ubar, T *tau, double *plane_mean, bool stress,
+              cudaStream_t s, const PhaseEvents *pe)
+{
+    const size_t np = (size_t)p->nx * p->ny * p->nz;
+    const size_t nl = (size_t)p->nlx * p->nly * p->nlz;
+    for (int s0 = 0; s0 < nsnap; s0 += p->reserve) {
+        const int ns = nsnap - s0 < p->reserve ? nsnap - s0 : p->reserve;
+        const bool last = s0 + ns >= nsnap;
+        int rc = run_group<T>(p, ns, u + s0 * 3 * np, ubar + s0 * 3 * nl, stress ? tau + s0 * 6 * nl : nullptr,
+                              plane_mean ? plane_mean + (size_t)s0 * 3 * p->ny : nullptr, stress, s,
+                              last ? pe : nullptr);
+        if (rc) return rc;
+    }
     return EF_OK;
 }
 
 }  // namespace
 
-int run_filter(ef_plan *p, const void *u, void *ubar, void *tau, double *plane_mean, bool stress,
+int run_filter(ef_plan *p, int nsnap, const void *u, void *ubar, void *tau, double *plane_mean, bool stress,
                cudaStream_t s, const PhaseEvents *pe)
 {
     if (p->prec == EF_PREC_FP64)
-        return run_typed<double>(p, static_cast<const double *>(u), static_cast<double *>(ubar),
+        return run_typed<double>(p, nsnap, static_cast<const double *>(u), static_cast<double *>(ubar),
                                  static_cast<double *>(tau), plane_mean, stress, s, pe);
-    return run_typed<float>(p, static_cast<const float *>(u), static_cast<float *>(ubar),
+    return run_typed<float>(p, nsnap, static_cast<const float *>(u), static_cast<float *>(ubar),
                             static_cast<float *>(tau), plane_mean, stress, s, pe);
 }
 

@@ -28,6 +28,7 @@ PREC_FP64, PREC_FP32, PREC_TF32X2, PREC_BF16X3 = 0, 1, 2, 3
 
 # every symbol include/eles.h declares
 EXPORTED = ("ef_filter_setup", "ef_plan_destroy", "ef_filter_fields", "ef_subfilter_stress",
+            "ef_subfilter_stress_batch", "ef_plan_reserve",
             "ef_check_device_error", "ef_plan_info", "ef_plan_weights", "ef_profile_enable",
             "ef_profile_read", "ef_last_error", "ef_version")
 
@@ -66,6 +67,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             lib.ef_filter_fields.restype = i
             lib.ef_subfilter_stress.argtypes = [vp, vp, vp, vp, vp, vp]
             lib.ef_subfilter_stress.restype = i
+            lib.ef_subfilter_stress_batch.argtypes = [vp, i, vp, vp, vp, vp, vp]
+            lib.ef_subfilter_stress_batch.restype = i
+            lib.ef_plan_reserve.argtypes = [vp, i]
+            lib.ef_plan_reserve.restype = i
             lib.ef_check_device_error.argtypes = [vp, vp]
             lib.ef_check_device_error.restype = i
             lib.ef_plan_info.argtypes = [vp, i, ctypes.POINTER(ctypes.c_long)]
@@ -163,6 +168,22 @@ def subfilter_stress(plan: Plan, u, ubar, tau, plane_mean=None, stream=None) -> 
     _check(load().ef_subfilter_stress(plan.handle, pu, pb, pt, pm, _stream(stream)))
 
 
+def subfilter_stress_batch(plan: Plan, u, ubar, tau, plane_mean=None, stream=None) -> None:
+    """u [S][3][ny][nz][nx], ubar [S][3][..], tau [S][6][..], plane_mean [S][3][ny] or None."""
+    import torch
+    d, l = plan.dns, plan.les
+    ns = u.shape[0]
+    pu = _field(u, (ns, 3, d.ny, d.nz, d.nx), plan.dtype, "u")
+    pb = _field(ubar, (ns, 3, l.ny, l.nz, l.nx), plan.dtype, "ubar")
+    pt = _field(tau, (ns, 6, l.ny, l.nz, l.nx), plan.dtype, "tau")
+    pm = _field(plane_mean, (ns, 3, d.ny), torch.float64, "plane_mean")
+    _check(load().ef_subfilter_stress_batch(plan.handle, ns, pu, pb, pt, pm, _stream(stream)))
+
+
+def plan_reserve(plan: Plan, max_snapshots: int) -> None:
+    _check(load().ef_plan_reserve(plan.handle, int(max_snapshots)))
+
+
 def check_device_error(plan: Plan, stream=None) -> int:
     return load().ef_check_device_error(plan.handle, _stream(stream))
 
@@ -186,7 +207,7 @@ def profile_enable(plan: Plan, on: bool = True) -> None:
 
 
 def profile_read(plan: Plan):
-    """(ms per phase [profile, x, z, y], calls) summed since profile_enable."""
+    """(ms per phase [x+z, 0, y + recovery, 0], calls) summed since profile_enable."""
     ms = np.zeros(4)
     n = ctypes.c_long()
     _check(load().ef_profile_read(plan.handle, ms.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)))

@@ -193,6 +193,40 @@ def test_nan_input_sets_device_error():
     assert eles.check_device_error(plan) == 0      # the word is cleared by the read
 
 
+@pytest.mark.parametrize("name", ["tiny", "tiles"])
+def test_batch_equals_single_calls(name):
+    """Three snapshots in one batched call (two groups: reserve 2) give the
+    same bits as three single calls."""
+    dns, les, delta, u0 = case(name, seed=31)
+    us = np.stack([u0, I.shifted(u0, 3, 1), I.channel_velocity(dns, 32)])
+    plan = eles.filter_setup(dns, les, delta, precision=eles.PREC_FP32)
+    eles.plan_reserve(plan, 2)
+    dev = torch.device("cuda")
+    ud = torch.from_numpy(us).to(dev, torch.float32)
+    ub = torch.empty((3, 3, les.ny, les.nz, les.nx), device=dev)
+    tau = torch.empty((3, 6, les.ny, les.nz, les.nx), device=dev)
+    pm = torch.empty((3, 3, dns.ny), device=dev, dtype=torch.float64)
+    eles.subfilter_stress_batch(plan, ud, ub, tau, pm)
+    for k in range(3):
+        ub1 = torch.empty((3, les.ny, les.nz, les.nx), device=dev)
+        t1 = torch.empty((6, les.ny, les.nz, les.nx), device=dev)
+        pm1 = torch.empty((3, dns.ny), device=dev, dtype=torch.float64)
+        eles.subfilter_stress(plan, ud[k].contiguous(), ub1, t1, pm1)
+        torch.cuda.synchronize()
+        assert torch.equal(ub1, ub[k]) and torch.equal(t1, tau[k]) and torch.equal(pm1, pm[k])
+    _, tau_ref = O.subfilter_stress(dns, les, delta, us[2])
+    assert np.abs(tau[2].double().cpu().numpy() - tau_ref).max() <= TOL32
+
+
+def test_fused_path_is_used_for_channel_shapes():
+    for (nx, ny, nz, Lx, Lz, nlx, nly, nlz, dfrac) in [(192, 129, 192, 4 * math.pi, 2 * math.pi, 32, 33, 32, 32),
+                                                        (512, 257, 384, 2 * math.pi, math.pi, 64, 65, 48, 64),
+                                                        (512, 257, 384, 2 * math.pi, math.pi, 64, 65, 48, 32)]:
+        dns = I.dns_grid(nx, ny, nz, Lx, Lz)
+        plan = eles.filter_setup(dns, I.les_grid(dns, nlx, nly, nlz), Lx / dfrac, precision=eles.PREC_FP32)
+        assert eles.plan_info(plan, 11) == 1
+
+
 def test_repeat_calls_are_bitwise_stable():
     dns, les, delta, u = case("tiles", seed=2)
     plan = eles.filter_setup(dns, les, delta, precision=eles.PREC_FP32)
