@@ -43,8 +43,8 @@ UNIT = "DNS points/s"
 WORKLOADS = {
     # name: (nx, ny, nz, Lx, Lz, nlx, nly, nlz, delta/Lx, snapshots per step)
     "re180": (192, 129, 192, 4 * math.pi, 2 * math.pi, 32, 33, 32, 1 / 32, 10),
-    "re550_d64": (512, 257, 384, 2 * math.pi, math.pi, 64, 65, 48, 1 / 64, 2),
-    "re550_d32": (512, 257, 384, 2 * math.pi, math.pi, 64, 65, 48, 1 / 32, 2),
+    "re550_d64": (512, 257, 384, 2 * math.pi, math.pi, 64, 65, 48, 1 / 64, 4),
+    "re550_d32": (512, 257, 384, 2 * math.pi, math.pi, 64, 65, 48, 1 / 32, 4),
 }
 PREC = {"fp32": 1, "fp64": 0, "bf16x3": 3}
 L2_BYTES = 129e6
@@ -56,8 +56,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="re180", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp32", choices=sorted(PREC))
+    ap.add_argument("--workload", default="re550_d64", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="bf16x3", choices=sorted(PREC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     return ap.parse_args()

@@ -155,6 +155,7 @@ void ef_plan_destroy(ef_plan *p)
     cudaFree(p->d_AUU);
     cudaFree(p->d_wy);
     cudaFree(p->d_ytmp);
+    cudaFree(p->d_zfrag);
     cudaFree(p->d_err);
     for (int t = 0; t < ef_plan::kProfSlots; t++)
         for (int k = 0; k < ef_plan::kProfEvents; k++)
@@ -173,7 +174,7 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
     if (!(delta > 0) || !isfinite(delta)) { set_error("delta must be finite and > 0"); return EF_ERR_ARG; }
     if (kernel != EF_KERNEL_GAUSSIAN) { set_error("only the Gaussian kernel is implemented"); return EF_ERR_UNSUPPORTED; }
     if (extension < EF_EXT_EVEN_ODD || extension > EF_EXT_NONE) { set_error("unknown extension %d", extension); return EF_ERR_ARG; }
-    if (precision != EF_PREC_FP64 && precision != EF_PREC_FP32) {
+    if (precision != EF_PREC_FP64 && precision != EF_PREC_FP32 && precision != EF_PREC_BF16X3) {
         set_error("precision %d not implemented", precision);
         return EF_ERR_UNSUPPORTED;
     }
@@ -203,12 +204,21 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
         if ((rc = build_ring(p->bz, &p->rz))) goto fail;
         p->x_variant = p->rx.ok ? 1 : 0;
         // FP32 plans use the fused x-z kernel when its ring sizes are instantiated
-        if (precision == EF_PREC_FP32 && p->rx.ok && p->rz.ok && p->nz <= kFusedMaxRows && p->nz % 32 == 0 &&
-            fused_supported(p->rx.r, p->rx.D, p->rz.r, p->rz.D) && p->nlx % fused_stage_blocks(p->rx.r) == 0) {
+        const bool tc = precision == EF_PREC_BF16X3 && p->rx.ok && p->rz.ok &&
+                        tc_supported(p->rx.r, p->rx.D, p->rz.r, p->rz.D, p->nlz);
+        if (precision != EF_PREC_FP64 && p->rx.ok && p->rz.ok && p->nz <= kFusedMaxRows && p->nz % 32 == 0 &&
+            (tc || fused_supported(p->rx.r, p->rx.D, p->rz.r, p->rz.D)) &&
+            p->nlx % fused_stage_blocks(p->rx.r) == 0) {
             const int SB = fused_stage_blocks(p->rx.r);
+            std::vector<unsigned> zf;
+            int zoff = 0;
+            const int KS = tc ? tc_zfrags(p->rz, p->nlz, zf, &zoff) : 0;
+            auto smem = [&](int P) {
+                return tc ? tc_smem_bytes(P, p->nz, KS) : fused_smem_bytes(p->rx.r, P, p->nz);
+            };
             p->P = 8;
-            while (p->P > 1 && fused_smem_bytes(p->rx.r, p->P, p->nz) > 222 * 1024) p->P /= 2;
-            if (fused_smem_bytes(p->rx.r, p->P, p->nz) <= 222 * 1024) {
+            while (p->P > 1 && smem(p->P) > 222 * 1024) p->P /= 2;
+            if (smem(p->P) <= 222 * 1024) {
                 p->fused = true;
                 p->NQ = 1;
                 for (int q = p->nz / (9 * p->P); q > 1; q--)
@@ -219,6 +229,18 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
                 p->bshift = (p->rx.dmax + SB - 1) / SB * SB;
                 const int need = p->nlx - p->rx.dmin + p->bshift;
                 p->nblk_x = (need + SB - 1) / SB * SB;
+                if (tc) {
+                    p->x_variant = 2;
+                    tc_weights(p->rx, &p->tc);
+                    p->tc.KS = KS;
+                    p->tc.zoff = zoff;
+                    if (KS > 0) {
+                        CK(cudaMalloc(&p->d_zfrag, sizeof(unsigned) * zf.size()), "cudaMalloc z fragments");
+                        CK(cudaMemcpy(p->d_zfrag, zf.data(), sizeof(unsigned) * zf.size(), cudaMemcpyHostToDevice),
+                           "copy z fragments");
+                        p->tc.afrag = p->d_zfrag;
+                    }
+                }
             }
         }
         p->nzw = (p->nz + 31) / 32;

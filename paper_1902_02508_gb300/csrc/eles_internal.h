@@ -2,8 +2,11 @@
 // Nothing here is part of the C ABI (that is include/eles.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <vector>
 
 #include "eles.h"
 
@@ -35,6 +38,8 @@ constexpr int kFusedMaxRows = 384;   // largest nz of the fused x-z kernel (one 
 
 // Parameters of the fused x-z kernel (FP32).
 struct FusedArgs {
+    CUtensorMap tmap;     // TMA view of u: {nx, nz, 3 ny S} floats, box {8, box_rows, 1} (when use_tma)
+    int use_tma, box_rows;
     const float *u;       // [S][3][ny][nz][nx]
     float *h;             // [S][9][ny][nlz][nlx]
     double *uref;         // [S][3][ny]
@@ -45,9 +50,27 @@ struct FusedArgs {
     int dmax_z, ZQs, NQ;  // z ring: dmax, Z outputs per work item, items per column
     int P, lP;            // completed columns parked per z phase (a power of two), log2 P
     int nf;               // fields to contract in z (9, or 3 for the velocities only)
+    int *err;             // device error word
     float WX[kMaxStride * kMaxRing];
     float WZ[kMaxStride * kMaxRing];
 };
+
+// Tensor-core variant: FusedArgs plus the B fragments (hi and lo split) of
+// the x-operator tile, two 32-bit words per lane.
+struct FusedTCArgs {
+    FusedArgs f;
+    unsigned Bh[64];
+    unsigned Bl[64];
+    int KS = 0, zoff = 0;          // tensor-core z phase: k-steps per Z tile, window offset (KS 0: CUDA cores)
+    const uint4 *afrag = nullptr;  // its A fragments [KS][32][hi, lo] (device)
+};
+bool tc_supported(int rx, int dx, int rz, int dz, int nlz);
+void tc_weights(const Ring &rx, FusedTCArgs *ta);
+size_t tc_smem_bytes(int P, int nz, int KS);
+// Encode the TMA view of a batch of snapshots u [S][3][ny][nz][nx] (host).
+int encode_u_map(const float *u, int nx, int ny, int nz, int nsnap, int box_rows, CUtensorMap *map);
+cudaError_t launch_fused_tc(int rz, int dz, const FusedTCArgs &ta, int nsnap, cudaStream_t st);
+int tc_zfrags(const Ring &rz, int nlz, std::vector<unsigned> &out, int *zoff_out);
 
 bool fused_supported(int rx, int dx, int rz, int dz);
 int fused_stage_blocks(int rx);
@@ -96,6 +119,8 @@ struct ef_plan {
     bool fused = false;           // FP32 fused x-z kernel available for this plan
     int NQ = 1, ZQs = 0, P = 8;   // its z work split and columns per z phase
     int bshift = 0, nblk_x = 0;   // its x stream
+    eles::FusedTCArgs tc;         // tensor-core B fragments (x_variant 2)
+    uint4 *d_zfrag = nullptr;     // tensor-core z-phase A fragments
     // scratch owned by the plan, sized for `reserve` snapshots per launch
     int reserve = 0;
     void *d_g = nullptr;          // x-contracted fields of one snapshot [9][ny][nz][nlx] (unfused path)

@@ -18,6 +18,7 @@
 // precision; the large mean-flow terms are FP64.
 #include <math.h>
 #include <stdio.h>
+#include <string.h>
 
 #include "eles_internal.h"
 
@@ -442,6 +443,8 @@ int run_group(ef_plan *p, int ns, const T *u, T *ubar, T *tau, double *plane_mea
     if constexpr (sizeof(T) == 4) {
         if (p->fused) {
             FusedArgs a;
+            memset(&a, 0, sizeof a);
+            a.err = p->d_err;
             a.u = u; a.h = h; a.uref = p->d_uref; a.plane_mean = plane_mean;
             a.nx = p->nx; a.ny = p->ny; a.nz = p->nz; a.nlx = p->nlx; a.nlz = p->nlz;
             a.nblk_x = p->nblk_x; a.bshift = p->bshift; a.dmin_x = p->rx.dmin;
@@ -450,7 +453,17 @@ int run_group(ef_plan *p, int ns, const T *u, T *ubar, T *tau, double *plane_mea
             while ((1 << a.lP) < a.P) a.lP++;
             for (int i = 0; i < p->rx.r * p->rx.D; i++) a.WX[i] = p->rx.W32[i];
             for (int i = 0; i < p->rz.r * p->rz.D; i++) a.WZ[i] = p->rz.W32[i];
-            e = launch_fused(p->rx.r, p->rx.D, p->rz.r, p->rz.D, a, ns, s);
+            if (p->x_variant == 2) {
+                FusedTCArgs ta = p->tc;
+                a.box_rows = p->nz > 256 ? p->nz / 2 : p->nz;
+                a.use_tma = 1;
+                int rc = encode_u_map(u, p->nx, p->ny, p->nz, ns, a.box_rows, &a.tmap);
+                if (rc) return rc;
+                ta.f = a;     // KS, zoff, afrag and the B fragments come from the plan
+                e = launch_fused_tc(p->rz.r, p->rz.D, ta, ns, s);
+            } else {
+                e = launch_fused(p->rx.r, p->rx.D, p->rz.r, p->rz.D, a, ns, s);
+            }
             if (e != cudaSuccess) return cuda_fail(e, "xz_fused launch");
         }
     }

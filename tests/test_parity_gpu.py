@@ -65,6 +65,8 @@ CASES = {
     "stride6": (96, 49, 96, 4 * math.pi, 2 * math.pi, 16, 13, 16, 4 * math.pi / 16),
     # non-integer DNS/LES ratios in x, y and z: generic banded path + interpolation
     "interp": (30, 25, 20, 2 * math.pi, math.pi, 9, 8, 6, 0.5),
+    # stride 8 in x and z with a short x ring: the tensor-core x-contraction
+    "tc": (128, 65, 128, 2 * math.pi, math.pi, 16, 17, 16, 12 * math.pi / 128),
 }
 
 
@@ -87,7 +89,7 @@ def test_weights_match_oracle(name):
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
-@pytest.mark.parametrize("prec", [eles.PREC_FP64, eles.PREC_FP32])
+@pytest.mark.parametrize("prec", [eles.PREC_FP64, eles.PREC_FP32, eles.PREC_BF16X3])
 def test_subfilter_stress_matches_oracle(name, prec):
     dns, les, delta, u = case(name)
     ub_ref, tau_ref = O.subfilter_stress(dns, les, delta, u)
@@ -131,13 +133,15 @@ def big_field():
     return _BIG["v"]
 
 
-@pytest.mark.parametrize("dfrac", [64, 32])
-def test_full_size_sampled_points(dfrac):
+@pytest.mark.parametrize("dfrac,prec", [(64, eles.PREC_FP32), (32, eles.PREC_FP32), (64, eles.PREC_BF16X3)])
+def test_full_size_sampled_points(dfrac, prec):
     """512 x 257 x 384 -> 64 x 65 x 48 at full size, checked at seeded LES
     points (wall rows included) by the oracle's direct 3-D summation."""
     dns, les, u = big_field()
     delta = dns.Lx / dfrac
-    _, (ub, tau) = run_gpu(dns, les, delta, u, eles.PREC_FP32)
+    plan, (ub, tau) = run_gpu(dns, les, delta, u, prec)
+    if prec == eles.PREC_BF16X3:
+        assert eles.plan_info(plan, 10) == 2          # tensor-core x-contraction
     rng = np.random.default_rng(3)
     pts = np.stack([rng.integers(0, les.nx, 12), rng.integers(0, les.ny, 12),
                     rng.integers(0, les.nz, 12)], axis=1)
@@ -225,6 +229,14 @@ def test_fused_path_is_used_for_channel_shapes():
         dns = I.dns_grid(nx, ny, nz, Lx, Lz)
         plan = eles.filter_setup(dns, I.les_grid(dns, nlx, nly, nlz), Lx / dfrac, precision=eles.PREC_FP32)
         assert eles.plan_info(plan, 11) == 1
+
+
+def test_tensor_core_variant_selected():
+    dns, les, delta, _ = case("tc")
+    plan = eles.filter_setup(dns, les, delta, precision=eles.PREC_BF16X3)
+    assert eles.plan_info(plan, 10) == 2 and eles.plan_info(plan, 11) == 1
+    plan32 = eles.filter_setup(dns, les, delta, precision=eles.PREC_FP32)
+    assert eles.plan_info(plan32, 10) == 1
 
 
 def test_repeat_calls_are_bitwise_stable():
