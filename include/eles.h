@@ -192,6 +192,83 @@ int ef_plan_weights(const ef_plan *plan, int which, double *dst);
 int ef_profile_enable(ef_plan *plan, int on);
 int ef_profile_read(ef_plan *plan, double *ms, long *calls);
 
+/* ------------------------------------------------------------------------
+ * Learned closure.  The paper proposes using the exact stress computed from
+ * DNS to inform subgrid models, e.g. by machine learning (Sec. 2.1 and the
+ * summary, Sec. 5).  The library provides one such model: an MLP
+ * 10 -> 128 -> 128 -> 128 -> 6 with SiLU activations mapping the nine
+ * filtered velocity gradients d~bar(u_i)/dx_j and the wall distance
+ * y+ = (1 - |y|) Re_tau to T_11, T_12, T_13, T_22, T_23, T_33, trained with
+ * Adam (mean-squared error on standardised inputs and targets) on the exact
+ * T_ij of ef_subfilter_stress.  FP32 master weights, BF16 working weights,
+ * FP32 accumulation; fixed-order reductions (reproducible bit for bit).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int hidden;               /* must be 128 */
+    int batch;                /* mini-batch size (also the inference chunk) */
+    float lr;                 /* Adam learning rate */
+    float guard_sigma;        /* inference guard: a standardised input beyond this uses the exact stress */
+    unsigned long long seed;  /* initialisation and batch order */
+} ef_closure_cfg;
+
+typedef struct ef_closure ef_closure;
+
+/* Create a closure on the current device (allocates; synchronises). */
+int ef_closure_create(const ef_closure_cfg *cfg, ef_closure **out);
+void ef_closure_destroy(ef_closure *closure);
+
+/*
+ * ef_closure_features -- the ten inputs at every LES node.
+ *  les     LES grid (host; y nodes as in ef_filter_setup)
+ *  ubar    device float [3][nly][nlz][nlx] (e.g. from ef_subfilter_stress)
+ *  re_tau  friction Reynolds number for y+
+ *  extension  EF_EXT_* (wall parities of the mirror ghosts in y)
+ *  feats   device float [N][10], N = nly nlz nlx, point order (J, Z, X):
+ *          d~bar(u_i)/dx_j at 3i + j (j = x, y, z), then y+.
+ * Second-order central differences; periodic in x and z; three-point
+ * non-uniform stencil in y with mirror ghosts at the walls (Eq. 8).
+ * Allocates a small temporary for the y nodes (stream-ordered).
+ */
+int ef_closure_features(const ef_grid *les, const float *ubar, double re_tau, int extension, float *feats,
+                        void *stream);
+
+/* Standardisation statistics from training data: feats device [N][10],
+ * tau device [6][N] (component-major, the layout of ef_subfilter_stress). */
+int ef_closure_fit_norm(ef_closure *closure, const float *feats, const float *tau, long n, void *stream);
+
+/* Train for `epochs` passes over n points (fits the statistics first if not
+ * yet done).  Synchronises the stream; *loss_out = mean loss of the last
+ * epoch (standardised units). */
+int ef_closure_train(ef_closure *closure, const float *feats, const float *tau, long n, int epochs,
+                     void *stream, float *loss_out);
+
+/*
+ * ef_closure_infer -- tau_out device [6][N] from feats device [N][10].  Where
+ * a standardised input exceeds the guard the model is outside its training
+ * range: if exact_tau (device [6][N]) is given that exact stress is used
+ * there, and *n_fallback (if not NULL) receives the count (synchronises).
+ */
+int ef_closure_infer(ef_closure *closure, const float *feats, float *tau_out, long n, const float *exact_tau,
+                     long *n_fallback, void *stream);
+
+/* One forward and backward pass over n <= batch points without an update:
+ * host grad_out[param count] (layout of ef_closure_get_params), *loss_out. */
+int ef_closure_gradients(ef_closure *closure, const float *feats, const float *tau, long n, float *grad_out,
+                         float *loss_out, void *stream);
+
+/* Parameter count; parameters are stored per layer as W [out][in] then b [out]. */
+long ef_closure_param_count(const ef_closure *closure);
+/* Copy the FP32 master parameters (host [count]) and the 32 statistics
+ * (fmu[10], fsd[10], tmu[6], tsd[6]) out or in (either pointer may be NULL). */
+int ef_closure_get_params(const ef_closure *closure, float *params, double *norm_stats);
+int ef_closure_set_params(ef_closure *closure, const float *params, const double *norm_stats);
+
+/* Checkpoint to / from a flat little-endian file with a CRC-32 (weights,
+ * Adam moments, step count, statistics); resuming training from a checkpoint
+ * reproduces an uninterrupted run bit for bit. */
+int ef_closure_save(const ef_closure *closure, const char *path);
+int ef_closure_load(ef_closure *closure, const char *path);
+
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char *ef_last_error(void);
 

@@ -30,7 +30,10 @@ PREC_FP64, PREC_FP32, PREC_TF32X2, PREC_BF16X3 = 0, 1, 2, 3
 EXPORTED = ("ef_filter_setup", "ef_plan_destroy", "ef_filter_fields", "ef_subfilter_stress",
             "ef_subfilter_stress_batch", "ef_plan_reserve",
             "ef_check_device_error", "ef_plan_info", "ef_plan_weights", "ef_profile_enable",
-            "ef_profile_read", "ef_last_error", "ef_version")
+            "ef_profile_read", "ef_last_error", "ef_version", "ef_closure_create", "ef_closure_destroy",
+            "ef_closure_features", "ef_closure_fit_norm", "ef_closure_train", "ef_closure_infer",
+            "ef_closure_gradients", "ef_closure_param_count", "ef_closure_get_params", "ef_closure_set_params",
+            "ef_closure_save", "ef_closure_load")
 
 
 class EFError(RuntimeError):
@@ -43,6 +46,11 @@ class _Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("Lx", ctypes.c_double), ("Lz", ctypes.c_double),
                 ("y", ctypes.POINTER(ctypes.c_double))]
+
+
+class _ClosureCfg(ctypes.Structure):
+    _fields_ = [("hidden", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
+                ("guard_sigma", ctypes.c_float), ("seed", ctypes.c_ulonglong)]
 
 
 _lib = None
@@ -81,6 +89,31 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             lib.ef_profile_enable.restype = i
             lib.ef_profile_read.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_long)]
             lib.ef_profile_read.restype = i
+            L = ctypes.c_long
+            lib.ef_closure_create.argtypes = [ctypes.POINTER(_ClosureCfg), ctypes.POINTER(vp)]
+            lib.ef_closure_create.restype = i
+            lib.ef_closure_destroy.argtypes = [vp]
+            lib.ef_closure_destroy.restype = None
+            lib.ef_closure_features.argtypes = [ctypes.POINTER(_Grid), vp, d, i, vp, vp]
+            lib.ef_closure_features.restype = i
+            lib.ef_closure_fit_norm.argtypes = [vp, vp, vp, L, vp]
+            lib.ef_closure_fit_norm.restype = i
+            lib.ef_closure_train.argtypes = [vp, vp, vp, L, i, vp, ctypes.POINTER(ctypes.c_float)]
+            lib.ef_closure_train.restype = i
+            lib.ef_closure_infer.argtypes = [vp, vp, vp, L, vp, ctypes.POINTER(L), vp]
+            lib.ef_closure_infer.restype = i
+            lib.ef_closure_gradients.argtypes = [vp, vp, vp, L, vp, ctypes.POINTER(ctypes.c_float), vp]
+            lib.ef_closure_gradients.restype = i
+            lib.ef_closure_param_count.argtypes = [vp]
+            lib.ef_closure_param_count.restype = L
+            lib.ef_closure_get_params.argtypes = [vp, vp, vp]
+            lib.ef_closure_get_params.restype = i
+            lib.ef_closure_set_params.argtypes = [vp, vp, vp]
+            lib.ef_closure_set_params.restype = i
+            lib.ef_closure_save.argtypes = [vp, ctypes.c_char_p]
+            lib.ef_closure_save.restype = i
+            lib.ef_closure_load.argtypes = [vp, ctypes.c_char_p]
+            lib.ef_closure_load.restype = i
             lib.ef_last_error.restype = ctypes.c_char_p
             lib.ef_version.restype = ctypes.c_char_p
             _lib = lib
@@ -216,3 +249,125 @@ def profile_read(plan: Plan):
 
 def version() -> str:
     return load().ef_version().decode()
+
+
+# ----------------------------------------------------------------- closure --
+class Closure:
+    """Owns an ef_closure*.  Created by closure_create()."""
+
+    def __init__(self, handle, cfg):
+        self.handle, self.cfg = handle, cfg
+
+    def close(self):
+        if self.handle:
+            load().ef_closure_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def closure_create(batch: int = 4096, lr: float = 1e-3, guard_sigma: float = 8.0, seed: int = 1,
+                   hidden: int = 128) -> Closure:
+    cfg = _ClosureCfg(hidden, batch, lr, guard_sigma, seed)
+    h = ctypes.c_void_p()
+    _check(load().ef_closure_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return Closure(h, cfg)
+
+
+def closure_features(les, ubar, feats, re_tau: float = 180.0, extension: int = EXT_EVEN_ODD, stream=None):
+    import torch
+    g, y = _grid(les)
+    n = les.nx * les.ny * les.nz
+    pb = _field(ubar, (3, les.ny, les.nz, les.nx), torch.float32, "ubar")
+    pf = _field(feats, (n, 10), torch.float32, "feats")
+    _check(load().ef_closure_features(ctypes.byref(g), pb, float(re_tau), int(extension), pf, _stream(stream)))
+
+
+def _n_feats(feats):
+    if feats.dim() != 2 or feats.shape[1] != 10:
+        raise ValueError("feats must be [N][10]")
+    return feats.shape[0]
+
+
+def closure_fit_norm(cl: Closure, feats, tau, stream=None):
+    import torch
+    n = _n_feats(feats)
+    _check(load().ef_closure_fit_norm(cl.handle, _field(feats, (n, 10), torch.float32, "feats"),
+                                      _field(tau, (6, n), torch.float32, "tau"), n, _stream(stream)))
+
+
+def closure_train(cl: Closure, feats, tau, epochs: int, stream=None) -> float:
+    import torch
+    n = _n_feats(feats)
+    loss = ctypes.c_float()
+    _check(load().ef_closure_train(cl.handle, _field(feats, (n, 10), torch.float32, "feats"),
+                                   _field(tau, (6, n), torch.float32, "tau"), n, int(epochs), _stream(stream),
+                                   ctypes.byref(loss)))
+    return loss.value
+
+
+def closure_infer(cl: Closure, feats, tau_out, exact_tau=None, stream=None) -> int:
+    import torch
+    n = _n_feats(feats)
+    nf = ctypes.c_long()
+    _check(load().ef_closure_infer(cl.handle, _field(feats, (n, 10), torch.float32, "feats"),
+                                   _field(tau_out, (6, n), torch.float32, "tau_out"), n,
+                                   _field(exact_tau, (6, n), torch.float32, "exact_tau"), ctypes.byref(nf),
+                                   _stream(stream)))
+    return nf.value
+
+
+def closure_param_count(cl: Closure) -> int:
+    return load().ef_closure_param_count(cl.handle)
+
+
+def closure_gradients(cl: Closure, feats, tau, stream=None):
+    import torch
+    n = _n_feats(feats)
+    g = np.zeros(closure_param_count(cl), dtype=np.float32)
+    loss = ctypes.c_float()
+    _check(load().ef_closure_gradients(cl.handle, _field(feats, (n, 10), torch.float32, "feats"),
+                                       _field(tau, (6, n), torch.float32, "tau"), n,
+                                       g.ctypes.data_as(ctypes.c_void_p), ctypes.byref(loss), _stream(stream)))
+    return g, loss.value
+
+
+def closure_get_params(cl: Closure):
+    p = np.zeros(closure_param_count(cl), dtype=np.float32)
+    st = np.zeros(32)
+    _check(load().ef_closure_get_params(cl.handle, p.ctypes.data_as(ctypes.c_void_p), st.ctypes.data_as(ctypes.c_void_p)))
+    return p, st
+
+
+def closure_set_params(cl: Closure, params=None, stats=None):
+    pp = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+    ss = None if stats is None else np.ascontiguousarray(stats, dtype=np.float64)
+    _check(load().ef_closure_set_params(cl.handle, None if pp is None else pp.ctypes.data_as(ctypes.c_void_p),
+                                        None if ss is None else ss.ctypes.data_as(ctypes.c_void_p)))
+
+
+def closure_save(cl: Closure, path: str):
+    _check(load().ef_closure_save(cl.handle, path.encode()))
+
+
+def closure_load(cl: Closure, path: str):
+    _check(load().ef_closure_load(cl.handle, path.encode()))
+
+
+CLOSURE_LAYERS = ((10, 128), (128, 128), (128, 128), (128, 6))
+
+
+def closure_unpack(params):
+    """Flat parameter vector -> [(W [out][in], b [out]), ...]."""
+    out, off = [], 0
+    for fi, fo in CLOSURE_LAYERS:
+        W = params[off:off + fi * fo].reshape(fo, fi)
+        off += fi * fo
+        b = params[off:off + fo]
+        off += fo
+        out.append((W, b))
+    return out

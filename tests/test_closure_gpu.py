@@ -1,0 +1,153 @@
+"""GPU tests of the learned closure (through the C ABI).
+
+* features against the FP64 reference (oracle/mlp.py);
+* one forward + backward pass against the FP64 reference gradients at the
+  same (BF16-rounded) weights and standardisation, per layer;
+* training lowers the loss; resuming from a checkpoint reproduces an
+  uninterrupted run bit for bit;
+* the gain: on a held-out snapshot the trained network's error against the
+  exact T_ij is well below that of the model-free LES (T = 0), and the
+  guarded inference falls back to the exact stress where asked.
+"""
+import math
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import __graft_entry__ as entry
+from oracle import mlp as M
+from oracle import oracle as O
+from paper_1902_02508_gb300 import eles
+from paper_1902_02508_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    entry.build()
+
+
+def bf16(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+_DATA = {}
+
+
+def dataset(nsnap=5):
+    """Exact (ubar, tau, features) of channel snapshots: DNS 128 x 65 x 128 in
+    4 pi x 2 x 2 pi -> LES 32 x 33 x 32, Delta = Lx / 32."""
+    if "v" not in _DATA:
+        dns = I.dns_grid(128, 65, 128, 4 * math.pi, 2 * math.pi)
+        les = I.les_grid(dns, 32, 33, 32)
+        delta = dns.Lx / 32
+        plan = eles.filter_setup(dns, les, delta, precision=eles.PREC_FP32)
+        dev = torch.device("cuda")
+        ubs, taus, feats = [], [], []
+        n = les.nx * les.ny * les.nz
+        for s in range(nsnap):
+            u = torch.from_numpy(I.channel_velocity(dns, 2000 + s)).to(dev, torch.float32)
+            ub = torch.empty((3, les.ny, les.nz, les.nx), device=dev)
+            tau = torch.empty((6, les.ny, les.nz, les.nx), device=dev)
+            eles.subfilter_stress(plan, u, ub, tau)
+            f = torch.empty((n, 10), device=dev)
+            eles.closure_features(les, ub, f)
+            ubs.append(ub), taus.append(tau.reshape(6, n)), feats.append(f)
+        torch.cuda.synchronize()
+        _DATA["v"] = (dns, les, delta, ubs, taus, feats)
+    return _DATA["v"]
+
+
+def test_features_match_reference():
+    dns, les, delta, ubs, taus, feats = dataset()
+    ref = M.features(ubs[0].double().cpu().numpy(), les)
+    got = feats[0].double().cpu().numpy()
+    scale = np.abs(ref).max(axis=0)
+    assert np.all(np.abs(got - ref).max(axis=0) <= 2e-5 * np.maximum(scale, 1.0))
+
+
+def test_gradients_match_reference():
+    dns, les, delta, ubs, taus, feats = dataset()
+    cl = eles.closure_create(batch=512, seed=7)
+    f, t = feats[0][:512].contiguous(), taus[0][:, :512].contiguous()
+    eles.closure_fit_norm(cl, f, t)
+    g, loss = eles.closure_gradients(cl, f, t)
+    p, st = eles.closure_get_params(cl)
+    params = [(bf16(W), bf16(b)) for W, b in eles.closure_unpack(p)]
+    X = (f.double().cpu().numpy() - st[:10]) / st[10:20]
+    T = ((t.double().cpu().numpy().T) - st[20:26]) / st[26:32]
+    X = X.astype(np.float32).astype(np.float64)
+    T = T.astype(np.float32).astype(np.float64)
+    Y, cache = M.forward(params, X)
+    ref = M.backward(params, cache, Y, T)
+    assert abs(loss - M.mse(Y, T)) <= 1e-4 * M.mse(Y, T)
+    gl = eles.closure_unpack(g)
+    for l, ((gW, gb), (rW, rb)) in enumerate(zip(gl, ref)):
+        assert np.abs(gW - rW).max() <= 2e-3 * np.abs(rW).max(), f"layer {l} W"
+        assert np.abs(gb - rb).max() <= 2e-3 * np.abs(rb).max(), f"layer {l} b"
+
+
+def _concat(xs, axis):
+    return torch.cat(xs, dim=axis).contiguous()
+
+
+def test_training_gain_and_fallback():
+    dns, les, delta, ubs, taus, feats = dataset()
+    ftr, ttr = _concat(feats[:4], 0), _concat(taus[:4], 1)
+    cl = eles.closure_create(batch=4096, lr=2e-3, seed=3)
+    l0 = eles.closure_train(cl, ftr, ttr, epochs=1)
+    l1 = eles.closure_train(cl, ftr, ttr, epochs=40)
+    assert l1 < 0.5 * l0
+    # held-out snapshot
+    n = feats[4].shape[0]
+    out = torch.empty((6, n), device="cuda")
+    eles.closure_infer(cl, feats[4], out)
+    exact = taus[4].double().cpu().numpy()
+    pred = out.double().cpu().numpy()
+    err_mlp = np.linalg.norm(pred - exact) / np.linalg.norm(exact)
+    gm = M.gradient_model(ubs[4].double().cpu().numpy(), les, delta).reshape(6, -1)
+    err_grad = np.linalg.norm(gm - exact) / np.linalg.norm(exact)
+    print(f"relative error: MLP {err_mlp:.3f}, gradient model {err_grad:.3f}, no model 1.000")
+    assert err_mlp < 0.5
+    # guard: a tiny threshold sends (almost) every point to the exact stress
+    cl2 = eles.closure_create(batch=4096, lr=2e-3, seed=3, guard_sigma=1e-3)
+    p, st = eles.closure_get_params(cl)
+    eles.closure_set_params(cl2, p, st)
+    out2 = torch.empty_like(out)
+    nfall = eles.closure_infer(cl2, feats[4], out2, exact_tau=taus[4])
+    assert nfall >= n - 100
+    fell = (out2 == taus[4]).all(dim=0)
+    assert int(fell.sum()) == nfall
+
+
+def test_checkpoint_resume_is_bitwise():
+    dns, les, delta, ubs, taus, feats = dataset()
+    ftr, ttr = _concat(feats[:2], 0), _concat(taus[:2], 1)
+    a = eles.closure_create(batch=2048, seed=11)
+    eles.closure_train(a, ftr, ttr, epochs=2)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        eles.closure_save(a, path)
+        eles.closure_train(a, ftr, ttr, epochs=2)
+        pa, _ = eles.closure_get_params(a)
+        b = eles.closure_create(batch=2048, seed=11)
+        eles.closure_load(b, path)
+        eles.closure_train(b, ftr, ttr, epochs=2)
+        pb, _ = eles.closure_get_params(b)
+        assert np.array_equal(pa, pb)
+        # a corrupted file is refused
+        raw = bytearray(open(path, "rb").read())
+        raw[100] ^= 0xFF
+        open(path, "wb").write(bytes(raw))
+        with pytest.raises(eles.EFError):
+            eles.closure_load(b, path)
