@@ -193,6 +193,32 @@ int ef_profile_enable(ef_plan *plan, int on);
 int ef_profile_read(ef_plan *plan, double *ms, long *calls);
 
 /* ------------------------------------------------------------------------
+ * Batches over several plans (different DNS grids, LES grids and filter
+ * widths): item i runs nsnap[i] snapshots of plans[i].  ef_batch_run replays
+ * every item's kernels as one CUDA graph on `stream` (captured on the first
+ * run and again whenever a field pointer changes).  A plan may appear in one
+ * batch only once (plans own their scratch); ef_batch_create reserves each
+ * plan's scratch for its item (allocates).  Fields as in
+ * ef_subfilter_stress_batch, one pointer per item.
+ * ---------------------------------------------------------------------- */
+typedef struct ef_batch ef_batch;
+int ef_batch_create(ef_plan *const *plans, const int *nsnap, int n, ef_batch **out);
+int ef_batch_run(ef_batch *batch, const void *const *u, void *const *ubar, void *const *tau, void *stream);
+void ef_batch_destroy(ef_batch *batch);
+
+/*
+ * ef_plan_autotune -- time the x-z kernel variants the plan supports (the
+ * unfused kernels; the fused kernel on CUDA cores or, for EF_PREC_BF16X3, on
+ * the tensor cores; 2, 4 or 8 columns per z phase) on one sample snapshot u
+ * (device, plan precision; ubar, tau are scratch outputs of one snapshot),
+ * keep the fastest, and report it as *choice = variant * 16 + columns
+ * (variant 0 unfused, 1 fused CUDA cores, 2 fused tensor cores) and its time.
+ * Synchronises the device.  ef_plan_set_variant applies a stored choice.
+ */
+int ef_plan_autotune(ef_plan *plan, const void *u, void *ubar, void *tau, int reps, int *choice, float *best_ms);
+int ef_plan_set_variant(ef_plan *plan, int choice);
+
+/* ------------------------------------------------------------------------
  * Learned closure.  The paper proposes using the exact stress computed from
  * DNS to inform subgrid models, e.g. by machine learning (Sec. 2.1 and the
  * summary, Sec. 5).  The library provides one such model: an MLP

@@ -230,6 +230,7 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
                 const int need = p->nlx - p->rx.dmin + p->bshift;
                 p->nblk_x = (need + SB - 1) / SB * SB;
                 if (tc) {
+                    p->tc_ok = true;
                     p->x_variant = 2;
                     tc_weights(p->rx, &p->tc);
                     p->tc.KS = KS;

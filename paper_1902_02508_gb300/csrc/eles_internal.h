@@ -120,6 +120,7 @@ struct ef_plan {
     int NQ = 1, ZQs = 0, P = 8;   // its z work split and columns per z phase
     int bshift = 0, nblk_x = 0;   // its x stream
     eles::FusedTCArgs tc;         // tensor-core B fragments (x_variant 2)
+    bool tc_ok = false;           // the tensor-core x-z kernel supports this plan
     uint4 *d_zfrag = nullptr;     // tensor-core z-phase A fragments
     // scratch owned by the plan, sized for `reserve` snapshots per launch
     int reserve = 0;

@@ -186,8 +186,8 @@ cudaError_t launch(const FusedArgs &a, int nsnap, cudaStream_t st)
 
 // Which (RX, DX, RZ, DZ) rings have a fused instantiation.
 #define ELES_FUSED_LIST(X) \
-    X(4, 4, 4, 6) X(4, 6, 4, 8) X(4, 6, 4, 11) X(4, 8, 4, 11) X(4, 11, 4, 16) \
-    X(6, 6, 6, 11) X(8, 6, 8, 8) X(8, 11, 8, 16)
+    X(4, 4, 4, 6) X(4, 4, 4, 8) X(4, 6, 4, 8) X(4, 6, 4, 11) X(4, 8, 4, 11) X(4, 11, 4, 16) \
+    X(6, 6, 6, 11) X(8, 4, 8, 8) X(8, 6, 8, 8) X(8, 11, 8, 16)
 
 bool fused_supported(int rx, int dx, int rz, int dz)
 {

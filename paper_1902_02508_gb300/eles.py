@@ -33,7 +33,8 @@ EXPORTED = ("ef_filter_setup", "ef_plan_destroy", "ef_filter_fields", "ef_subfil
             "ef_profile_read", "ef_last_error", "ef_version", "ef_closure_create", "ef_closure_destroy",
             "ef_closure_features", "ef_closure_fit_norm", "ef_closure_train", "ef_closure_infer",
             "ef_closure_gradients", "ef_closure_param_count", "ef_closure_get_params", "ef_closure_set_params",
-            "ef_closure_save", "ef_closure_load")
+            "ef_closure_save", "ef_closure_load", "ef_batch_create", "ef_batch_run", "ef_batch_destroy",
+            "ef_plan_autotune", "ef_plan_set_variant")
 
 
 class EFError(RuntimeError):
@@ -114,6 +115,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             lib.ef_closure_save.restype = i
             lib.ef_closure_load.argtypes = [vp, ctypes.c_char_p]
             lib.ef_closure_load.restype = i
+            lib.ef_batch_create.argtypes = [vp, vp, i, ctypes.POINTER(vp)]
+            lib.ef_batch_create.restype = i
+            lib.ef_batch_run.argtypes = [vp, vp, vp, vp, vp]
+            lib.ef_batch_run.restype = i
+            lib.ef_batch_destroy.argtypes = [vp]
+            lib.ef_batch_destroy.restype = None
+            lib.ef_plan_autotune.argtypes = [vp, vp, vp, vp, i, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float)]
+            lib.ef_plan_autotune.restype = i
+            lib.ef_plan_set_variant.argtypes = [vp, i]
+            lib.ef_plan_set_variant.restype = i
             lib.ef_last_error.restype = ctypes.c_char_p
             lib.ef_version.restype = ctypes.c_char_p
             _lib = lib
@@ -371,3 +382,58 @@ def closure_unpack(params):
         off += fo
         out.append((W, b))
     return out
+
+
+# ------------------------------------------------------------------ batches --
+class Batch:
+    """Owns an ef_batch*: items (plan, snapshots) replayed as one CUDA graph."""
+
+    def __init__(self, handle, plans, nsnap):
+        self.handle, self.plans, self.nsnap = handle, plans, nsnap
+
+    def close(self):
+        if self.handle:
+            load().ef_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_create(plans, nsnap) -> Batch:
+    hp = (ctypes.c_void_p * len(plans))(*[p.handle for p in plans])
+    ns = (ctypes.c_int * len(plans))(*nsnap)
+    h = ctypes.c_void_p()
+    _check(load().ef_batch_create(hp, ns, len(plans), ctypes.byref(h)))
+    return Batch(h, list(plans), list(nsnap))
+
+
+def batch_run(batch: Batch, us, ubars, taus, stream=None) -> None:
+    n = len(batch.plans)
+    for k, (p, ns) in enumerate(zip(batch.plans, batch.nsnap)):
+        d, l = p.dns, p.les
+        _field(us[k], (ns, 3, d.ny, d.nz, d.nx), p.dtype, f"u[{k}]")
+        _field(ubars[k], (ns, 3, l.ny, l.nz, l.nx), p.dtype, f"ubar[{k}]")
+        _field(taus[k], (ns, 6, l.ny, l.nz, l.nx), p.dtype, f"tau[{k}]")
+    pu = (ctypes.c_void_p * n)(*[t.data_ptr() for t in us])
+    pb = (ctypes.c_void_p * n)(*[t.data_ptr() for t in ubars])
+    pt = (ctypes.c_void_p * n)(*[t.data_ptr() for t in taus])
+    _check(load().ef_batch_run(batch.handle, pu, pb, pt, _stream(stream)))
+
+
+def plan_autotune(plan: Plan, u, ubar, tau, reps: int = 3):
+    """Returns (choice, ms): choice = variant * 16 + columns per z phase."""
+    d, l = plan.dns, plan.les
+    pu = _field(u, (3, d.ny, d.nz, d.nx), plan.dtype, "u")
+    pb = _field(ubar, (3, l.ny, l.nz, l.nx), plan.dtype, "ubar")
+    pt = _field(tau, (6, l.ny, l.nz, l.nx), plan.dtype, "tau")
+    ch, ms = ctypes.c_int(), ctypes.c_float()
+    _check(load().ef_plan_autotune(plan.handle, pu, pb, pt, int(reps), ctypes.byref(ch), ctypes.byref(ms)))
+    return ch.value, ms.value
+
+
+def plan_set_variant(plan: Plan, choice: int) -> None:
+    _check(load().ef_plan_set_variant(plan.handle, int(choice)))
