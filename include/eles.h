@@ -258,6 +258,21 @@ void ef_closure_destroy(ef_closure *closure);
 int ef_closure_features(const ef_grid *les, const float *ubar, double re_tau, int extension, float *feats,
                         void *stream);
 
+/*
+ * ef_closure_features_static -- the same features as ef_closure_features
+ * without allocating anything (no cudaMalloc, cudaMallocAsync or cudaFree),
+ * for callers that are not allowed to allocate device memory.  The paper has
+ * no counterpart; this is a deployment variant.  The LES y nodes go to a
+ * fixed device array of 4096 doubles (32 KB) that every device loading the
+ * library holds until exit; les->ny above 4096 is rejected with EF_ERR_ARG.
+ * The first call on a device looks up that array's address (make it before
+ * any stream capture).  All calls share the array: calls that overlap on the
+ * GPU race, so issue them on one stream.  Other arguments and errors as
+ * ef_closure_features.
+ */
+int ef_closure_features_static(const ef_grid *les, const float *ubar, double re_tau, int extension, float *feats,
+                               void *stream);
+
 /* Standardisation statistics from training data: feats device [N][10],
  * tau device [6][N] (component-major, the layout of ef_subfilter_stress). */
 int ef_closure_fit_norm(ef_closure *closure, const float *feats, const float *tau, long n, void *stream);

@@ -474,6 +474,51 @@ int ef_closure_features(const ef_grid *les, const float *ubar, double re_tau, in
     return EF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of ef_closure_features.  Its only scratch, the LES
+// y nodes on the device, lives in a fixed file-scope device array instead of
+// a per-call allocation, for callers that may not allocate device memory
+// (a host code that owns every allocation itself, or one running where the
+// allocator must not be called).  The array holds kStaticMaxNy nodes; every
+// device that loads the library keeps it until the process exits.  The
+// first call on a device looks up the array's device address (set-up; make
+// that first call before any stream capture).  All calls share the array:
+// calls that overlap on the GPU race and must be serialised by the caller.
+constexpr int kStaticMaxNy = 4096;
+static __device__ __align__(256) double g_static_y[kStaticMaxNy];
+
+int ef_closure_features_static(const ef_grid *les, const float *ubar, double re_tau, int extension, float *feats,
+                               void *stream)
+{
+    if (!les || !les->y || !ubar || !feats) { set_error("ef_closure_features_static: NULL argument"); return EF_ERR_ARG; }
+    if (les->nx < 2 || les->nz < 2 || les->ny < 3) { set_error("ef_closure_features_static: grid too small"); return EF_ERR_SHAPE; }
+    if (les->ny > kStaticMaxNy) {
+        set_error("ef_closure_features_static: ny = %d exceeds the static limit of %d nodes", les->ny, kStaticMaxNy);
+        return EF_ERR_ARG;
+    }
+    static double *addr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "ef_closure_features_static");
+    if (dev < 0 || dev >= 64) { set_error("ef_closure_features_static: device index %d unsupported", dev); return EF_ERR_ARG; }
+    if (!addr[dev]) {
+        double *p = nullptr;
+        e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_static_y);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+        addr[dev] = p;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    e = cudaMemcpyAsync(addr[dev], les->y, sizeof(double) * les->ny, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ef_closure_features_static");
+    const int flip = extension == EF_EXT_ODD_EVEN;
+    const long n = (long)les->nx * les->ny * les->nz;
+    features_kernel<<<grid1(n), 256, 0, s>>>(ubar, addr[dev], les->nx, les->ny, les->nz, les->Lx, les->Lz,
+                                             flip ? -1 : 1, flip ? 1 : -1, flip ? -1 : 1, re_tau, feats);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "features_kernel");
+    return EF_OK;
+}
+
 int ef_closure_fit_norm(ef_closure *c, const float *feats, const float *tau, long n, void *stream)
 {
     int rc = check_closure(c, "ef_closure_fit_norm");

@@ -34,7 +34,7 @@ EXPORTED = ("ef_filter_setup", "ef_plan_destroy", "ef_filter_fields", "ef_subfil
             "ef_closure_features", "ef_closure_fit_norm", "ef_closure_train", "ef_closure_infer",
             "ef_closure_gradients", "ef_closure_param_count", "ef_closure_get_params", "ef_closure_set_params",
             "ef_closure_save", "ef_closure_load", "ef_batch_create", "ef_batch_run", "ef_batch_destroy",
-            "ef_plan_autotune", "ef_plan_set_variant")
+            "ef_plan_autotune", "ef_plan_set_variant", "ef_closure_features_static")
 
 
 class EFError(RuntimeError):
@@ -97,6 +97,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             lib.ef_closure_destroy.restype = None
             lib.ef_closure_features.argtypes = [ctypes.POINTER(_Grid), vp, d, i, vp, vp]
             lib.ef_closure_features.restype = i
+            lib.ef_closure_features_static.argtypes = [ctypes.POINTER(_Grid), vp, d, i, vp, vp]
+            lib.ef_closure_features_static.restype = i
             lib.ef_closure_fit_norm.argtypes = [vp, vp, vp, L, vp]
             lib.ef_closure_fit_norm.restype = i
             lib.ef_closure_train.argtypes = [vp, vp, vp, L, i, vp, ctypes.POINTER(ctypes.c_float)]
@@ -296,6 +298,18 @@ def closure_features(les, ubar, feats, re_tau: float = 180.0, extension: int = E
     pb = _field(ubar, (3, les.ny, les.nz, les.nx), torch.float32, "ubar")
     pf = _field(feats, (n, 10), torch.float32, "feats")
     _check(load().ef_closure_features(ctypes.byref(g), pb, float(re_tau), int(extension), pf, _stream(stream)))
+
+
+def closure_features_static(les, ubar, feats, re_tau: float = 180.0, extension: int = EXT_EVEN_ODD,
+                            stream=None):
+    """ef_closure_features without any device allocation (static scratch)."""
+    import torch
+    g, y = _grid(les)
+    n = les.nx * les.ny * les.nz
+    pb = _field(ubar, (3, les.ny, les.nz, les.nx), torch.float32, "ubar")
+    pf = _field(feats, (n, 10), torch.float32, "feats")
+    _check(load().ef_closure_features_static(ctypes.byref(g), pb, float(re_tau), int(extension), pf,
+                                             _stream(stream)))
 
 
 def _n_feats(feats):
