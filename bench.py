@@ -179,18 +179,27 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------- ours ----
-def traffic_from_profile(kernel_tag):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source."""
+KERNEL_SOURCES = ("fused_stage.cuh", "fused_kernels.cu", "tc_kernels.cu", "eles_internal.h")
+
+
+def kernel_source_hash():
     import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1902_02508_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(kernel_tag, points_per_launch):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; scaled from the captured launch's points to
+    this launch's points (the traffic is proportional to the points read)."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.json")
-    src = os.path.join(ROOT, "paper_1902_02508_gb300", "csrc", "filter_kernels.cu")
     try:
         prof = json.load(open(path))
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if prof.get("source_sha256_16") == h:
-            return prof.get("dram_bytes_per_launch")
-    except (OSError, ValueError):
+        if prof.get("source_sha256_16") == kernel_source_hash():
+            return prof["dram_bytes_per_point"] * points_per_launch
+    except (OSError, ValueError, KeyError):
         pass
     return None
 
@@ -328,7 +337,8 @@ def main():
             "kernel": "xz_fused (x and z contractions + reference profile, reads the input once)" if fused
             else "x and z contractions (unfused)",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_source": peak_src, "traffic": traffic_from_profile(f"xz_fused_{args.workload}_{args.precision}"),
+            "peak_source": peak_src,
+            "traffic": traffic_from_profile(f"xz_fused_{args.workload}_{args.precision}", dns.npts * ns),
             "algorithmic_bytes_per_launch": alg_bytes,
             "phase_ms_per_step": {"xz": xz_ms, "y_recovery": phase_ms[2] / max(calls, 1)},
             "path_frac": (value / world) * (alg_bytes / (dns.npts * ns)) / 1e9 / peak}
