@@ -166,8 +166,9 @@ int ef_check_device_error(ef_plan *plan, void *stream);
 /* Plan facts for callers and tests.  ints: 0 nx, 1 ny, 2 nz, 3 nlx, 4 nly,
  * 5 nlz, 6 precision, 7 x-taps per row, 8 z-taps per row, 9 max y-taps per
  * row, 10 x-contraction variant (0 generic, 1 banded ring on CUDA cores,
- * 2 tensor cores), 11 x and z fused in one kernel (0/1), 12 reserved
- * snapshots.  Returns EF_ERR_ARG for an unknown index. */
+ * 2 tensor cores, 3 tensor cores with warp-specialised producer, x and z
+ * roles), 11 x and z fused in one kernel (0/1), 12 reserved snapshots.
+ * Returns EF_ERR_ARG for an unknown index. */
 int ef_plan_info(const ef_plan *plan, int what, long *value);
 
 /*
@@ -212,8 +213,11 @@ void ef_batch_destroy(ef_batch *batch);
  * the tensor cores; 2, 4 or 8 columns per z phase) on one sample snapshot u
  * (device, plan precision; ubar, tau are scratch outputs of one snapshot),
  * keep the fastest, and report it as *choice = variant * 16 + columns
- * (variant 0 unfused, 1 fused CUDA cores, 2 fused tensor cores) and its time.
- * Synchronises the device.  ef_plan_set_variant applies a stored choice.
+ * (variant 0 unfused, 1 fused CUDA cores, 2 fused tensor cores, 3 fused
+ * tensor cores warp-specialised, which always parks two columns and ignores
+ * the column count) and its time.  Synchronises the device.
+ * ef_plan_set_variant applies a stored choice (EF_ERR_UNSUPPORTED if the
+ * plan cannot run that variant).
  */
 int ef_plan_autotune(ef_plan *plan, const void *u, void *ubar, void *tau, int reps, int *choice, float *best_ms);
 int ef_plan_set_variant(ef_plan *plan, int choice);

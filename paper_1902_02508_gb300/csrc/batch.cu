@@ -110,7 +110,8 @@ int ef_batch_run(ef_batch *b, const void *const *u, void *const *ubar, void *con
 // Try the x-z variants the plan supports and keep the fastest.  u: one
 // sample snapshot on the device in the plan's precision; ubar/tau scratch
 // outputs.  *choice receives the variant (0 unfused, 1 fused CUDA cores,
-// 2 fused tensor cores) * 16 + P.  Synchronises the device.
+// 2 fused tensor cores, 3 fused tensor cores, warp-specialised) * 16 + P.
+// Synchronises the device.
 int ef_plan_autotune(ef_plan *p, const void *u, void *ubar, void *tau, int reps, int *choice, float *best_ms)
 {
     if (!p || !u || !ubar || !tau) { set_error("ef_plan_autotune: NULL argument"); return EF_ERR_ARG; }
@@ -119,7 +120,8 @@ int ef_plan_autotune(ef_plan *p, const void *u, void *ubar, void *tau, int reps,
     std::vector<Cand> cands;
     const Cand orig = {p->fused, p->x_variant, p->P};
     cands.push_back({false, p->rx.ok ? 1 : 0, p->P});
-    if (orig.fused)
+    if (orig.fused) {
+        if (p->tcws_ok) cands.push_back({true, 3, p->P});
         for (int xv = 1; xv <= 2; xv++) {
             if (xv == 2 && !p->tc_ok) continue;
             if (xv == 1 && !fused_supported(p->rx.r, p->rx.D, p->rz.r, p->rz.D)) continue;
@@ -128,6 +130,7 @@ int ef_plan_autotune(ef_plan *p, const void *u, void *ubar, void *tau, int reps,
                 if (need <= 222 * 1024) cands.push_back({true, xv, P});
             }
         }
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -176,7 +179,7 @@ int ef_plan_autotune(ef_plan *p, const void *u, void *ubar, void *tau, int reps,
         p->ZQs = p->nlz / NQ;
     }
     if (rc) return rc;
-    if (choice) *choice = (win.fused ? (win.xv == 2 ? 2 : 1) : 0) * 16 + win.P;
+    if (choice) *choice = (win.fused ? win.xv : 0) * 16 + win.P;
     if (best_ms) *best_ms = best;
     return EF_OK;
 }
@@ -197,6 +200,13 @@ int ef_plan_set_variant(ef_plan *p, int choice)
         p->x_variant = p->rx.ok ? 1 : 0;
         return EF_OK;
     }
+    if (v == 3) {
+        if (!p->tcws_ok) { set_error("ef_plan_set_variant: warp-specialised kernel unavailable"); return EF_ERR_UNSUPPORTED; }
+        p->fused = true;
+        p->x_variant = 3;
+        return EF_OK;
+    }
+    if (v > 3) { set_error("ef_plan_set_variant: unknown variant %d", v); return EF_ERR_ARG; }
     if (v == 2 && !p->tc_ok) { set_error("ef_plan_set_variant: tensor cores unavailable"); return EF_ERR_UNSUPPORTED; }
     if (v == 1 && !fused_supported(p->rx.r, p->rx.D, p->rz.r, p->rz.D)) { set_error("ef_plan_set_variant: fused kernel unavailable"); return EF_ERR_UNSUPPORTED; }
     const size_t need = v == 2 ? tc_smem_bytes(P, p->nz, p->tc.KS) : fused_smem_bytes(p->rx.r, P, p->nz);

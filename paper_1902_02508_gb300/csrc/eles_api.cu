@@ -212,7 +212,7 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
             const int SB = fused_stage_blocks(p->rx.r);
             std::vector<unsigned> zf;
             int zoff = 0;
-            const int KS = tc ? tc_zfrags(p->rz, p->nlz, zf, &zoff) : 0;
+            const int KS = tc ? tc_zfrags(p->rz, p->nlz, zf, &zoff, false) : 0;
             auto smem = [&](int P) {
                 return tc ? tc_smem_bytes(P, p->nz, KS) : fused_smem_bytes(p->rx.r, P, p->nz);
             };
@@ -236,10 +236,26 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
                     p->tc.KS = KS;
                     p->tc.zoff = zoff;
                     if (KS > 0) {
+                        // z-phase A fragments, the rotated x B fragments, the z-phase A
+                        // fragments in pair order
+                        std::vector<unsigned> bv, zfp;
+                        tc_bvar(p->rx, bv);
+                        int zoff2 = 0;
+                        tc_zfrags(p->rz, p->nlz, zfp, &zoff2, true);
+                        const size_t nz4 = zf.size() / 4;
+                        zf.insert(zf.end(), bv.begin(), bv.end());
+                        zf.insert(zf.end(), zfp.begin(), zfp.end());
                         CK(cudaMalloc(&p->d_zfrag, sizeof(unsigned) * zf.size()), "cudaMalloc z fragments");
                         CK(cudaMemcpy(p->d_zfrag, zf.data(), sizeof(unsigned) * zf.size(), cudaMemcpyHostToDevice),
                            "copy z fragments");
                         p->tc.afrag = p->d_zfrag;
+                        p->tc.bvar = p->d_zfrag + nz4;
+                        p->tc.afrag_ws = p->d_zfrag + nz4 + bv.size() / 4;
+                        if (tcws_supported(p->rx.r, p->rx.D, p->rz.r, p->nlz, p->nz) && 2 * zoff <= p->nz &&
+                            tcws_smem_bytes(p->nz, KS) <= 227 * 1024 - 1024) {
+                            p->tcws_ok = true;
+                            p->x_variant = 3;
+                        }
                     }
                 }
             }

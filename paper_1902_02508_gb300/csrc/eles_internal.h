@@ -63,14 +63,21 @@ struct FusedTCArgs {
     unsigned Bl[64];
     int KS = 0, zoff = 0;          // tensor-core z phase: k-steps per Z tile, window offset (KS 0: CUDA cores)
     const uint4 *afrag = nullptr;  // its A fragments [KS][32][hi, lo] (device)
+    const uint4 *bvar = nullptr;   // rotated x-operator B fragments [4][32] (device; x_variant 3)
+    const uint4 *afrag_ws = nullptr;   // z A fragments in the pre-split pair order (device; x_variant 3)
 };
 bool tc_supported(int rx, int dx, int rz, int dz, int nlz);
 void tc_weights(const Ring &rx, FusedTCArgs *ta);
 size_t tc_smem_bytes(int P, int nz, int KS);
 // Encode the TMA view of a batch of snapshots u [S][3][ny][nz][nx] (host).
-int encode_u_map(const float *u, int nx, int ny, int nz, int nsnap, int box_rows, CUtensorMap *map);
+int encode_u_map(const float *u, int nx, int ny, int nz, int nsnap, int box_w, int box_rows, CUtensorMap *map);
+constexpr int kTcwsStageWidth = 16;   // floats per row of a warp-specialised kernel stage
 cudaError_t launch_fused_tc(int rz, int dz, const FusedTCArgs &ta, int nsnap, cudaStream_t st);
-int tc_zfrags(const Ring &rz, int nlz, std::vector<unsigned> &out, int *zoff_out);
+int tc_zfrags(const Ring &rz, int nlz, std::vector<unsigned> &out, int *zoff_out, bool pairperm);
+bool tcws_supported(int rx, int dx, int rz, int nlz, int nz);
+size_t tcws_smem_bytes(int nz, int KS);
+void tc_bvar(const Ring &rx, std::vector<unsigned> &out);
+cudaError_t launch_tcws(const FusedTCArgs &ta, int nsnap, cudaStream_t st);
 
 bool fused_supported(int rx, int dx, int rz, int dz);
 int fused_stage_blocks(int rx);
@@ -109,7 +116,8 @@ struct ef_plan {
     int par[3] = {1, -1, 1};      // wall parity of u1, u2, u3 (Eq. 7 or Eq. 9)
     eles::Band bx, bz;            // x and z operators
     eles::Ring rx, rz;            // their strided-convolution tables (if ok)
-    int x_variant = 0;            // 0 generic gather, 1 ring (CUDA cores), 2 tensor cores
+    int x_variant = 0;            // 0 generic gather, 1 ring (CUDA cores), 2 tensor cores,
+                                  // 3 tensor cores, warp-specialised
     // y operators, dense [nly][ny] rows with a nonzero range per row
     int *d_ystart = nullptr, *d_ycount = nullptr;
     double *d_yw64[2] = {nullptr, nullptr};   // [0] even, [1] odd
@@ -121,6 +129,7 @@ struct ef_plan {
     int bshift = 0, nblk_x = 0;   // its x stream
     eles::FusedTCArgs tc;         // tensor-core B fragments (x_variant 2)
     bool tc_ok = false;           // the tensor-core x-z kernel supports this plan
+    bool tcws_ok = false;         // so does its warp-specialised form
     uint4 *d_zfrag = nullptr;     // tensor-core z-phase A fragments
     // scratch owned by the plan, sized for `reserve` snapshots per launch
     int reserve = 0;

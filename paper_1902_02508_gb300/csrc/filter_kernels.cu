@@ -453,14 +453,15 @@ int run_group(ef_plan *p, int ns, const T *u, T *ubar, T *tau, double *plane_mea
             while ((1 << a.lP) < a.P) a.lP++;
             for (int i = 0; i < p->rx.r * p->rx.D; i++) a.WX[i] = p->rx.W32[i];
             for (int i = 0; i < p->rz.r * p->rz.D; i++) a.WZ[i] = p->rz.W32[i];
-            if (p->x_variant == 2) {
+            if (p->x_variant >= 2) {
                 FusedTCArgs ta = p->tc;
                 a.box_rows = p->nz > 256 ? p->nz / 2 : p->nz;
                 a.use_tma = 1;
-                int rc = encode_u_map(u, p->nx, p->ny, p->nz, ns, a.box_rows, &a.tmap);
+                int rc = encode_u_map(u, p->nx, p->ny, p->nz, ns, p->x_variant == 3 ? kTcwsStageWidth : 8,
+                                      a.box_rows, &a.tmap);
                 if (rc) return rc;
                 ta.f = a;     // KS, zoff, afrag and the B fragments come from the plan
-                e = launch_fused_tc(p->rz.r, p->rz.D, ta, ns, s);
+                e = p->x_variant == 3 ? launch_tcws(ta, ns, s) : launch_fused_tc(p->rz.r, p->rz.D, ta, ns, s);
             } else {
                 e = launch_fused(p->rx.r, p->rx.D, p->rz.r, p->rz.D, a, ns, s);
             }

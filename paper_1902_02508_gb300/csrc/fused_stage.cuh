@@ -148,7 +148,9 @@ namespace fz {
 
 constexpr int TW = 8;            // floats per row per stage
 constexpr int TSTG = 4;          // stages in flight
-constexpr long kWaitLimit = 1L << 20;
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at the SM clock: the bound of one wait
+constexpr unsigned kSuspendNs = 100000;              // suspend-time hint of one try_wait (the thread
+                                                     // wakes as soon as the phase completes)
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -165,16 +167,18 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
 {
     unsigned ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
                  : "=r"(ok)
-                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
                  : "memory");
     return ok != 0;
 }
-// Bounded wait; returns false (and flags the plan) if the copy never landed.
+// Bounded wait; returns false (and flags the plan) if the phase never completed.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *err)
 {
-    for (long i = 0; i < kWaitLimit; i++)
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (clock64() - t0 < kWaitCycles)
         if (mbar_try_wait(bar, parity)) return true;
     if (err) atomicCAS(err, 0, (int)EF_ERR_TIMEOUT);
     return false;

@@ -80,7 +80,7 @@ def test_autotune_choices_all_meet_tolerance(tmp_path):
     assert not res["cached"] and res["ms"] > 0
     again = autotune.tune(plan, ud, ub, tau, cache_path=str(tmp_path / "tune.json"))
     assert again["cached"] and again["choice"] == res["choice"]
-    for choice in (0 * 16 + 8, 1 * 16 + 4, 2 * 16 + 2, 2 * 16 + 8, res["choice"]):
+    for choice in (0 * 16 + 8, 1 * 16 + 4, 2 * 16 + 2, 2 * 16 + 8, 3 * 16 + 2, res["choice"]):
         eles.plan_set_variant(plan, choice)
         eles.subfilter_stress(plan, ud, ub, tau)
         torch.cuda.synchronize()

@@ -67,6 +67,9 @@ CASES = {
     "interp": (30, 25, 20, 2 * math.pi, math.pi, 9, 8, 6, 0.5),
     # stride 8 in x and z with a short x ring: the tensor-core x-contraction
     "tc": (128, 65, 128, 2 * math.pi, math.pi, 16, 17, 16, 12 * math.pi / 128),
+    # stride 8, 8 x warps, odd first output of the x stream, 24 outputs per row
+    # (not a multiple of the four B rotations): warp-specialised tensor-core kernel
+    "tc2": (192, 33, 256, 2 * math.pi, math.pi, 24, 17, 32, 10 * math.pi / 192),
 }
 
 
@@ -141,7 +144,7 @@ def test_full_size_sampled_points(dfrac, prec):
     delta = dns.Lx / dfrac
     plan, (ub, tau) = run_gpu(dns, les, delta, u, prec)
     if prec == eles.PREC_BF16X3:
-        assert eles.plan_info(plan, 10) == 2          # tensor-core x-contraction
+        assert eles.plan_info(plan, 10) == 3          # warp-specialised tensor-core x-z kernel
     rng = np.random.default_rng(3)
     pts = np.stack([rng.integers(0, les.nx, 12), rng.integers(0, les.ny, 12),
                     rng.integers(0, les.nz, 12)], axis=1)
@@ -234,9 +237,38 @@ def test_fused_path_is_used_for_channel_shapes():
 def test_tensor_core_variant_selected():
     dns, les, delta, _ = case("tc")
     plan = eles.filter_setup(dns, les, delta, precision=eles.PREC_BF16X3)
-    assert eles.plan_info(plan, 10) == 2 and eles.plan_info(plan, 11) == 1
+    assert eles.plan_info(plan, 10) == 3 and eles.plan_info(plan, 11) == 1
     plan32 = eles.filter_setup(dns, les, delta, precision=eles.PREC_FP32)
     assert eles.plan_info(plan32, 10) == 1
+    with pytest.raises(eles.EFError):
+        eles.plan_set_variant(plan32, 3 * 16 + 2)     # no tensor cores for an FP32 plan
+
+
+@pytest.mark.parametrize("name", ["tc", "tc2"])
+@pytest.mark.parametrize("variant", [2, 3])
+def test_tensor_core_variants_match_oracle(name, variant):
+    """Both tensor-core x-z kernels (slide and warp-specialised), with and
+    without plane means, against the oracle; the plane means against the
+    FP64 mean of the field."""
+    dns, les, delta, u = case(name, seed=31)
+    ub_ref, tau_ref = O.subfilter_stress(dns, les, delta, u)
+    plan = eles.filter_setup(dns, les, delta, precision=eles.PREC_BF16X3)
+    eles.plan_set_variant(plan, variant * 16 + 2)
+    assert eles.plan_info(plan, 10) == variant
+    dev = torch.device("cuda")
+    ud = torch.from_numpy(u).to(dev, torch.float32)
+    for with_mean in (False, True):
+        ub = torch.full((3, les.ny, les.nz, les.nx), float("nan"), device=dev)
+        tau = torch.full((6, les.ny, les.nz, les.nx), float("nan"), device=dev)
+        pm = torch.zeros((3, dns.ny), device=dev, dtype=torch.float64) if with_mean else None
+        eles.subfilter_stress(plan, ud, ub, tau, pm)
+        torch.cuda.synchronize()
+        assert eles.check_device_error(plan) == 0
+        assert_close(ub.double().cpu().numpy(), ub_ref, TOL32, "ubar")
+        assert_close(tau.double().cpu().numpy(), tau_ref, TOL32, "tau")
+        if with_mean:
+            ref = u.mean(axis=(2, 3))
+            assert np.abs(pm.cpu().numpy() - ref).max() <= 1e-5
 
 
 def test_repeat_calls_are_bitwise_stable():
