@@ -98,8 +98,11 @@ int plan_reserve(ef_plan *p, int nsnap)
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "reserve");
     cudaFree(p->d_g); cudaFree(p->d_h); cudaFree(p->d_uref); cudaFree(p->d_urefT); cudaFree(p->d_rowsum);
-    cudaFree(p->d_AU); cudaFree(p->d_AUU); cudaFree(p->d_wy); cudaFree(p->d_ytmp);
+    cudaFree(p->d_AU); cudaFree(p->d_AUU); cudaFree(p->d_wy); cudaFree(p->d_ytmp); cudaFree(p->d_yfrag);
+    cudaFree(p->d_Kab);
+    p->d_Kab = nullptr;
     p->d_g = p->d_h = p->d_urefT = p->d_wy = p->d_ytmp = nullptr;
+    p->d_yfrag = nullptr;
     p->d_uref = p->d_rowsum = p->d_AU = p->d_AUU = nullptr;
     p->reserve = 0;
     const size_t es = (p->prec == EF_PREC_FP64) ? sizeof(double) : sizeof(float);
@@ -112,8 +115,10 @@ int plan_reserve(ef_plan *p, int nsnap)
         {(void **)&p->d_rowsum, sizeof(double) * 3 * (size_t)p->ny * p->nzw},
         {(void **)&p->d_AU, sizeof(double) * 3 * S * p->nly},
         {(void **)&p->d_AUU, sizeof(double) * 6 * S * p->nly},
+        {(void **)&p->d_Kab, sizeof(float) * 6 * S * p->nly},
         {&p->d_wy, es * 8 * S * p->nly * p->ny},
-        {&p->d_ytmp, es * 12 * S * p->nly * p->nlz * p->nlx},
+        {&p->d_ytmp, es * kYTmp * S * p->nly * p->nlz * p->nlx},
+        {(void **)&p->d_yfrag, p->ytc_ok ? sizeof(uint4) * kYOps * 64 * S * p->ytc.kstot : 0},
     };
     for (auto &r : req) {
         if (!r.bytes) continue;
@@ -153,8 +158,10 @@ void ef_plan_destroy(ef_plan *p)
     cudaFree(p->d_rowsum);
     cudaFree(p->d_AU);
     cudaFree(p->d_AUU);
+    cudaFree(p->d_Kab);
     cudaFree(p->d_wy);
     cudaFree(p->d_ytmp);
+    cudaFree(p->d_yfrag);
     cudaFree(p->d_zfrag);
     cudaFree(p->d_err);
     for (int t = 0; t < ef_plan::kProfSlots; t++)

@@ -99,10 +99,41 @@ struct YArgs {
     int *err;
 };
 
+// Tensor-core y passes for EF_PREC_BF16X3 (ypass_tc.cu): the banded y
+// operators as split-BF16 A fragments per 16-row LES tile and 16-row k-step,
+// h of a field triple staged in shared memory by TMA.
+constexpr int kYMaxTiles = 32;     // LES row tiles of 16 (nly <= 512)
+constexpr int kYOps = 9;           // y operators per snapshot (A+, A-, A- - A+, six deviation-folded)
+constexpr int kYTmp = 21;          // scratch slots: q_a, C'_ab, d_a, q_11 .. q_33
+struct YTcGeom {
+    int nmt = 0;                   // LES row tiles
+    int jb[kYMaxTiles] = {};       // first DNS row of tile mt's band
+    int ks[kYMaxTiles] = {};       // its 16-row k-steps
+    int koff[kYMaxTiles] = {};     // their offset in the fragment table
+    int kstot = 0;                 // k-steps of all tiles
+    int box_rows = 0;              // TMA box rows (two boxes stage the band rows of every tile)
+};
+struct YTcArgs {
+    CUtensorMap hmap;              // TMA view of h: {nplane, 9 ny S} floats, box {36, box_rows}
+    YTcGeom geo;
+    const uint4 *frag;             // [S][kYOps][kstot][hi, lo][32 lanes]
+    const double *AU;              // [S][3][nly]
+    const float *Kab;              // [S][6][nly]: A_y(U_a U_b) - A_y U_a A_y U_b
+    float *ubar, *tau;             // [S][3][nly][nplane], [S][6][nly][nplane]
+    float *tmp;                    // [S][kYTmp][nly][nplane]
+    int ny, nly, nplane, stress, flip;
+    int *err;
+};
+bool ytc_geometry(const std::vector<int> &ystart, const std::vector<int> &ycount, int ny, int nplane, YTcGeom *g);
+cudaError_t launch_yfrag(const YTcGeom &g, const double *yw_even, const double *yw_odd, const double *uref,
+                         const double *AU, int ny, int nly, int nsnap, uint4 *frag, cudaStream_t st);
+int encode_h_map(const float *h, int nplane, int ny, int nsnap, int box_rows, CUtensorMap *map);
+cudaError_t launch_ytc(const YTcArgs &a, int nsnap, cudaStream_t st);
+
 template <typename T>
 cudaError_t launch_yprofile(const double *uref, const int *ystart, const int *ycount, const double *we,
                             const double *wo, int ny, int nly, int flip, int nsnap, double *AU, double *AUU,
-                            T *wy, cudaStream_t st);
+                            T *wy, float *Kab, cudaStream_t st);
 template <typename T>
 cudaError_t launch_ypass(const YArgs<T> &a, int nsnap, cudaStream_t st);
 
@@ -123,6 +154,9 @@ struct ef_plan {
     double *d_yw64[2] = {nullptr, nullptr};   // [0] even, [1] odd
     float *d_yw32[2] = {nullptr, nullptr};
     int ytaps_max = 0;
+    bool ytc_ok = false;          // tensor-core y passes (EF_PREC_BF16X3)
+    eles::YTcGeom ytc;            // their banded tiling
+    uint4 *d_yfrag = nullptr;     // their A fragments, [S][kYOps][kstot][2][32]
     double *d_ygrid = nullptr;    // DNS y nodes on the device
     bool fused = false;           // FP32 fused x-z kernel available for this plan
     int NQ = 1, ZQs = 0, P = 8;   // its z work split and columns per z phase
@@ -141,8 +175,9 @@ struct ef_plan {
     int nzw = 0;
     double *d_AU = nullptr;       // A_y U_c, [S][3][nly]
     double *d_AUU = nullptr;      // A_y (U_a U_b), [S][6][nly]
+    float *d_Kab = nullptr;       // A_y (U_a U_b) - A_y U_a A_y U_b, [S][6][nly]
     void *d_wy = nullptr;         // y weights with U folded in, [S][nly][ny][8]
-    void *d_ytmp = nullptr;       // q_a, C_ab between the y passes, [S][12][nly][nlz][nlx]
+    void *d_ytmp = nullptr;       // partial sums between the y passes, [S][kYTmp][nly][nlz][nlx]
     int *d_err = nullptr;         // device error word
     // phase timing (ef_profile_enable)
     bool prof_on = false;

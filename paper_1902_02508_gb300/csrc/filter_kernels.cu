@@ -477,8 +477,31 @@ int run_group(ef_plan *p, int ns, const T *u, T *ubar, T *tau, double *plane_mea
     prof_mark(pe, 2, s);
     T *wy = static_cast<T *>(p->d_wy);
     e = launch_yprofile<T>(p->d_uref, p->d_ystart, p->d_ycount, p->d_yw64[0], p->d_yw64[1], p->ny, p->nly,
-                           p->ext == EF_EXT_ODD_EVEN, ns, p->d_AU, p->d_AUU, wy, s);
+                           p->ext == EF_EXT_ODD_EVEN, ns, p->d_AU, p->d_AUU, wy, p->d_Kab, s);
     if (e != cudaSuccess) return cuda_fail(e, "yprofile launch");
+    if constexpr (sizeof(T) == 4) {
+        if (p->ytc_ok) {   // tensor-core y passes (EF_PREC_BF16X3)
+            YTcArgs yt;
+            memset(&yt, 0, sizeof yt);
+            yt.geo = p->ytc;
+            const int nplane = p->nlz * p->nlx;
+            int rc = encode_h_map(h, nplane, p->ny, ns, p->ytc.box_rows, &yt.hmap);
+            if (rc) return rc;
+            e = launch_yfrag(p->ytc, p->d_yw64[0], p->d_yw64[1], p->d_uref, p->d_AU, p->ny, p->nly, ns, p->d_yfrag, s);
+            if (e != cudaSuccess) return cuda_fail(e, "yfrag launch");
+            yt.frag = p->d_yfrag; yt.AU = p->d_AU; yt.Kab = p->d_Kab;
+            yt.ubar = ubar; yt.tau = tau; yt.tmp = static_cast<float *>(p->d_ytmp);
+            yt.ny = p->ny; yt.nly = p->nly; yt.nplane = nplane;
+            yt.stress = stress ? 1 : 0; yt.flip = p->ext == EF_EXT_ODD_EVEN; yt.err = p->d_err;
+            e = launch_ytc(yt, ns, s);
+            if (e != cudaSuccess) return cuda_fail(e, "ytc launch");
+            prof_mark(pe, 3, s);
+            prof_mark(pe, 4, s);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(e, "filter launch");
+            return EF_OK;
+        }
+    }
     YArgs<T> y;
     y.h = h; y.wy = wy; y.AU = p->d_AU; y.AUU = p->d_AUU; y.ystart = p->d_ystart; y.ycount = p->d_ycount;
     y.ubar = ubar; y.tau = tau; y.tmp = static_cast<T *>(p->d_ytmp); y.ny = p->ny; y.nly = p->nly; y.nlz = p->nlz; y.nlx = p->nlx;

@@ -24,7 +24,7 @@ template <typename T>
 __global__ void __launch_bounds__(YPT) yprofile_kernel(const double *__restrict__ uref, const int *__restrict__ ystart,
                                                        const int *__restrict__ ycount, const double *__restrict__ we,
                                                        const double *__restrict__ wo, int ny, int nly, int flip,
-                                                       double *AU, double *AUU, T *wy)
+                                                       double *AU, double *AUU, T *wy, float *Kab)
 {
     const int J = blockIdx.x, s = blockIdx.y;
     const int pv[3] = {flip ? -1 : 1, flip ? 1 : -1, flip ? -1 : 1};
@@ -50,12 +50,21 @@ __global__ void __launch_bounds__(YPT) yprofile_kernel(const double *__restrict_
         if ((threadIdx.x & 31) == 0) part[k][threadIdx.x >> 5] = v;
     }
     __syncthreads();
+    __shared__ double tot[9];
     if (threadIdx.x < 9) {
         const int k = threadIdx.x;
         double v = 0.0;
         for (int w = 0; w < YPT / 32; w++) v += part[k][w];
+        tot[k] = v;
         if (k < 3) AU[((size_t)s * 3 + k) * nly + J] = v;
         else AUU[((size_t)s * 6 + (k - 3)) * nly + J] = v;
+    }
+    // the profile bracket of T_ab, A_y(U_a U_b) - A_y U_a A_y U_b: cancels
+    // ~U^2 to O(1), so it is formed here in FP64 (once per row)
+    __syncthreads();
+    if (Kab && threadIdx.x >= 3 && threadIdx.x < 9) {
+        const int k = threadIdx.x - 3;
+        Kab[((size_t)s * 6 + k) * nly + J] = (float)(tot[3 + k] - tot[PI[k]] * tot[PJ[k]]);
     }
 }
 
@@ -208,9 +217,10 @@ __global__ void __launch_bounds__(YT) ypass_kernel(const __grid_constant__ YArgs
 template <typename T>
 cudaError_t launch_yprofile(const double *uref, const int *ystart, const int *ycount, const double *we,
                             const double *wo, int ny, int nly, int flip, int nsnap, double *AU, double *AUU,
-                            T *wy, cudaStream_t st)
+                            T *wy, float *Kab, cudaStream_t st)
 {
-    yprofile_kernel<T><<<dim3(nly, nsnap), YPT, 0, st>>>(uref, ystart, ycount, we, wo, ny, nly, flip, AU, AUU, wy);
+    yprofile_kernel<T><<<dim3(nly, nsnap), YPT, 0, st>>>(uref, ystart, ycount, we, wo, ny, nly, flip, AU, AUU, wy,
+                                                         Kab);
     return cudaGetLastError();
 }
 
@@ -242,10 +252,10 @@ cudaError_t launch_ypass(const YArgs<T> &a, int nsnap, cudaStream_t st)
 
 template cudaError_t launch_yprofile<float>(const double *, const int *, const int *, const double *,
                                             const double *, int, int, int, int, double *, double *, float *,
-                                            cudaStream_t);
+                                            float *, cudaStream_t);
 template cudaError_t launch_yprofile<double>(const double *, const int *, const int *, const double *,
                                              const double *, int, int, int, int, double *, double *, double *,
-                                             cudaStream_t);
+                                             float *, cudaStream_t);
 template cudaError_t launch_ypass<float>(const YArgs<float> &, int, cudaStream_t);
 template cudaError_t launch_ypass<double>(const YArgs<double> &, int, cudaStream_t);
 
