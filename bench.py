@@ -179,7 +179,7 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------- ours ----
-KERNEL_SOURCES = ("fused_stage.cuh", "fused_kernels.cu", "tc_kernels.cu", "eles_internal.h")
+KERNEL_SOURCES = ("fused_stage.cuh", "tc_kernels.cu", "eles_internal.h")
 
 
 def kernel_source_hash():
@@ -342,7 +342,10 @@ def main():
             "algorithmic_bytes_per_launch": alg_bytes,
             "phase_ms_per_step": {"xz": xz_ms, "y_recovery": phase_ms[2] / max(calls, 1)},
             "path_frac": (value / world) * (alg_bytes / (dns.npts * ns)) / 1e9 / peak}
-    per_call_launches = 3 if fused else 2 + 5 * ns
+    # x-z: one fused launch (or 5 per snapshot + 2 unfused); y: profile, then
+    # fragments + velocities + products + recovery (tensor cores) or 2 passes
+    ytc = eles.plan_info(plan, 13) == 1
+    per_call_launches = (1 if fused else 2 + 5 * ns) + 1 + (4 if ytc else 2)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

@@ -167,7 +167,8 @@ int ef_check_device_error(ef_plan *plan, void *stream);
  * 5 nlz, 6 precision, 7 x-taps per row, 8 z-taps per row, 9 max y-taps per
  * row, 10 x-contraction variant (0 generic, 1 banded ring on CUDA cores,
  * 2 tensor cores, 3 tensor cores with warp-specialised producer, x and z
- * roles), 11 x and z fused in one kernel (0/1), 12 reserved snapshots.
+ * roles), 11 x and z fused in one kernel (0/1), 12 reserved snapshots,
+ * 13 y-contraction variant (0 CUDA cores, 1 tensor cores, EF_PREC_BF16X3).
  * Returns EF_ERR_ARG for an unknown index. */
 int ef_plan_info(const ef_plan *plan, int what, long *value);
 

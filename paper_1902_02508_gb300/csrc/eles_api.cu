@@ -382,6 +382,7 @@ int ef_plan_info(const ef_plan *p, int what, long *value)
     case 10: *value = p->x_variant; break;
     case 11: *value = p->fused ? 1 : 0; break;
     case 12: *value = p->reserve; break;
+    case 13: *value = p->ytc_ok ? 1 : 0; break;
     default: set_error("ef_plan_info: unknown index %d", what); return EF_ERR_ARG;
     }
     return EF_OK;

@@ -114,9 +114,13 @@ __global__ void yfrag_kernel(const YTcGeom g, const double *__restrict__ we, con
 }
 
 // One field per CTA (blockIdx.z): NOPS 5, a velocity (q_f with A_y^{p_f},
-// d_f, and C'_cf for c = 1..3); NOPS 1, a product (q only).  Warp units are
-// (LES row tile, pair of 8-point column tiles).
-template <int NOPS>
+// d_f, and C'_cf for c = 1..3); NOPS 1, a product (q only).  After the TMA
+// load the CTA splits its h column once, in place: the fp32 pair of rows
+// (2r, 2r + 1) at a point becomes the two B fragment words (hi in row 2r's
+// slot, lo in row 2r + 1's).  Warp units are (LES row tile, operator, NG
+// column tiles of 8 points); a unit streams its k-steps with the next
+// k-step's operator fragment loaded ahead.
+template <int NOPS, int NG>
 __global__ void __launch_bounds__(YTW * 32, 5) ytc_kernel(const __grid_constant__ YTcArgs a)
 {
     extern __shared__ float4 ysm4[];
@@ -131,6 +135,7 @@ __global__ void __launch_bounds__(YTW * 32, 5) ytc_kernel(const __grid_constant_
     const int tile = blockIdx.x, s = blockIdx.y, F = NOPS == 5 ? blockIdx.z : 3 + blockIdx.z;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
+    const int rows = 2 * geo.box_rows;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         mbar_fence_init();
@@ -144,49 +149,54 @@ __global__ void __launch_bounds__(YTW * 32, 5) ytc_kernel(const __grid_constant_
     }
     const int nplane = a.nplane;
     const size_t nl = (size_t)a.nly * nplane;
-    int op[NOPS];
-    if constexpr (NOPS == 5) {
-        op[0] = (F == 1) != (a.flip != 0) ? 1 : 0;          // velocities: Eq. 7 (+,-,+) or Eq. 9 (-,+,-)
-        op[1] = 2;
-#pragma unroll
-        for (int c = 0; c < 3; c++) op[2 + c] = 3 + 2 * c + pprod(c, F);
-    } else {
-        op[0] = (F == 4 || F == 7) ? 1 : 0;                 // products 12 and 23 are odd
-    }
     mbar_wait(&bar, 0, a.err);
+    // split the column once: (rows 2r, 2r + 1) -> (hi word, lo word)
+    unsigned *hw = reinterpret_cast<unsigned *>(hs);
+    for (int i = threadIdx.x; i < (rows / 2) * YTP; i += YTW * 32) {
+        const int r2 = i / YTP, pc = i - r2 * YTP;
+        unsigned hi, lo;
+        split_b(hs[(2 * r2) * YTS + pc], hs[(2 * r2 + 1) * YTS + pc], hi, lo);
+        hw[(2 * r2) * YTS + pc] = hi;
+        hw[(2 * r2 + 1) * YTS + pc] = lo;
+    }
+    __syncthreads();
 
+    constexpr int NGRP = 4 / NG;                   // column groups per 32-point tile
     bool bad = false;
-    for (int unit = warp; unit < 2 * geo.nmt; unit += YTW) {
-        const int mt = unit >> 1, n0 = 2 * (unit & 1);
-        float acc[NOPS][2][4];
+    for (int unit = warp; unit < geo.nmt * NOPS * NGRP; unit += YTW) {
+        const int mt = unit / (NOPS * NGRP), rem = unit - mt * NOPS * NGRP;
+        const int o = rem / NGRP, n0 = NG * (rem - o * NGRP);
+        float acc[NG][4];
 #pragma unroll
-        for (int o = 0; o < NOPS; o++)
+        for (int n = 0; n < NG; n++)
 #pragma unroll
-            for (int n = 0; n < 2; n++)
-#pragma unroll
-                for (int i = 0; i < 4; i++) acc[o][n][i] = 0.f;
-        const float *hf = hs + g + 8 * n0;
-        const uint4 *fr = a.frag + (size_t)s * kYOps * geo.kstot * 64 + lane;
-        for (int kk = 0; kk < geo.ks[mt]; kk++) {
-            const int j0 = geo.jb[mt] + 16 * kk;
-            unsigned bh[2][2], bl[2][2];
-#pragma unroll
-            for (int n = 0; n < 2; n++) {
-                const float *x = hf + (size_t)(j0 + 2 * t) * YTS + 8 * n;
-                split_b(x[0], x[YTS], bh[n][0], bl[n][0]);                 // rows 2t, 2t + 1
-                split_b(x[8 * YTS], x[9 * YTS], bh[n][1], bl[n][1]);       // rows 2t + 8, 2t + 9
+            for (int i = 0; i < 4; i++) acc[n][i] = 0.f;
+        const unsigned *bw = hw + g + 8 * n0 + (size_t)(geo.jb[mt] + 2 * t) * YTS;
+        // operator: velocities q (A_y^{p_F}, Eq. 7 (+,-,+) or Eq. 9 (-,+,-)), d, C'_cF;
+        // products q (12 and 23 odd)
+        const int opo = NOPS == 5 ? (o == 0 ? ((F == 1) != (a.flip != 0) ? 1 : 0)
+                                   : o == 1 ? 2 : 3 + 2 * (o - 2) + pprod(o - 2, F))
+                                  : ((F == 4 || F == 7) ? 1 : 0);
+        const uint4 *fo = a.frag + (((size_t)s * kYOps + opo) * geo.kstot + geo.koff[mt]) * 64 + lane;
+        uint4 ah = __ldg(fo), al = __ldg(fo + 32);
+        const int ks = geo.ks[mt];
+        for (int kk = 0; kk < ks; kk++) {
+            uint4 nah = ah, nal = al;
+            if (kk + 1 < ks) {
+                nah = __ldg(fo + 64 * (kk + 1));
+                nal = __ldg(fo + 64 * (kk + 1) + 32);
             }
+            const unsigned *x = bw + (size_t)16 * kk * YTS;
 #pragma unroll
-            for (int o = 0; o < NOPS; o++) {
-                const uint4 *fo = fr + ((size_t)op[o] * geo.kstot + geo.koff[mt] + kk) * 64;
-                const uint4 ah = __ldg(fo), al = __ldg(fo + 32);
-#pragma unroll
-                for (int n = 0; n < 2; n++) {
-                    mma16816(acc[o][n], ah, bh[n][0], bh[n][1]);
-                    mma16816(acc[o][n], al, bh[n][0], bh[n][1]);
-                    mma16816(acc[o][n], ah, bl[n][0], bl[n][1]);
-                }
+            for (int n = 0; n < NG; n++) {
+                const unsigned b0h = x[8 * n], b0l = x[YTS + 8 * n];                       // rows 2t, 2t + 1
+                const unsigned b1h = x[8 * YTS + 8 * n], b1l = x[9 * YTS + 8 * n];         // rows 2t + 8, 2t + 9
+                mma16816(acc[n], ah, b0h, b1h);
+                mma16816(acc[n], al, b0h, b1h);
+                mma16816(acc[n], ah, b0l, b1l);
             }
+            ah = nah;
+            al = nal;
         }
         // lane (g, t) holds rows 16 mt + g (+8) and points 8n + 2t (+1) of the tile
 #pragma unroll
@@ -195,25 +205,25 @@ __global__ void __launch_bounds__(YTW * 32, 5) ytc_kernel(const __grid_constant_
             if (J >= a.nly) continue;
             const size_t o0 = (size_t)J * nplane;
 #pragma unroll
-            for (int n = 0; n < 2; n++)
+            for (int n = 0; n < NG; n++)
 #pragma unroll
                 for (int e = 0; e < 2; e++) {
                     const int p = tile * YTP + 8 * (n0 + n) + 2 * t + e;
                     if (p >= nplane) continue;
                     float *tmp = a.tmp + (size_t)s * kYTmp * nl + o0 + p;
-                    const float q = acc[0][n][2 * hr + e];
+                    const float v = acc[n][2 * hr + e];
                     if constexpr (NOPS == 5) {
-                        const float v = (float)a.AU[((size_t)s * 3 + F) * a.nly + J] + q;
-                        bad |= !isfinite(v);
-                        a.ubar[((size_t)s * 3 + F) * nl + o0 + p] = v;
+                        if (o == 0) {
+                            const float ub = (float)a.AU[((size_t)s * 3 + F) * a.nly + J] + v;
+                            bad |= !isfinite(ub);
+                            a.ubar[((size_t)s * 3 + F) * nl + o0 + p] = ub;
+                        }
                         if (a.stress) {
-                            tmp[(size_t)F * nl] = q;
-                            tmp[(size_t)(12 + F) * nl] = acc[1][n][2 * hr + e];
-#pragma unroll
-                            for (int c = 0; c < 3; c++) tmp[(size_t)(3 + 3 * c + F) * nl] = acc[2 + c][n][2 * hr + e];
+                            const int slot = o == 0 ? F : o == 1 ? 12 + F : 3 + 3 * (o - 2) + F;
+                            tmp[(size_t)slot * nl] = v;
                         }
                     } else {
-                        tmp[(size_t)(15 + F - 3) * nl] = q;
+                        tmp[(size_t)(15 + F - 3) * nl] = v;
                     }
                 }
         }
@@ -265,17 +275,17 @@ __global__ void yrecover_kernel(const __grid_constant__ YTcArgs a, int nsnap)
     if (bad && a.err) atomicCAS(a.err, 0, (int)EF_ERR_NAN);
 }
 
-template <int NOPS>
+template <int NOPS, int NG>
 cudaError_t launch_part(const YTcArgs &a, int nsnap, int nz, cudaStream_t st)
 {
     const size_t smem = sizeof(float) * 2 * (size_t)a.geo.box_rows * YTS + 128;
     static size_t attr = 0;
     if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(ytc_kernel<NOPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(ytc_kernel<NOPS, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = smem;
     }
-    ytc_kernel<NOPS><<<dim3((a.nplane + YTP - 1) / YTP, nsnap, nz), YTW * 32, smem, st>>>(a);
+    ytc_kernel<NOPS, NG><<<dim3((a.nplane + YTP - 1) / YTP, nsnap, nz), YTW * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -299,6 +309,7 @@ bool ytc_geometry(const std::vector<int> &ystart, const std::vector<int> &ycount
             hi = ystart[J] + ycount[J] > hi ? ystart[J] + ycount[J] : hi;
         }
         if (hi <= lo) lo = hi = 0;
+        lo &= ~1;                 // even: the split words pair rows (2r, 2r + 1)
         g->jb[mt] = lo;
         g->ks[mt] = (hi - lo + 15) / 16;
         g->koff[mt] = kstot;
@@ -354,9 +365,9 @@ int encode_h_map(const float *h, int nplane, int ny, int nsnap, int box_rows, CU
 
 cudaError_t launch_ytc(const YTcArgs &a, int nsnap, cudaStream_t st)
 {
-    cudaError_t e = launch_part<5>(a, nsnap, 3, st);
+    cudaError_t e = launch_part<5, 4>(a, nsnap, 3, st);
     if (e != cudaSuccess || !a.stress) return e;
-    if ((e = launch_part<1>(a, nsnap, 6, st)) != cudaSuccess) return e;
+    if ((e = launch_part<1, 2>(a, nsnap, 6, st)) != cudaSuccess) return e;
     const size_t n = (size_t)a.nly * a.nplane * nsnap;
     yrecover_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, nsnap);
     return cudaGetLastError();

@@ -238,8 +238,9 @@ def test_tensor_core_variant_selected():
     dns, les, delta, _ = case("tc")
     plan = eles.filter_setup(dns, les, delta, precision=eles.PREC_BF16X3)
     assert eles.plan_info(plan, 10) == 3 and eles.plan_info(plan, 11) == 1
+    assert eles.plan_info(plan, 13) == 1                  # tensor-core y contraction
     plan32 = eles.filter_setup(dns, les, delta, precision=eles.PREC_FP32)
-    assert eles.plan_info(plan32, 10) == 1
+    assert eles.plan_info(plan32, 10) == 1 and eles.plan_info(plan32, 13) == 0
     with pytest.raises(eles.EFError):
         eles.plan_set_variant(plan32, 3 * 16 + 2)     # no tensor cores for an FP32 plan
 
