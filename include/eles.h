@@ -195,6 +195,34 @@ int ef_profile_enable(ef_plan *plan, int on);
 int ef_profile_read(ef_plan *plan, double *ms, long *calls);
 
 /* ------------------------------------------------------------------------
+ * Host buffers.  The same computation as ef_subfilter_stress_batch (Eq. 6
+ * evaluated by the steps of Sec. 2.1 on the Eq. 7 extension) with the
+ * snapshots and results in host memory: the copy of one group of `chunk`
+ * snapshots in and of another group's results out overlap the compute of a
+ * third (two device slots, a copy-in and a copy-out stream).
+ *
+ * ef_io_create -- set-up call: reserves the plan for `chunk` snapshots and
+ * allocates two device slots of `chunk` snapshots (inputs and outputs) plus
+ * two streams and events.  The pipeline uses the plan's scratch: one
+ * pipeline per plan, and no other call on the plan while a host call runs.
+ * Errors: EF_ERR_ARG, EF_ERR_OOM/EF_ERR_CUDA.
+ *
+ * ef_subfilter_stress_host -- u_host [nsnap][3][ny][nz][nx], ubar_host
+ * [nsnap][3][..], tau_host [nsnap][6][..], plane_mean_host [nsnap][3][ny]
+ * (double) or NULL, all in host memory, the plan's precision.  The copies
+ * overlap only when the host buffers are page-locked (cudaHostAlloc, or
+ * torch pin_memory); pageable buffers give the same results, serialised.
+ * Asynchronous on `stream`: the results are in the host buffers once
+ * `stream` is synchronised (the call ends with `stream` waiting on the last
+ * copy out).  Errors: EF_ERR_ARG, EF_ERR_CUDA.
+ * ---------------------------------------------------------------------- */
+typedef struct ef_io ef_io;
+int ef_io_create(ef_plan *plan, int chunk, ef_io **out);
+void ef_io_destroy(ef_io *io);
+int ef_subfilter_stress_host(ef_io *io, int nsnap, const void *u_host, void *ubar_host, void *tau_host,
+                             double *plane_mean_host, void *stream);
+
+/* ------------------------------------------------------------------------
  * Batches over several plans (different DNS grids, LES grids and filter
  * widths): item i runs nsnap[i] snapshots of plans[i].  ef_batch_run replays
  * every item's kernels as one CUDA graph on `stream` (captured on the first

@@ -34,7 +34,8 @@ EXPORTED = ("ef_filter_setup", "ef_plan_destroy", "ef_filter_fields", "ef_subfil
             "ef_closure_features", "ef_closure_fit_norm", "ef_closure_train", "ef_closure_infer",
             "ef_closure_gradients", "ef_closure_param_count", "ef_closure_get_params", "ef_closure_set_params",
             "ef_closure_save", "ef_closure_load", "ef_batch_create", "ef_batch_run", "ef_batch_destroy",
-            "ef_plan_autotune", "ef_plan_set_variant", "ef_closure_features_static")
+            "ef_plan_autotune", "ef_plan_set_variant", "ef_closure_features_static", "ef_io_create",
+            "ef_io_destroy", "ef_subfilter_stress_host")
 
 
 class EFError(RuntimeError):
@@ -127,6 +128,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             lib.ef_plan_autotune.restype = i
             lib.ef_plan_set_variant.argtypes = [vp, i]
             lib.ef_plan_set_variant.restype = i
+            lib.ef_io_create.argtypes = [vp, i, ctypes.POINTER(vp)]
+            lib.ef_io_create.restype = i
+            lib.ef_io_destroy.argtypes = [vp]
+            lib.ef_io_destroy.restype = None
+            lib.ef_subfilter_stress_host.argtypes = [vp, i, vp, vp, vp, vp, vp]
+            lib.ef_subfilter_stress_host.restype = i
             lib.ef_last_error.restype = ctypes.c_char_p
             lib.ef_version.restype = ctypes.c_char_p
             _lib = lib
@@ -451,3 +458,52 @@ def plan_autotune(plan: Plan, u, ubar, tau, reps: int = 3):
 
 def plan_set_variant(plan: Plan, choice: int) -> None:
     _check(load().ef_plan_set_variant(plan.handle, int(choice)))
+
+
+class HostIO:
+    """Owns an ef_io*: the host-buffer pipeline of one plan."""
+
+    def __init__(self, handle, plan, chunk):
+        self.handle, self.plan, self.chunk = handle, plan, chunk
+
+    def close(self):
+        if self.handle:
+            load().ef_io_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def io_create(plan: Plan, chunk: int = 1) -> HostIO:
+    """Set-up call: device slots of `chunk` snapshots for ef_subfilter_stress_host."""
+    h = ctypes.c_void_p()
+    _check(load().ef_io_create(plan.handle, int(chunk), ctypes.byref(h)))
+    return HostIO(h, plan, chunk)
+
+
+def _host_field(t, shape, dtype, name):
+    if t is None:
+        return None
+    if t.is_cuda or t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name}: need a contiguous host {dtype} tensor of shape {shape}, "
+                         f"got {t.dtype} {tuple(t.shape)} on {t.device}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def subfilter_stress_host(io: HostIO, u, ubar, tau, plane_mean=None, stream=None) -> None:
+    """Host (preferably pinned) tensors: u [S][3][ny][nz][nx], ubar [S][3][..],
+    tau [S][6][..], plane_mean [S][3][ny] (float64) or None.  Asynchronous on
+    `stream`; synchronise it before reading the outputs."""
+    import torch
+    plan = io.plan
+    d, l = plan.dns, plan.les
+    ns = u.shape[0]
+    pu = _host_field(u, (ns, 3, d.ny, d.nz, d.nx), plan.dtype, "u")
+    pb = _host_field(ubar, (ns, 3, l.ny, l.nz, l.nx), plan.dtype, "ubar")
+    pt = _host_field(tau, (ns, 6, l.ny, l.nz, l.nx), plan.dtype, "tau")
+    pm = _host_field(plane_mean, (ns, 3, d.ny), torch.float64, "plane_mean")
+    _check(load().ef_subfilter_stress_host(io.handle, ns, pu, pb, pt, pm, _stream(stream)))
