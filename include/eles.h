@@ -195,6 +195,44 @@ int ef_profile_enable(ef_plan *plan, int on);
 int ef_profile_read(ef_plan *plan, double *ms, long *calls);
 
 /* ------------------------------------------------------------------------
+ * Error measures of Sec. 4 (Eq. 13-15), as device reductions.  Velocities are
+ * divided by each run's friction velocity u_tau before comparison.
+ * Quadrature (the paper states none): x and z periodic and uniform (node
+ * sums), trapezoid rule on the y nodes; the wall-to-centre integral of
+ * Eq. 14 and 15 is that of the piecewise-linear interpolant over y in
+ * [-1, 0].  All sums are FP64 and in a fixed order (repeat calls agree bit
+ * for bit).
+ *
+ * ef_stats_create -- set-up call for fields on `grid` (x, z uniform, y the
+ * given ascending nodes) in the dtype of `precision` (FP64 for
+ * EF_PREC_FP64, FP32 otherwise): uploads the weights and allocates the
+ * partial-sum scratch.  Errors: EF_ERR_ARG, EF_ERR_CUDA.
+ *
+ * ef_plane_stats -- u [3][ny][nz][nx] (device): the plane means <u_c>(y_j)
+ * and intensities u_c,rms(y_j) = sqrt(<(u_c - <u_c>)^2>) over x and z, into
+ * mean, rms (device double [3][ny]).
+ *
+ * ef_error_field -- Eq. 13 for velocity component `component` (0, 1, 2; the
+ * paper uses u_1) of two fields a, b [3][ny][nz][nx] (device) on the grid:
+ * writes ||a/utau_a - b/utau_b||_V / ||b/utau_b||_V to *err (device double).
+ *
+ * ef_error_profile -- Eq. 14 (mean profiles) or Eq. 15 (rms profiles):
+ * pa, pb device double [ny] on the grid's y nodes; writes the wall-to-centre
+ * relative L2 error to *err (device double).
+ *
+ * All three are asynchronous on `stream`; calls on one ef_stats share its
+ * scratch, so run them on one stream.  Errors: EF_ERR_ARG, EF_ERR_CUDA.
+ * ---------------------------------------------------------------------- */
+typedef struct ef_stats ef_stats;
+int ef_stats_create(const ef_grid *grid, int precision, ef_stats **out);
+void ef_stats_destroy(ef_stats *st);
+int ef_plane_stats(ef_stats *st, const void *u, double *mean, double *rms, void *stream);
+int ef_error_field(ef_stats *st, const void *a, const void *b, int component, double utau_a, double utau_b,
+                   double *err, void *stream);
+int ef_error_profile(ef_stats *st, const double *pa, const double *pb, double utau_a, double utau_b, double *err,
+                     void *stream);
+
+/* ------------------------------------------------------------------------
  * Host buffers.  The same computation as ef_subfilter_stress_batch (Eq. 6
  * evaluated by the steps of Sec. 2.1 on the Eq. 7 extension) with the
  * snapshots and results in host memory: the copy of one group of `chunk`

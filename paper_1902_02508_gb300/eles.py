@@ -35,7 +35,8 @@ EXPORTED = ("ef_filter_setup", "ef_plan_destroy", "ef_filter_fields", "ef_subfil
             "ef_closure_gradients", "ef_closure_param_count", "ef_closure_get_params", "ef_closure_set_params",
             "ef_closure_save", "ef_closure_load", "ef_batch_create", "ef_batch_run", "ef_batch_destroy",
             "ef_plan_autotune", "ef_plan_set_variant", "ef_closure_features_static", "ef_io_create",
-            "ef_io_destroy", "ef_subfilter_stress_host")
+            "ef_io_destroy", "ef_subfilter_stress_host", "ef_stats_create", "ef_stats_destroy", "ef_plane_stats",
+            "ef_error_field", "ef_error_profile")
 
 
 class EFError(RuntimeError):
@@ -134,6 +135,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             lib.ef_io_destroy.restype = None
             lib.ef_subfilter_stress_host.argtypes = [vp, i, vp, vp, vp, vp, vp]
             lib.ef_subfilter_stress_host.restype = i
+            lib.ef_stats_create.argtypes = [ctypes.POINTER(_Grid), i, ctypes.POINTER(vp)]
+            lib.ef_stats_create.restype = i
+            lib.ef_stats_destroy.argtypes = [vp]
+            lib.ef_stats_destroy.restype = None
+            lib.ef_plane_stats.argtypes = [vp, vp, vp, vp, vp]
+            lib.ef_plane_stats.restype = i
+            lib.ef_error_field.argtypes = [vp, vp, vp, i, ctypes.c_double, ctypes.c_double, vp, vp]
+            lib.ef_error_field.restype = i
+            lib.ef_error_profile.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, vp, vp]
+            lib.ef_error_profile.restype = i
             lib.ef_last_error.restype = ctypes.c_char_p
             lib.ef_version.restype = ctypes.c_char_p
             _lib = lib
@@ -507,3 +518,65 @@ def subfilter_stress_host(io: HostIO, u, ubar, tau, plane_mean=None, stream=None
     pt = _host_field(tau, (ns, 6, l.ny, l.nz, l.nx), plan.dtype, "tau")
     pm = _host_field(plane_mean, (ns, 3, d.ny), torch.float64, "plane_mean")
     _check(load().ef_subfilter_stress_host(io.handle, ns, pu, pb, pt, pm, _stream(stream)))
+
+
+class Stats:
+    """Owns an ef_stats*: the Sec. 4 error measures for fields on one grid."""
+
+    def __init__(self, handle, grid, precision):
+        self.handle, self.grid, self.precision = handle, grid, precision
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == PREC_FP64 else torch.float32
+
+    def close(self):
+        if self.handle:
+            load().ef_stats_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def stats_create(grid, precision: int = PREC_FP32) -> Stats:
+    g, y = _grid(grid)
+    h = ctypes.c_void_p()
+    _check(load().ef_stats_create(ctypes.byref(g), int(precision), ctypes.byref(h)))
+    return Stats(h, grid, precision)
+
+
+def plane_stats(st: Stats, u, mean, rms, stream=None) -> None:
+    """u [3][ny][nz][nx] (device); mean, rms device float64 [3][ny]."""
+    import torch
+    g = st.grid
+    pu = _field(u, (3, g.ny, g.nz, g.nx), st.dtype, "u")
+    pm = _field(mean, (3, g.ny), torch.float64, "mean")
+    pr = _field(rms, (3, g.ny), torch.float64, "rms")
+    _check(load().ef_plane_stats(st.handle, pu, pm, pr, _stream(stream)))
+
+
+def error_field(st: Stats, a, b, err, component: int = 0, utau_a: float = 1.0, utau_b: float = 1.0,
+                stream=None) -> None:
+    """Eq. 13 of component `component`: a, b [3][ny][nz][nx] (device); err device float64 [1]."""
+    import torch
+    g = st.grid
+    pa = _field(a, (3, g.ny, g.nz, g.nx), st.dtype, "a")
+    pb = _field(b, (3, g.ny, g.nz, g.nx), st.dtype, "b")
+    pe = _field(err, (1,), torch.float64, "err")
+    _check(load().ef_error_field(st.handle, pa, pb, int(component), float(utau_a), float(utau_b), pe,
+                                 _stream(stream)))
+
+
+def error_profile(st: Stats, pa, pb, err, utau_a: float = 1.0, utau_b: float = 1.0, stream=None) -> None:
+    """Eq. 14 / 15: profiles pa, pb device float64 [ny]; err device float64 [1]."""
+    import torch
+    g = st.grid
+    a = _field(pa, (g.ny,), torch.float64, "pa")
+    b = _field(pb, (g.ny,), torch.float64, "pb")
+    pe = _field(err, (1,), torch.float64, "err")
+    _check(load().ef_error_profile(st.handle, a, b, float(utau_a), float(utau_b), pe, _stream(stream)))
