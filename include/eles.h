@@ -56,8 +56,14 @@ typedef enum {
     EF_ERR_UNSUPPORTED = 7   /* valid request the library does not implement */
 } ef_status;
 
-/* Filter kernels.  Only the Gaussian is implemented. */
-enum { EF_KERNEL_GAUSSIAN = 0 };
+/* Filter kernels.  The Gaussian, with the y integral of Eq. 2 on the
+ * stretched, wall-extended line evaluated either by the trapezoid rule on
+ * the extended nodes (EF_KERNEL_GAUSSIAN) or exactly against the
+ * piecewise-linear interpolant of the extended field (EF_KERNEL_GAUSSIAN_HAT:
+ * the quadrature alternative Sec. 3 names for the commutation error; it
+ * reproduces linear profiles exactly away from the walls).  x and z use the
+ * trapezoid rule in both.  The differential filter of Sec. 3 is not built. */
+enum { EF_KERNEL_GAUSSIAN = 0, EF_KERNEL_GAUSSIAN_HAT = 1 };
 
 /* Wall treatment. */
 enum {
@@ -96,7 +102,7 @@ typedef struct ef_plan ef_plan;
  *             same box: les->Lx == dns->Lx, les->Lz == dns->Lz, les->y within
  *             [-1, 1] ascending with les->y[0] = -1 and les->y[nly-1] = +1.
  *  delta      filter width, > 0; 2.5 delta must be < Lx/2, Lz/2 and < 2.
- *  kernel     EF_KERNEL_GAUSSIAN.
+ *  kernel     EF_KERNEL_GAUSSIAN or EF_KERNEL_GAUSSIAN_HAT.
  *  extension  EF_EXT_*.
  *  precision  EF_PREC_*.
  *  out        receives the plan (owned by the caller, free with

@@ -17,6 +17,9 @@
  *   - support cut at |s| <= 2.5 Delta (the excluded mass is ~5e-18);
  *   - quadrature: trapezoid rule on the (extended) node set, then every row
  *     divided by its own weight sum (a constant is preserved exactly), Eq. 2;
+ *     optionally in y, the kernel integrated exactly against the
+ *     piecewise-linear interpolant of the extended field (a linear function
+ *     is then reproduced exactly away from the walls);
  *   - extension across the walls, Eq. 7: u1, u3 even and u2 odd about each
  *     wall, applied at both walls and repeated (a period-4 line in y);
  *     the alternative of Eq. 9 flips every parity; a "truncated" mode filters
@@ -45,6 +48,39 @@ static double gauss(double s, double delta)
 }
 
 static int in_support(double s, double delta) { return fabs(s) <= 2.5 * delta; }
+
+/* Moments of the kernel over s in [a, b] clipped to the support
+ * |s - yi| <= 2.5 delta: I0 = int G(yi - s) ds, J1 = int G(yi - s)(s - yi) ds.
+ * With sigma^2 = delta^2 / 12, int G = erf differences and t G(t) has the
+ * antiderivative -sigma^2 G(t). */
+static void gauss_moments(double yi, double a, double b, double delta, double *I0, double *J1)
+{
+    double R = 2.5 * delta, sig = delta / sqrt(12.0);
+    if (a < yi - R) a = yi - R;
+    if (b > yi + R) b = yi + R;
+    *I0 = 0.0;
+    *J1 = 0.0;
+    if (!(b > a)) return;
+    double ta = a - yi, tb = b - yi;
+    *I0 = 0.5 * (erf(tb / (sig * sqrt(2.0))) - erf(ta / (sig * sqrt(2.0))));
+    *J1 = sig * sig * (gauss(ta, delta) - gauss(tb, delta));
+}
+
+/* Exact integral of G(yi - s) times the hat function of a node at e whose
+ * neighbours are el < e < er (has_l / has_r: the neighbour exists). */
+static double hat_weight(double yi, double e, int has_l, double el, int has_r, double er, double delta)
+{
+    double w = 0.0, I0, J1;
+    if (has_l) {
+        gauss_moments(yi, el, e, delta, &I0, &J1);
+        w += (J1 + (yi - el) * I0) / (e - el);
+    }
+    if (has_r) {
+        gauss_moments(yi, e, er, delta, &I0, &J1);
+        w += ((er - yi) * I0 - J1) / (er - e);
+    }
+    return w;
+}
 
 int or_num_threads(void)
 {
@@ -130,8 +166,21 @@ static int cmp_ext(const void *a, const void *b)
     return (d > 0) - (d < 0);
 }
 
+int or_op_wall_q(int ny, const double *y, int nly, const double *Y, double delta,
+                 int mode, int parity, int quad, double *A);
+
 int or_op_wall(int ny, const double *y, int nly, const double *Y, double delta,
                int mode, int parity, double *A)
+{
+    return or_op_wall_q(ny, y, nly, Y, delta, mode, parity, 0, A);
+}
+
+/* quad 0: trapezoid weights G(y_i - e_n) h_n on the extended node set;
+ * quad 1: the kernel integrated exactly against the piecewise-linear
+ * interpolant of the extended field (hat function of each extended node,
+ * its neighbours in the sorted extended set), cut at the support. */
+int or_op_wall_q(int ny, const double *y, int nly, const double *Y, double delta,
+                 int mode, int parity, int quad, double *A)
 {
     if (ny < 3 || nly < 2 || !(delta > 0)) return 1;
     for (int j = 1; j < ny; j++) if (!(y[j] > y[j - 1])) return 1;
@@ -162,9 +211,15 @@ int or_op_wall(int ny, const double *y, int nly, const double *Y, double delta,
     for (int i = 0; i < ny; i++) {
         double norm = 0.0;
         for (int n = 0; n < ne; n++) {
-            double s = y[i] - E[n].e;
-            if (!in_support(s, delta)) continue;
-            double w = gauss(s, delta) * h[n];
+            double s = y[i] - E[n].e, w;
+            if (quad == 0) {
+                if (!in_support(s, delta)) continue;
+                w = gauss(s, delta) * h[n];
+            } else {
+                w = hat_weight(y[i], E[n].e, n > 0, n > 0 ? E[n - 1].e : 0.0, n < ne - 1,
+                               n < ne - 1 ? E[n + 1].e : 0.0, delta);
+                if (w == 0.0) continue;
+            }
             norm += w;
             /* A wall node is its own mirror image: an odd extension is zero
              * there, an even one takes the node's value. */
@@ -282,9 +337,21 @@ static const int PAIR_J[6] = {0, 1, 2, 1, 2, 2};
  * order 11, 12, 13, 22, 23, 33.  ext: 0 Eq. 7, 1 Eq. 9, 2 truncated.
  * Rows J outside [J0, J1) are left untouched (J1 <= 0: all rows).
  * ------------------------------------------------------------------------- */
+int or_subfilter_stress_q(int nx, int ny, int nz, double Lx, double Lz, const double *y,
+                          int nlx, int nly, int nlz, const double *Y, double delta, int ext, int quad,
+                          const double *u, double *ubar, double *tau, int J0, int J1);
+
 int or_subfilter_stress(int nx, int ny, int nz, double Lx, double Lz, const double *y,
                         int nlx, int nly, int nlz, const double *Y, double delta, int ext,
                         const double *u, double *ubar, double *tau, int J0, int J1)
+{
+    return or_subfilter_stress_q(nx, ny, nz, Lx, Lz, y, nlx, nly, nlz, Y, delta, ext, 0, u, ubar, tau, J0, J1);
+}
+
+/* The same with the y quadrature chosen as in or_op_wall_q. */
+int or_subfilter_stress_q(int nx, int ny, int nz, double Lx, double Lz, const double *y,
+                          int nlx, int nly, int nlz, const double *Y, double delta, int ext, int quad,
+                          const double *u, double *ubar, double *tau, int J0, int J1)
 {
     size_t np = (size_t)nx * ny * nz, nl = (size_t)nlx * nly * nlz;
     double *Ax = (double *)malloc(sizeof(double) * (size_t)nlx * nx);
@@ -300,8 +367,8 @@ int or_subfilter_stress(int nx, int ny, int nz, double Lx, double Lz, const doub
     int rc = or_op_periodic(nx, Lx, nlx, delta, Ax);
     rc |= or_op_periodic(nz, Lz, nlz, delta, Az);
     int wmode = (ext == 2) ? 1 : 0;
-    rc |= or_op_wall(ny, y, nly, Y, delta, wmode, +1, Ayp);
-    rc |= or_op_wall(ny, y, nly, Y, delta, wmode, -1, Aym);
+    rc |= or_op_wall_q(ny, y, nly, Y, delta, wmode, +1, quad, Ayp);
+    rc |= or_op_wall_q(ny, y, nly, Y, delta, wmode, -1, quad, Aym);
     if (rc) { free(Ax); free(Az); free(Ayp); free(Aym); free(prod); free(uu); return 1; }
     if (J1 <= 0 || J1 > nly) J1 = nly;
     /* steps 1-2 for the velocities themselves: bar(u_i) */

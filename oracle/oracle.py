@@ -60,6 +60,8 @@ def _load():
             lib.or_op_wall.argtypes = [i, p, i, p, d, i, i, p]
             lib.or_apply_separable.argtypes = [i, i, i, i, i, i, p, p, p, p, p, i, i]
             lib.or_subfilter_stress.argtypes = [i, i, i, d, d, p, i, i, i, p, d, i, p, p, p, i, i]
+            lib.or_subfilter_stress_q.argtypes = [i, i, i, d, d, p, i, i, i, p, d, i, i, p, p, p, i, i]
+            lib.or_op_wall_q.argtypes = [i, p, i, p, d, i, i, i, p]
             lib.or_direct3d_points.argtypes = [i, i, i, d, d, p, i, i, i, p, d, i, p, i, p, p, p]
             lib.or_num_threads.restype = i
             lib.or_set_threads.argtypes = [i]
@@ -91,11 +93,12 @@ def op_periodic(n: int, L: float, nl: int, delta: float) -> np.ndarray:
     return A
 
 
-def op_wall(y, Y, delta: float, parity: int, truncated: bool = False) -> np.ndarray:
+def op_wall(y, Y, delta: float, parity: int, truncated: bool = False, quad: int = 0) -> np.ndarray:
+    """quad 0: trapezoid; 1: kernel integrated exactly against the piecewise-linear interpolant."""
     y, Y = _f64(y), _f64(Y)
     A = np.zeros((Y.size, y.size))
-    rc = _load().or_op_wall(y.size, _ptr(y), Y.size, _ptr(Y), float(delta),
-                            1 if truncated else 0, int(parity), _ptr(A))
+    rc = _load().or_op_wall_q(y.size, _ptr(y), Y.size, _ptr(Y), float(delta),
+                              1 if truncated else 0, int(parity), int(quad), _ptr(A))
     if rc:
         raise ValueError(f"or_op_wall failed ({rc})")
     return A
@@ -114,7 +117,7 @@ def apply_separable(f, Ax, Ay, Az, J0: int = 0, J1: int = 0) -> np.ndarray:
 
 
 def subfilter_stress(dns, les, delta: float, u, ext: int = EXT_EVEN_ODD,
-                     J0: int = 0, J1: int = 0):
+                     J0: int = 0, J1: int = 0, quad: int = 0):
     """(ubar[3][nly][nlz][nlx], tau[6][nly][nlz][nlx]) for the whole snapshot
     (or LES rows J0 <= J < J1; other rows are zero)."""
     u = _f64(u)
@@ -122,9 +125,9 @@ def subfilter_stress(dns, les, delta: float, u, ext: int = EXT_EVEN_ODD,
     y, Y = _f64(dns.y), _f64(les.y)
     ubar = np.zeros((3, les.ny, les.nz, les.nx))
     tau = np.zeros((6, les.ny, les.nz, les.nx))
-    rc = _load().or_subfilter_stress(dns.nx, dns.ny, dns.nz, dns.Lx, dns.Lz, _ptr(y),
-                                     les.nx, les.ny, les.nz, _ptr(Y), float(delta), int(ext),
-                                     _ptr(u), _ptr(ubar), _ptr(tau), J0, J1)
+    rc = _load().or_subfilter_stress_q(dns.nx, dns.ny, dns.nz, dns.Lx, dns.Lz, _ptr(y),
+                                       les.nx, les.ny, les.nz, _ptr(Y), float(delta), int(ext), int(quad),
+                                       _ptr(u), _ptr(ubar), _ptr(tau), J0, J1)
     if rc:
         raise ValueError(f"or_subfilter_stress failed ({rc})")
     return ubar, tau

@@ -179,7 +179,10 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
     int rc;
     if ((rc = check_grid(dns, "dns")) || (rc = check_grid(les, "les"))) return rc;
     if (!(delta > 0) || !isfinite(delta)) { set_error("delta must be finite and > 0"); return EF_ERR_ARG; }
-    if (kernel != EF_KERNEL_GAUSSIAN) { set_error("only the Gaussian kernel is implemented"); return EF_ERR_UNSUPPORTED; }
+    if (kernel != EF_KERNEL_GAUSSIAN && kernel != EF_KERNEL_GAUSSIAN_HAT) {
+        set_error("only the Gaussian kernel is implemented (trapezoid or hat quadrature in y)");
+        return EF_ERR_UNSUPPORTED;
+    }
     if (extension < EF_EXT_EVEN_ODD || extension > EF_EXT_NONE) { set_error("unknown extension %d", extension); return EF_ERR_ARG; }
     if (precision != EF_PREC_FP64 && precision != EF_PREC_FP32 && precision != EF_PREC_BF16X3) {
         set_error("precision %d not implemented", precision);
@@ -197,6 +200,7 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
     p->nlx = les->nx; p->nly = les->ny; p->nlz = les->nz;
     p->Lx = dns->Lx; p->Lz = dns->Lz; p->delta = delta;
     p->ext = extension; p->prec = precision;
+    p->yquad = kernel == EF_KERNEL_GAUSSIAN_HAT ? 1 : 0;
     if (extension == EF_EXT_ODD_EVEN) { p->par[0] = -1; p->par[1] = 1; p->par[2] = -1; }
     cudaError_t e;
 #define CK(x, what) do { if ((e = (x)) != cudaSuccess) { rc = cuda_fail(e, what); goto fail; } } while (0)

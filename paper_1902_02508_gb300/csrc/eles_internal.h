@@ -144,6 +144,7 @@ struct ef_plan {
     int nx = 0, ny = 0, nz = 0, nlx = 0, nly = 0, nlz = 0;
     double Lx = 0, Lz = 0, delta = 0;
     int ext = 0, prec = 0;
+    int yquad = 0;                // y quadrature: 0 trapezoid, 1 hat (EF_KERNEL_GAUSSIAN_HAT)
     int par[3] = {1, -1, 1};      // wall parity of u1, u2, u3 (Eq. 7 or Eq. 9)
     eles::Band bx, bz;            // x and z operators
     eles::Ring rx, rz;            // their strided-convolution tables (if ok)

@@ -68,8 +68,63 @@ __device__ __forceinline__ double wall_trap(const double *y, int ny, int j, int 
     return 0.5 * (y[j + 1] - y[j - 1]);
 }
 
+// Kernel moments over s in [a, b] clipped to |s - yi| <= 2.5 delta:
+// I0 = int G(yi - s) ds (erf differences), J1 = int G(yi - s)(s - yi) ds
+// (t G(t) integrates to -sigma^2 G(t), sigma^2 = delta^2 / 12).
+__device__ void kernel_moments(double yi, double a, double b, double delta, double &I0, double &J1)
+{
+    const double R = 2.5 * delta, sig = delta / sqrt(12.0);
+    a = fmax(a, yi - R);
+    b = fmin(b, yi + R);
+    I0 = 0.0;
+    J1 = 0.0;
+    if (!(b > a)) return;
+    const double ta = a - yi, tb = b - yi, c = 1.0 / (sig * sqrt(2.0));
+    I0 = 0.5 * (erf(tb * c) - erf(ta * c));
+    J1 = sig * sig * (gauss(ta, delta) - gauss(tb, delta));
+}
+
+// Weight of a node at e of the extended line under the hat quadrature: the
+// kernel integrated exactly against the node's hat function, whose left and
+// right neighbours lie hl and hr away (0: no neighbour on that side).
+__device__ double hat_weight(double yi, double e, double hl, double hr, double delta)
+{
+    double w = 0.0, I0, J1;
+    if (hl > 0.0) {
+        kernel_moments(yi, e - hl, e, delta, I0, J1);
+        w += (J1 + (yi - (e - hl)) * I0) / hl;
+    }
+    if (hr > 0.0) {
+        kernel_moments(yi, e, e + hr, delta, I0, J1);
+        w += ((e + hr - yi) * I0 - J1) / hr;
+    }
+    return w;
+}
+
+// Weight of image e of DNS node j (mirror: the image reflected about a wall)
+// at the filtered node yi: trapezoid or hat quadrature.
+__device__ double image_weight(const double *y, int ny, int j, bool mirror, double e, double yi, double delta,
+                               int truncated, int hat)
+{
+    if (!hat) {
+        const double s = yi - e;
+        return fabs(s) <= 2.5 * delta ? gauss(s, delta) * wall_trap(y, ny, j, truncated) : 0.0;
+    }
+    // gaps to the neighbours on the extended line: the mirror image has its
+    // source's gaps swapped; a wall node's outer neighbour is the mirror of
+    // its inner one (none on the truncated line)
+    double hl = j > 0 ? y[j] - y[j - 1] : (truncated ? 0.0 : y[1] - y[0]);
+    double hr = j < ny - 1 ? y[j + 1] - y[j] : (truncated ? 0.0 : y[ny - 1] - y[ny - 2]);
+    if (mirror) {
+        const double t = hl;
+        hl = hr;
+        hr = t;
+    }
+    return hat_weight(yi, e, hl, hr, delta);
+}
+
 // Adds (scale x) row i of F^even and F^odd to the dense rows re, ro.
-__device__ void wall_row_accumulate(const double *y, int ny, int i, double delta, int truncated,
+__device__ void wall_row_accumulate(const double *y, int ny, int i, double delta, int truncated, int hat,
                                     double scale, double *re, double *ro)
 {
     double yi = y[i];
@@ -78,32 +133,27 @@ __device__ void wall_row_accumulate(const double *y, int ny, int i, double delta
     for (int m = -1; m <= 1; m++) {
         if (truncated && m != 0) continue;
         for (int j = 0; j < ny; j++) {
-            double h = wall_trap(y, ny, j, truncated);
-            double s = yi - (y[j] + 4.0 * m);
-            if (fabs(s) <= 2.5 * delta) norm += gauss(s, delta) * h;
-            if (!truncated && j > 0 && j < ny - 1) {
-                s = yi - (-2.0 - y[j] + 4.0 * m);
-                if (fabs(s) <= 2.5 * delta) norm += gauss(s, delta) * h;
-            }
+            norm += image_weight(y, ny, j, false, y[j] + 4.0 * m, yi, delta, truncated, hat);
+            if (!truncated && j > 0 && j < ny - 1)
+                norm += image_weight(y, ny, j, true, -2.0 - y[j] + 4.0 * m, yi, delta, truncated, hat);
         }
     }
     // pass 2: fold every image onto its source node with the parity sign
     for (int m = -1; m <= 1; m++) {
         if (truncated && m != 0) continue;
         for (int j = 0; j < ny; j++) {
-            double h = wall_trap(y, ny, j, truncated);
             bool wall = (j == 0 || j == ny - 1);
-            double s = yi - (y[j] + 4.0 * m);
-            if (fabs(s) <= 2.5 * delta) {
-                double w = scale * gauss(s, delta) * h / norm;
+            double w = image_weight(y, ny, j, false, y[j] + 4.0 * m, yi, delta, truncated, hat);
+            if (w != 0.0) {
+                w *= scale / norm;
                 re[j] += w;
                 // a wall node is its own mirror: an odd extension vanishes there
                 if (truncated || !wall) ro[j] += w;
             }
             if (!truncated && !wall) {
-                s = yi - (-2.0 - y[j] + 4.0 * m);
-                if (fabs(s) <= 2.5 * delta) {
-                    double w = scale * gauss(s, delta) * h / norm;
+                w = image_weight(y, ny, j, true, -2.0 - y[j] + 4.0 * m, yi, delta, truncated, hat);
+                if (w != 0.0) {
+                    w *= scale / norm;
                     re[j] += w;
                     ro[j] -= w;
                 }
@@ -115,7 +165,7 @@ __device__ void wall_row_accumulate(const double *y, int ny, int i, double delta
 // Row J of A_y^even / A_y^odd on the LES node Y[J]: linear interpolation of
 // rows i0, i0+1 of F (i0 = last DNS node <= Y, capped at ny - 2).
 __global__ void wall_rows_kernel(const double *y, int ny, const double *Y, int nly, double delta,
-                                 int truncated, double *we, double *wo, float *we32, float *wo32,
+                                 int truncated, int hat, double *we, double *wo, float *we32, float *wo32,
                                  int *start, int *count)
 {
     int J = blockIdx.x * blockDim.x + threadIdx.x;
@@ -124,8 +174,8 @@ __global__ void wall_rows_kernel(const double *y, int ny, const double *Y, int n
     int i0 = 0;
     while (i0 < ny - 2 && y[i0 + 1] <= Y[J]) i0++;
     double theta = (Y[J] - y[i0]) / (y[i0 + 1] - y[i0]);
-    if (1.0 - theta != 0.0) wall_row_accumulate(y, ny, i0, delta, truncated, 1.0 - theta, re, ro);
-    if (theta != 0.0) wall_row_accumulate(y, ny, i0 + 1, delta, truncated, theta, re, ro);
+    if (1.0 - theta != 0.0) wall_row_accumulate(y, ny, i0, delta, truncated, hat, 1.0 - theta, re, ro);
+    if (theta != 0.0) wall_row_accumulate(y, ny, i0 + 1, delta, truncated, hat, theta, re, ro);
     int lo = ny, hi = -1;
     for (int j = 0; j < ny; j++) {
         if (re[j] != 0.0 || ro[j] != 0.0) { if (j < lo) lo = j; hi = j; }
@@ -202,7 +252,7 @@ int build_wall_rows(ef_plan *p, const double *h_les_y)
     if (e == cudaSuccess) e = cudaMalloc(&p->d_ycount, sizeof(int) * p->nly);
     if (e != cudaSuccess) { cudaFree(dY); return cuda_fail(e, "allocate y operator"); }
     int truncated = (p->ext == EF_EXT_NONE) ? 1 : 0;
-    wall_rows_kernel<<<(p->nly + 63) / 64, 64>>>(p->d_ygrid, p->ny, dY, p->nly, p->delta, truncated,
+    wall_rows_kernel<<<(p->nly + 63) / 64, 64>>>(p->d_ygrid, p->ny, dY, p->nly, p->delta, truncated, p->yquad,
                                                  p->d_yw64[0], p->d_yw64[1], p->d_yw32[0],
                                                  p->d_yw32[1], p->d_ystart, p->d_ycount);
     e = cudaGetLastError();

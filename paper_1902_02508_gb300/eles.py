@@ -23,6 +23,7 @@ EF_OK = 0
 STATUS = {0: "EF_OK", 1: "EF_ERR_ARG", 2: "EF_ERR_SHAPE", 3: "EF_ERR_CUDA", 4: "EF_ERR_NAN",
           5: "EF_ERR_TIMEOUT", 6: "EF_ERR_OOM", 7: "EF_ERR_UNSUPPORTED"}
 KERNEL_GAUSSIAN = 0
+KERNEL_GAUSSIAN_HAT = 1      # y integral exact against the piecewise-linear interpolant
 EXT_EVEN_ODD, EXT_ODD_EVEN, EXT_NONE = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_TF32X2, PREC_BF16X3 = 0, 1, 2, 3
 

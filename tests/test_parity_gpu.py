@@ -285,3 +285,29 @@ def test_repeat_calls_are_bitwise_stable():
         outs.append(tau.cpu())
     torch.cuda.synchronize()
     assert torch.equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("name", ["tiny", "tc"])
+@pytest.mark.parametrize("prec", [eles.PREC_FP64, eles.PREC_FP32, eles.PREC_BF16X3])
+def test_hat_quadrature_matches_oracle(name, prec):
+    """EF_KERNEL_GAUSSIAN_HAT: the y operators built on the device equal the
+    oracle's hat-quadrature operators, and the whole path matches the
+    oracle evaluated with them."""
+    dns, les, delta, u = case(name, seed=77)
+    plan = eles.filter_setup(dns, les, delta, kernel=eles.KERNEL_GAUSSIAN_HAT, precision=prec)
+    # 1e-13, not 1e-14: the weights are differences of erf values (device and
+    # host erf differ in the last ulps) divided by the node gaps
+    assert np.abs(eles.plan_weights(plan, 2) - O.op_wall(dns.y, les.y, delta, +1, quad=1)).max() < 1e-13
+    assert np.abs(eles.plan_weights(plan, 3) - O.op_wall(dns.y, les.y, delta, -1, quad=1)).max() < 1e-13
+    ub_ref, tau_ref = O.subfilter_stress(dns, les, delta, u, quad=1)
+    dev = torch.device("cuda")
+    ud = torch.from_numpy(u).to(dev, plan.dtype)
+    ub = torch.empty((3, les.ny, les.nz, les.nx), device=dev, dtype=plan.dtype)
+    tau = torch.empty((6, les.ny, les.nz, les.nx), device=dev, dtype=plan.dtype)
+    eles.subfilter_stress(plan, ud, ub, tau)
+    torch.cuda.synchronize()
+    tol = TOL64 if prec == eles.PREC_FP64 else TOL32
+    assert_close(ub.double().cpu().numpy(), ub_ref, tol, "ubar")
+    assert_close(tau.double().cpu().numpy(), tau_ref, tol, "tau")
+    # the trapezoid operator differs (the quadrature really changed)
+    assert np.abs(eles.plan_weights(plan, 2) - O.op_wall(dns.y, les.y, delta, +1)).max() > 1e-8
