@@ -308,7 +308,7 @@ int ef_plan_set_variant(ef_plan *plan, int choice);
  * ---------------------------------------------------------------------- */
 typedef struct {
     int hidden;               /* must be 128 */
-    int batch;                /* mini-batch size (also the inference chunk) */
+    int batch;                /* training mini-batch size */
     float lr;                 /* Adam learning rate */
     float guard_sigma;        /* inference guard: a standardised input beyond this uses the exact stress */
     unsigned long long seed;  /* initialisation and batch order */
@@ -365,9 +365,19 @@ int ef_closure_train(ef_closure *closure, const float *feats, const float *tau, 
  * a standardised input exceeds the guard the model is outside its training
  * range: if exact_tau (device [6][N]) is given that exact stress is used
  * there, and *n_fallback (if not NULL) receives the count (synchronises).
+ * One tensor-core kernel over all N points (tcgen05, accumulators in TMEM):
+ * BF16 working weights, activations split into two BF16 parts, FP32
+ * accumulation; standardisation, guard, SiLU and the fallback are fused.
+ * A wait inside the kernel that ran out is recorded in the closure's error
+ * word: returned here when n_fallback is requested, else read by
+ * ef_closure_check_device_error.
  */
 int ef_closure_infer(ef_closure *closure, const float *feats, float *tau_out, long n, const float *exact_tau,
                      long *n_fallback, void *stream);
+
+/* Read (and clear) the closure's device error word; synchronises `stream`.
+ * Returns EF_OK or the recorded ef_status (EF_ERR_TIMEOUT). */
+int ef_closure_check_device_error(ef_closure *closure, void *stream);
 
 /* One forward and backward pass over n <= batch points without an update:
  * host grad_out[param count] (layout of ef_closure_get_params), *loss_out. */

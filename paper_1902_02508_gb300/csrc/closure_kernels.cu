@@ -244,23 +244,6 @@ __global__ void round_copy(const float *w, float *Wq, long n)
     if (i < n) Wq[i] = bf16_round(w[i]);
 }
 
-// Inference output: tau[q][p] = mu_q + sd_q * Y[p][q]; where a standardised
-// input exceeds the guard and an exact stress is given, use the exact one.
-__global__ void finish_infer(const float *__restrict__ Y, const float *__restrict__ H0, long p0, int nb, long n,
-                             const double *tmu, const double *tsd, float guard, const float *exact, float *tau,
-                             int *nfall)
-{
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
-    const long p = p0 + b;
-    bool out_of_range = false;
-    for (int k = 0; k < NIN; k++) out_of_range |= fabsf(H0[(long)b * NIN + k]) > guard;
-    const bool fall = out_of_range && exact != nullptr;
-    for (int q = 0; q < NOUT; q++)
-        tau[(long)q * n + p] = fall ? exact[(long)q * n + p] : (float)(tmu[q] + tsd[q] * Y[(long)b * NOUT + q]);
-    if (out_of_range) atomicAdd(nfall, 1);
-}
-
 __global__ void iota_range(long *idx, long p0, int nb)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -301,7 +284,8 @@ struct ef_closure {
     float *Z[eles::NLAYER] = {};
     float *T = nullptr, *dA = nullptr, *dB = nullptr, *rowloss = nullptr, *parts = nullptr;
     long *idx = nullptr;
-    int *nfall = nullptr;
+    int *nfall = nullptr;      // [0] guarded points of the last inference, [1] device error word
+    void *image = nullptr;     // tensor-core inference image (packed weights and statistics)
     size_t parts_len = 0;
 };
 
@@ -425,7 +409,9 @@ int ef_closure_create(const ef_closure_cfg *cfg, ef_closure **out)
     for (auto b : bufs)
         if (e == cudaSuccess) e = cudaMalloc(b, sizeof(float) * c->nparam);
     if (e == cudaSuccess) e = cudaMalloc(&c->stats, sizeof(double) * 32);
-    if (e == cudaSuccess) e = cudaMalloc(&c->nfall, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->nfall, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->nfall, 0, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->image, closure_tc_image_bytes());
     if (e == cudaSuccess) e = cudaMemset(c->w, 0, sizeof(float) * c->nparam);
     if (e == cudaSuccess) e = cudaMemset(c->m, 0, sizeof(float) * c->nparam);
     if (e == cudaSuccess) e = cudaMemset(c->v, 0, sizeof(float) * c->nparam);
@@ -448,6 +434,7 @@ void ef_closure_destroy(ef_closure *c)
     if (!c) return;
     cudaFree(c->w); cudaFree(c->wq); cudaFree(c->m); cudaFree(c->v); cudaFree(c->g); cudaFree(c->stats);
     cudaFree(c->nfall);
+    cudaFree(c->image);
     for (int l = 0; l <= NLAYER; l++) cudaFree(c->H[l]);
     for (int l = 0; l < NLAYER; l++) cudaFree(c->Z[l]);
     cudaFree(c->T); cudaFree(c->dA); cudaFree(c->dB); cudaFree(c->rowloss); cudaFree(c->idx); cudaFree(c->parts);
@@ -595,26 +582,37 @@ int ef_closure_infer(ef_closure *c, const float *feats, float *tau_out, long n, 
     if (!c->fitted) { set_error("ef_closure_infer: the closure has not been fitted or loaded"); return EF_ERR_ARG; }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(c->nfall, 0, sizeof(int), s);
-    const int B = c->cap;
-    for (long p0 = 0; p0 < n && e == cudaSuccess; p0 += B) {
-        const int nb = (int)(n - p0 < B ? n - p0 : B);
-        iota_range<<<grid1(nb), 256, 0, s>>>(c->idx, p0, nb);
-        gather_batch<<<grid1(nb), 256, 0, s>>>(feats, nullptr, n, c->idx, nb, c->stats, c->stats + 10, c->stats + 20,
-                                               c->stats + 26, c->H[0], nullptr);
-        forward(c, nb, s);
-        finish_infer<<<grid1(nb), 256, 0, s>>>(c->H[NLAYER], c->H[0], p0, nb, n, c->stats + 20, c->stats + 26,
-                                               c->cfg.guard_sigma, exact_tau, tau_out, c->nfall);
-        e = cudaGetLastError();
-    }
     if (e != cudaSuccess) return cuda_fail(e, "ef_closure_infer");
+    rc = closure_infer_tc(c->wq, c->off_w, c->off_b, c->stats, c->image, feats, n, c->cfg.guard_sigma, exact_tau,
+                          tau_out, c->nfall, c->nfall + 1, s);
+    if (rc) return rc;
     if (n_fallback) {
-        int nf = 0;
-        e = cudaMemcpyAsync(&nf, c->nfall, sizeof(int), cudaMemcpyDeviceToHost, s);
+        int w[2] = {0, 0};
+        e = cudaMemcpyAsync(w, c->nfall, sizeof w, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "fallback count");
-        *n_fallback = nf;
+        if (w[1]) {
+            cudaMemsetAsync(c->nfall + 1, 0, sizeof(int), s);
+            set_error("ef_closure_infer: device error %d (a wait ran out)", w[1]);
+            return w[1];
+        }
+        *n_fallback = w[0];
     }
     return EF_OK;
+}
+
+int ef_closure_check_device_error(ef_closure *c, void *stream)
+{
+    int rc = check_closure(c, "ef_closure_check_device_error");
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int code = 0;
+    cudaError_t e = cudaMemcpyAsync(&code, c->nfall + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->nfall + 1, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "ef_closure_check_device_error");
+    if (code) set_error("closure device error %d (a wait ran out)", code);
+    return code;
 }
 
 int ef_closure_gradients(ef_closure *c, const float *feats, const float *tau, long n, float *grad_out,

@@ -212,4 +212,13 @@ int run_filter(ef_plan *p, int nsnap, const void *u, void *ubar, void *tau, doub
                bool stress, cudaStream_t s, const PhaseEvents *pe);
 int plan_reserve(ef_plan *p, int nsnap);
 
+// closure_tc.cu: tensor-core inference of the closure MLP.  `image` is a
+// device buffer of closure_tc_image_bytes() that the call repacks from the
+// working weights and statistics; nfall counts guarded points; err receives
+// EF_ERR_TIMEOUT if a wait ran out.
+size_t closure_tc_image_bytes();
+int closure_infer_tc(const float *wq, const long *off_w, const long *off_b, const double *stats, void *image,
+                     const float *feats, long n, float guard, const float *exact, float *tau, int *nfall, int *err,
+                     cudaStream_t s);
+
 }  // namespace eles

@@ -36,6 +36,7 @@ EXPORTED = ("ef_filter_setup", "ef_plan_destroy", "ef_filter_fields", "ef_subfil
             "ef_closure_gradients", "ef_closure_param_count", "ef_closure_get_params", "ef_closure_set_params",
             "ef_closure_save", "ef_closure_load", "ef_batch_create", "ef_batch_run", "ef_batch_destroy",
             "ef_plan_autotune", "ef_plan_set_variant", "ef_closure_features_static", "ef_io_create",
+            "ef_closure_check_device_error",
             "ef_io_destroy", "ef_subfilter_stress_host", "ef_stats_create", "ef_stats_destroy", "ef_plane_stats",
             "ef_error_field", "ef_error_profile")
 
@@ -108,6 +109,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             lib.ef_closure_train.restype = i
             lib.ef_closure_infer.argtypes = [vp, vp, vp, L, vp, ctypes.POINTER(L), vp]
             lib.ef_closure_infer.restype = i
+            lib.ef_closure_check_device_error.argtypes = [vp, vp]
+            lib.ef_closure_check_device_error.restype = i
             lib.ef_closure_gradients.argtypes = [vp, vp, vp, L, vp, ctypes.POINTER(ctypes.c_float), vp]
             lib.ef_closure_gradients.restype = i
             lib.ef_closure_param_count.argtypes = [vp]
@@ -354,15 +357,22 @@ def closure_train(cl: Closure, feats, tau, epochs: int, stream=None) -> float:
     return loss.value
 
 
-def closure_infer(cl: Closure, feats, tau_out, exact_tau=None, stream=None) -> int:
+def closure_infer(cl: Closure, feats, tau_out, exact_tau=None, stream=None, count: bool = True):
+    """Tensor-core inference; returns the number of guarded points (count=True,
+    synchronises) or None (count=False: asynchronous on the stream)."""
     import torch
     n = _n_feats(feats)
     nf = ctypes.c_long()
     _check(load().ef_closure_infer(cl.handle, _field(feats, (n, 10), torch.float32, "feats"),
                                    _field(tau_out, (6, n), torch.float32, "tau_out"), n,
-                                   _field(exact_tau, (6, n), torch.float32, "exact_tau"), ctypes.byref(nf),
-                                   _stream(stream)))
-    return nf.value
+                                   _field(exact_tau, (6, n), torch.float32, "exact_tau"),
+                                   ctypes.byref(nf) if count else None, _stream(stream)))
+    return nf.value if count else None
+
+
+def closure_check_device_error(cl: Closure, stream=None) -> int:
+    """Read and clear the closure's device error word (0 = none)."""
+    return load().ef_closure_check_device_error(cl.handle, _stream(stream))
 
 
 def closure_param_count(cl: Closure) -> int:
