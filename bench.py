@@ -1,11 +1,13 @@
 """Benchmark: DNS points filtered (+ T_ij) per second on one GB300.
 
-Workload (default, the Re_tau ~ 180 channel shape): DNS 192 x 129 x 192 in a
-4 pi x 2 x 2 pi box, tanh-stretched y, filtered with a Gaussian of constant
-width Delta = Lx / 32 (wall extension of Eq. 7) onto a 32 x 33 x 32 LES grid;
-one step = ~bar(u_i), T_ij and the plane means of 10 seeded synthetic
-snapshots.  Inputs are 10 x 57 MB = 570 MB per step, larger than the 129 MB
-L2, so no flush is needed between steps.
+Workload (default, the Re_tau ~ 550 precision form): DNS 512 x 257 x 384 in
+a 2 pi x 2 x pi box, tanh-stretched y, filtered with a Gaussian of constant
+width Delta = Lx / 64 (wall extension of Eq. 7) onto a 64 x 65 x 48 LES grid
+with split-BF16 tensor-core contractions; one step = ~bar(u_i), T_ij and the
+plane means of 4 seeded synthetic snapshots.  Inputs are 4 x 607 MB = 2.4 GB
+per step, far larger than the 129 MB L2, so no flush is needed between
+steps.  `--workload re180` selects the 192 x 129 x 192 -> 32 x 33 x 32,
+Delta = Lx / 32 channel (10 snapshots per step).
 
 Output: one JSON line (rank 0).  `value` is whole-job throughput in DNS
 points per second with inputs resident in HBM; `e2e` is the same metric
@@ -14,9 +16,13 @@ inputs and outputs, the copies in and out overlapped with the compute of
 other snapshots) inside the timed region.  `roofline` reports the
 x-contraction kernel (the dominant phase) against the measured HBM copy
 bandwidth.  `cpu_baseline` times the CPU oracle on a bounded sample.
+`closure` reports the learned closure on the same workload: trained on the
+exact T_ij of snapshot 0, its error against the exact T_ij of snapshot 1 (a
+field of another seed), and tensor-core inference on 2^20 LES points with its
+roofline against the measured bf16 tensor peak.
 
 Multi-GPU: one process per GPU; snapshots are independent, so every rank
-filters its own 10 snapshots with no collective on the data path (weak
+filters its own snapshots with no collective on the data path (weak
 scaling, "replicas only").
 
 --impl reference times the CPU oracle (the only reference that exists for
@@ -61,6 +67,7 @@ def parse():
     ap.add_argument("--precision", default="bf16x3", choices=sorted(PREC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-closure", action="store_true")
     return ap.parse_args()
 
 
@@ -180,29 +187,99 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------- ours ----
-KERNEL_SOURCES = ("fused_stage.cuh", "tc_kernels.cu", "eles_internal.h")
+KERNEL_SOURCES = {"xz": ("fused_stage.cuh", "tc_kernels.cu", "eles_internal.h"),
+                  "closure": ("closure_tc.cu", "fused_stage.cuh", "eles_internal.h")}
 
 
-def kernel_source_hash():
+def kernel_source_hash(kind="xz"):
     import hashlib
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in KERNEL_SOURCES[kind]:
         h.update(open(os.path.join(ROOT, "paper_1902_02508_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(kernel_tag, points_per_launch):
+def traffic_from_profile(kernel_tag, points_per_launch, kind="xz"):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source; scaled from the captured launch's points to
     this launch's points (the traffic is proportional to the points read)."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.json")
     try:
         prof = json.load(open(path))
-        if prof.get("source_sha256_16") == kernel_source_hash():
+        if prof.get("source_sha256_16") == kernel_source_hash(kind):
             return prof["dram_bytes_per_point"] * points_per_launch
     except (OSError, ValueError, KeyError):
         pass
     return None
+
+
+CLOSURE_FLOP_PER_POINT = 2 * (10 * 128 + 128 * 128 + 128 * 128 + 128 * 6)   # 69,632: the four layers' MACs
+CLOSURE_POINTS = 1 << 20
+# The SiLU of the 384 hidden activations per point takes one ex2.approx and one
+# rcp.approx each; on GB300 these issue at 32 and 16 lanes per SM per clock
+# (throughput of independent chains, measured), so a point needs
+# 384 (1/32 + 1/16) = 36 SM-clocks of the special-function units.
+CLOSURE_SFU_CLK_PER_POINT = 384 * (1 / 32 + 1 / 16)
+
+
+def closure_measure(eles, torch, les, ub, tau, stream, timed, exact_ms_per_les_point, peaks, re_tau):
+    """The learned closure on this workload's exact stress: train on snapshot
+    0, report the error against the exact T_ij of snapshot 1 (a field of
+    another seed), and time tensor-core inference on 2^20 LES points."""
+    n = les.nx * les.ny * les.nz
+    feats = []
+    with torch.cuda.stream(stream):          # every tensor op below is ordered with the library calls
+        for s in (0, 1):
+            f = torch.empty((n, 10), device=ub.device)
+            eles.closure_features(les, ub[s].float().contiguous(), f, re_tau=re_tau, stream=stream)
+            feats.append(f)
+        t_ex = [tau[s].reshape(6, n).float().contiguous() for s in (0, 1)]
+    cl = eles.closure_create(batch=4096, lr=2e-3, seed=3)
+    t0 = time.perf_counter()
+    epochs = 15
+    loss = eles.closure_train(cl, feats[0], t_ex[0], epochs=epochs, stream=stream)
+    train_s = time.perf_counter() - t0
+    with torch.cuda.stream(stream):
+        pred = torch.empty((6, n), device=ub.device)
+        nfall = eles.closure_infer(cl, feats[1], pred, stream=stream)
+        diff = (pred.double() - t_ex[1].double())
+        rel = float(diff.norm() / t_ex[1].double().norm())
+        rel_c = [float(diff[q].norm() / t_ex[1][q].double().norm()) for q in range(6)]
+        # inference throughput: the held-out features repeated to 2^20 points
+        reps = (CLOSURE_POINTS + n - 1) // n
+        f1m = feats[1].repeat(reps, 1)[:CLOSURE_POINTS].contiguous()
+        out = torch.empty((6, CLOSURE_POINTS), device=ub.device)
+    torch.cuda.synchronize()
+    k = 20
+    ms = timed(lambda: eles.closure_infer(cl, f1m, out, stream=stream, count=False), k, 3) / k
+    assert eles.closure_check_device_error(cl, stream) == 0
+    tflops = CLOSURE_FLOP_PER_POINT * CLOSURE_POINTS / (ms / 1e3) / 1e12
+    tpeak = peaks.get("bf16_tflops", 1900.0)
+    nsm = torch.cuda.get_device_properties(ub.device).multi_processor_count
+    sm_hz = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    pts = CLOSURE_POINTS / (ms / 1e3)
+    sfu_peak = nsm * sm_hz / CLOSURE_SFU_CLK_PER_POINT
+    cl.close()
+    return {"workload": f"MLP 10-128-128-128-6 (SiLU) inference on {CLOSURE_POINTS} LES points "
+                        f"(features of the held-out snapshot, repeated)",
+            "ms_per_call": ms, "points_per_s": CLOSURE_POINTS / (ms / 1e3),
+            "precision": "BF16 weights, split-BF16 activations, FP32 accumulation (tcgen05, TMEM)",
+            "roofline": {"bound": "alu", "achieved": pts, "peak": sfu_peak, "unit": "points/s",
+                         "frac": pts / sfu_peak,
+                         "peak_source": f"SiLU on the special-function units: {nsm} SMs x {sm_hz / 1e6:.0f} MHz / "
+                                        f"{CLOSURE_SFU_CLK_PER_POINT:.0f} SM-clocks per point (ex2 32, rcp 16 "
+                                        f"lanes per SM per clock, measured)",
+                         "tensor": {"achieved": tflops, "peak": tpeak, "unit": "TFLOP/s", "frac": tflops / tpeak,
+                                    "peak_source": "measured bf16 burst" if "bf16_tflops" in peaks else "fallback",
+                                    "flop_per_point": CLOSURE_FLOP_PER_POINT},
+                         "traffic": traffic_from_profile("closure_mlp_tc_1m", CLOSURE_POINTS, "closure")},
+            "error_vs_exact": {"rel_l2": rel, "rel_l2_per_component": rel_c, "no_model_rel_l2": 1.0,
+                               "tau_order": ["11", "12", "13", "22", "23", "33"],
+                               "train": f"snapshot 0 ({n} LES points), {epochs} epochs, {train_s:.1f} s, "
+                                        f"final loss {loss:.4f} (standardised)",
+                               "test": "snapshot 1 (another seed)", "guarded_points": nfall},
+            "speedup_vs_exact_per_les_point": exact_ms_per_les_point / (ms / CLOSURE_POINTS),
+            "gpu_launches_per_call": 2}
 
 
 def main():
@@ -315,6 +392,15 @@ def main():
         del u64
         p64.close()
 
+    # --- the learned closure (trained on this workload's exact stress)
+    from_json = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    closure = None
+    if not args.no_closure and ns >= 2:
+        closure = closure_measure(eles, torch, les, ub, tau, stream, timed,
+                                  (ms / args.steps) / (ns * les.nx * les.ny * les.nz), from_json,
+                                  180.0 if args.workload == "re180" else 550.0)
+
     # --- accuracy at the stated tolerance: snapshot 0 against the CPU oracle
     err = None
     cpu = None
@@ -330,8 +416,6 @@ def main():
             cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     # --- roofline of the dominant phase (x-contraction: it alone reads the input)
-    from_json = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = from_json.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in from_json else "fallback"
     xz_ms = phase_ms[0] / max(calls, 1)
@@ -359,7 +443,7 @@ def main():
                 "data": "synthetic (seeded solenoidal channel fields, Reichardt mean profile)",
                 "config": workload_config(args.workload, args.precision),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64,
-                "accuracy": err, "clocks": clk.summary(),
+                "accuracy": err, "closure": closure, "clocks": clk.summary(),
                 "gpu_launches": per_call_launches * args.steps,
                 "x_variant": eles.plan_info(plan, 10)}
         print(json.dumps(line), flush=True)
