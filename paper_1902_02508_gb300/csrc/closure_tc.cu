@@ -13,19 +13,19 @@
 // the FP32-activation network the training passes evaluate, to a few parts
 // in 10^6, not a BF16-activation approximation of it.
 //
-// Layout: shared memory holds only the weight image, every matrix in the
-// K-major no-swizzle canonical layout of tcgen05 (8 x 8 BF16 core matrices of
-// 128 contiguous bytes, core (r/8, k/8) at ((r/8)(K/8) + k/8) * 128 bytes,
-// i.e. leading (K) byte offset 128 and stride (row-group) byte offset
-// K * 16).  The activations stay in tensor memory: per tile slot, 128 FP32
-// accumulator columns and the A operand of the next layer (a_hi and a_lo,
-// two BF16 per 32-bit column, 64 columns each), written by the epilogue with
-// tcgen05.st and read by the MMA from TMEM.  Two slots of eight warps each
-// fill the 512 TMEM columns: the MMAs of one slot's layer run while the other
-// slot's warps do their epilogue.  Warp w owns TMEM lanes (rows)
-// 32 (w % 4) .. +31, one row per thread, and the two warps of a slot on the
-// same lanes take 64 columns each, so every thread carries its point from
-// the features to the output.
+// Layout: shared memory holds the weight image, every matrix in the K-major
+// no-swizzle canonical layout of tcgen05 (8 x 8 BF16 core matrices of 128
+// contiguous bytes, core (r/8, k/8) at ((r/8)(K/8) + k/8) * 128 bytes, i.e.
+// leading (K) byte offset 128 and stride (row-group) byte offset K * 16).
+// Three tile slots of eight warps each keep three tiles in flight: each has
+// 128 FP32 accumulator columns in TMEM, and the next layer's A operand (a_hi,
+// a_lo) lives in shared memory for slots 0 and 1 (same layout, 64 KB each)
+// and in the remaining 128 TMEM columns for slot 2 (two BF16 per 32-bit
+// column, written with tcgen05.st and read by the MMA from TMEM).  The MMAs
+// of one slot's layer run while the other slots' warps do their epilogues.
+// Warp w owns TMEM lanes (rows) 32 (w % 4) .. +31, one row per thread, and
+// the two warps of a slot on the same lanes take 64 columns each, so every
+// thread carries its point from the features to the output.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -51,11 +51,17 @@ constexpr int kImgStats = kImgBias + 4 * (3 * kHid + kN3); // float mu[16] inv_s
 constexpr int kImgBytes = kImgStats + 4 * 48;
 static_assert(kImgBytes % 128 == 0, "image must keep the operand buffers 128-byte aligned");
 
-constexpr int kBarOff = kImgBytes;
-constexpr int kSmemBytes = kBarOff + 32;                   // 2 mbarriers, TMEM address, 2 abort flags
-constexpr int kThreads = 512;                              // 2 slots x 8 warps
-constexpr unsigned kTmemCols = 512;                        // per slot: D [0,128), a_hi [128,192), a_lo [192,256)
-constexpr unsigned kSlotCols = 256, kAhiCol = 128, kAloCol = 192;
+constexpr int kSlots = 3;
+constexpr int kSmemSlots = 2;                              // slots 0, 1: A operand in shared memory
+constexpr int kOperandBytes = kRows * kHid * 2;            // one of a_hi, a_lo: 128 x 128 BF16
+constexpr int kAOff = kImgBytes;
+constexpr int kBarOff = kAOff + kSmemSlots * 2 * kOperandBytes;
+constexpr int kSmemBytes = kBarOff + 64;                   // 3 mbarriers, TMEM address, 3 abort flags
+constexpr int kSlotThreads = 256;                          // 8 warps per slot
+constexpr int kThreads = kSlots * kSlotThreads;
+constexpr unsigned kTmemCols = 512;                        // D of slot g at [128 g, 128 g + 128); slot 2's
+constexpr unsigned kAhiCol = 384, kAloCol = 448;           // a_hi at [384, 448), a_lo at [448, 512)
+static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 
 __host__ __device__ constexpr int core_off(int r, int k, int K)
 {
@@ -76,6 +82,14 @@ __host__ __device__ constexpr unsigned idesc_bf16(int M, int N)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
 }
+// D (+)= A B, A and B from shared memory (descriptors).
+__device__ __forceinline__ void mma_bf16_ss(unsigned dtmem, unsigned long long a, unsigned long long b, unsigned id,
+                                            unsigned acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 ::"r"(dtmem), "l"(a), "l"(b), "r"(id), "r"(acc));
+}
 // D (+)= A B with A read from tensor memory (a_tmem: lane 0, first column)
 // and B from shared memory (descriptor).
 __device__ __forceinline__ void mma_bf16_ts(unsigned dtmem, unsigned a_tmem, unsigned long long b, unsigned id,
@@ -93,24 +107,22 @@ __device__ __forceinline__ void mma_commit(unsigned long long *bar)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
-// 32 consecutive FP32 columns of this thread's TMEM lane; the wait carries
-// the registers so that no use of them is scheduled before it.
-__device__ __forceinline__ void tmem_ld32(unsigned taddr, unsigned (&v)[32])
+// 16 consecutive FP32 columns of this thread's TMEM lane: the load is
+// issued here and completes at tmem_ld16_wait, which carries the registers
+// so that no use of them is scheduled before it (a wait covers every load
+// issued before it).
+__device__ __forceinline__ void tmem_ld16_issue(unsigned taddr, unsigned (&v)[16])
 {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
                  : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                   "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                   "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
                  : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld16_wait(unsigned (&v)[16])
+{
     asm volatile("tcgen05.wait::ld.sync.aligned;\n"
                  : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
-                   "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]),
-                   "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]),
-                   "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]),
-                   "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
+                   "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
                  :: "memory");
 }
 __device__ __forceinline__ void tmem_ld8(unsigned taddr, unsigned (&v)[8])
@@ -123,11 +135,10 @@ __device__ __forceinline__ void tmem_ld8(unsigned taddr, unsigned (&v)[8])
                  :: "memory");
 }
 
-__device__ __forceinline__ void tmem_st16(unsigned taddr, const unsigned (&v)[16])
+__device__ __forceinline__ void tmem_st8(unsigned taddr, const unsigned (&v)[8])
 {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n"
-                 ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
-                   "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n"
+                 ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
                  : "memory");
 }
 __device__ __forceinline__ void tmem_st4(unsigned taddr, const unsigned (&v)[4])
@@ -212,18 +223,70 @@ __global__ void pack_image(const float *__restrict__ wq, long w0, long b0, long 
 constexpr int kImgElems = kHid * kK0 + 2 * kHid * kHid + kN3 * kHid + 3 * kHid + kN3 + 48;
 
 // ------------------------------------------------------------ the kernel --
-// Slot g (warps 8g .. 8g+7) handles tiles g, g + 2 G, ... of CTA b's
-// sequence 2 (b + k G) + g (G CTAs).  The two warps of a TMEM lane quadrant
-// split the 128 columns of the epilogue.  Per tile: inputs -> MMA layer 0 ->
+// Slot g (warps 8g .. 8g+7) handles tiles g, g + 3 G, ... of CTA b's
+// sequence 3 (b + k G) + g (G CTAs).  The two warps of a TMEM lane quadrant
+// split the 128 columns of the epilogue.  Slots 0 and 1 keep the A operand
+// in shared memory, slot 2 in tensor memory (512 columns hold three
+// accumulators and one hi/lo operand).  Per tile: inputs -> MMA layer 0 ->
 // (wait, epilogue, MMA) x 3 -> wait -> output; the next tile's features are
 // fetched while the four layers run.  Every wait is bounded; on expiry the
 // slot records EF_ERR_TIMEOUT and stops, and the CTA frees its TMEM.
-constexpr int kSlotThreads = 256;
 
 __device__ __forceinline__ void load_feats(const float *__restrict__ feats, long p, long n, float (&f)[kIn])
 {
 #pragma unroll
     for (int k = 0; k < kIn; k++) f[k] = p < n ? __ldg(feats + p * kIn + k) : 0.f;
+}
+
+// bias, SiLU and split of 16 accumulator columns (8 pairs)
+__device__ __forceinline__ void act16(const unsigned (&v)[16], const float2 *b2, unsigned (&hw)[8], unsigned (&lw)[8])
+{
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const float2 z = __fadd2_rn(make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])), b2[j]);
+        split2(silu2(z), hw[j], lw[j]);
+    }
+}
+
+// Epilogue of one thread over its 64 accumulator columns [c0, c0 + 64):
+// four pieces of 16, the TMEM load of the next piece in flight while one is
+// computed.  tl_d: the warp's lanes at the slot's accumulator; tl_a: the
+// warp's lanes at column 0 (the TMEM operand columns are absolute).  The
+// hi/lo words go to the slot's operand in TMEM (kTmemA) or shared memory.
+template <bool kTmemA>
+__device__ __forceinline__ void epilogue64(unsigned tl_d, unsigned tl_a, int c0, const float2 *b2,
+                                           unsigned char *Ahi, unsigned char *Alo, int r)
+{
+    unsigned va[16], vb[16], hw[8], lw[8];
+    auto put = [&](int piece) {
+        const int k = c0 + 16 * piece;                 // next layer's k of these 16 activations
+        if (kTmemA) {
+            tmem_st8(tl_a + kAhiCol + k / 2, hw);
+            tmem_st8(tl_a + kAloCol + k / 2, lw);
+        } else {
+            *reinterpret_cast<uint4 *>(Ahi + core_off(r, k, kHid)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4 *>(Ahi + core_off(r, k + 8, kHid)) = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+            *reinterpret_cast<uint4 *>(Alo + core_off(r, k, kHid)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            *reinterpret_cast<uint4 *>(Alo + core_off(r, k + 8, kHid)) = make_uint4(lw[4], lw[5], lw[6], lw[7]);
+        }
+    };
+    const unsigned src = tl_d + c0;
+    tmem_ld16_issue(src, va);
+    tmem_ld16_wait(va);
+    tmem_ld16_issue(src + 16, vb);
+    act16(va, b2, hw, lw);
+    put(0);
+    tmem_ld16_wait(vb);
+    tmem_ld16_issue(src + 32, va);
+    act16(vb, b2 + 8, hw, lw);
+    put(1);
+    tmem_ld16_wait(va);
+    tmem_ld16_issue(src + 48, vb);
+    act16(va, b2 + 16, hw, lw);
+    put(2);
+    tmem_ld16_wait(vb);
+    act16(vb, b2 + 24, hw, lw);
+    put(3);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -235,13 +298,13 @@ closure_mlp_tc_kernel(const uint4 *__restrict__ img, const float *__restrict__ f
     const int g = warp >> 3, quad = warp & 3, half = (warp >> 2) & 1, r = 32 * quad + lane;
     for (int i = tid; i < kImgBytes / 16; i += kThreads) reinterpret_cast<uint4 *>(sm)[i] = img[i];
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(sm + kBarOff);
-    unsigned *tmem_holder = reinterpret_cast<unsigned *>(sm + kBarOff + 16);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + kBarOff + 24);
+    unsigned *tmem_holder = reinterpret_cast<unsigned *>(sm + kBarOff + 8 * kSlots);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + kBarOff + 8 * kSlots + 4);
     if (tid == 0) {
-        fz::mbar_init(&bar[0], 1);
-        fz::mbar_init(&bar[1], 1);
-        abort_flag[0] = 0;
-        abort_flag[1] = 0;
+        for (int k = 0; k < kSlots; k++) {
+            fz::mbar_init(&bar[k], 1);
+            abort_flag[k] = 0;
+        }
         fz::mbar_fence_init();
     }
     if (warp == 0) {
@@ -254,13 +317,16 @@ closure_mlp_tc_kernel(const uint4 *__restrict__ img, const float *__restrict__ f
     __syncthreads();
     tc_fence_after();
     const unsigned tmem = *tmem_holder;
-    const unsigned dslot = tmem + kSlotCols * g;                  // this slot's accumulator (lane 0)
+    const bool tmemA = g == kSmemSlots;                          // this slot's operand lives in TMEM
+    const unsigned dslot = tmem + kRows * g;                     // this slot's accumulator (lane 0)
     const unsigned tlane = dslot + ((unsigned)(32 * quad) << 16);  // this warp's lanes
+    const unsigned tlane_a = tmem + ((unsigned)(32 * quad) << 16); // the same lanes, column 0 (operand base)
+    unsigned char *Ahi = sm + kAOff + (tmemA ? 0 : g) * 2 * kOperandBytes, *Alo = Ahi + kOperandBytes;
     const float *bias = reinterpret_cast<const float *>(sm + kImgBias);
     const float *st = reinterpret_cast<const float *>(sm + kImgStats);
     const bool issuer = (tid & (kSlotThreads - 1)) == 0;
     const int barid = 1 + g;
-    const unsigned sImg = fz::smem_u32(sm);
+    const unsigned sA_hi = fz::smem_u32(Ahi), sA_lo = fz::smem_u32(Alo), sImg = fz::smem_u32(sm);
     constexpr unsigned id128 = idesc_bf16(kRows, kHid), id16 = idesc_bf16(kRows, kN3);
     unsigned phase = 0;
 
@@ -273,17 +339,35 @@ closure_mlp_tc_kernel(const uint4 *__restrict__ img, const float *__restrict__ f
         tc_fence_after();
         return abort_flag[g] == 0;
     };
-    // the A operand written by every thread is complete before the MMA is issued
+    // the A operand written by every thread (TMEM or shared memory) is
+    // complete and visible to the tensor core before the MMA is issued
     auto operand_ready = [&]() {
-        tmem_wait_st();
+        if (tmemA) tmem_wait_st();
+        else fz::proxy_fence();
         tc_fence_before();
         slot_sync();
     };
+    // one layer's MMAs: K = 16 ks-steps of hi and of lo, B from the image
+    auto issue = [&](unsigned wofs, int ksteps, unsigned sbo, unsigned id) {
+        tc_fence_after();
+#pragma unroll 1
+        for (int ks = 0; ks < ksteps; ks++) {
+            const unsigned long long bw = sdesc(sImg + wofs + 256 * ks, 128, sbo);
+            if (tmemA) {
+                mma_bf16_ts(dslot, tmem + kAhiCol + 8 * ks, bw, id, ks > 0 ? 1u : 0u);
+                mma_bf16_ts(dslot, tmem + kAloCol + 8 * ks, bw, id, 1u);
+            } else {
+                mma_bf16_ss(dslot, sdesc(sA_hi + 256 * ks, 128, sbo), bw, id, ks > 0 ? 1u : 0u);
+                mma_bf16_ss(dslot, sdesc(sA_lo + 256 * ks, 128, sbo), bw, id, 1u);
+            }
+        }
+        mma_commit(&bar[g]);
+    };
 
-    long t = g + 2L * blockIdx.x;
+    long t = g + (long)kSlots * blockIdx.x;
     float f[kIn];
     load_feats(feats, t * kRows + r, n, f);
-    for (; t < ntiles; t += 2L * gridDim.x) {
+    for (; t < ntiles; t += (long)kSlots * gridDim.x) {
         const long p = t * kRows + r;
         const bool valid = p < n;
         // standardised inputs and the guard; each half writes 8 of the 16 k
@@ -304,56 +388,31 @@ closure_mlp_tc_kernel(const uint4 *__restrict__ img, const float *__restrict__ f
                 const float2 a = half ? make_float2(h[8 + 2 * i], h[9 + 2 * i]) : make_float2(h[2 * i], h[2 * i + 1]);
                 split2(a, hv[i], lv[i]);
             }
-            tmem_st4(tlane + kAhiCol + 4 * half, hv);
-            tmem_st4(tlane + kAloCol + 4 * half, lv);
+            if (tmemA) {
+                tmem_st4(tlane_a + kAhiCol + 4 * half, hv);
+                tmem_st4(tlane_a + kAloCol + 4 * half, lv);
+            } else {
+                *reinterpret_cast<uint4 *>(Ahi + core_off(r, 8 * half, kK0)) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                *reinterpret_cast<uint4 *>(Alo + core_off(r, 8 * half, kK0)) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+            }
         }
         if (half == 0) {
             const unsigned ballot = __ballot_sync(0xffffffffu, out);
             if (lane == 0 && ballot) atomicAdd(nfall, __popc(ballot));
         }
         operand_ready();
-        if (issuer) {
-            tc_fence_after();
-            const unsigned long long bw = sdesc(sImg + kImgW0, 128, kK0 * 16);
-            mma_bf16_ts(dslot, dslot + kAhiCol, bw, id128, 0);
-            mma_bf16_ts(dslot, dslot + kAloCol, bw, id128, 1);
-            mma_commit(&bar[g]);
-        }
-        load_feats(feats, (t + 2L * gridDim.x) * kRows + r, n, f);   // the next tile's, in flight meanwhile
+        if (issuer) issue(kImgW0, 1, kK0 * 16, id128);
+        load_feats(feats, (t + (long)kSlots * gridDim.x) * kRows + r, n, f);   // the next tile's, in flight meanwhile
         bool ok = true;
         for (int l = 1; l < 4 && ok; l++) {
             ok = slot_wait();
             if (!ok) break;
             // epilogue of hidden layer l - 1: bias, SiLU, split into the next A operand
-            const float2 *b2 = reinterpret_cast<const float2 *>(bias + (l - 1) * kHid);
-#pragma unroll 1
-            for (int cc = 0; cc < 2; cc++) {
-                const int c = 2 * half + cc;
-                unsigned v[32];
-                tmem_ld32(tlane + 32 * c, v);
-                unsigned hw[16], lw[16];
-#pragma unroll
-                for (int j = 0; j < 16; j++) {
-                    const float2 z = __fadd2_rn(make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])),
-                                                b2[16 * c + j]);
-                    split2(silu2(z), hw[j], lw[j]);
-                }
-                tmem_st16(tlane + kAhiCol + 16 * c, hw);
-                tmem_st16(tlane + kAloCol + 16 * c, lw);
-            }
+            const float2 *b2 = reinterpret_cast<const float2 *>(bias + (l - 1) * kHid) + 32 * half;
+            if (tmemA) epilogue64<true>(tlane, tlane_a, 64 * half, b2, Ahi, Alo, r);
+            else epilogue64<false>(tlane, tlane_a, 64 * half, b2, Ahi, Alo, r);
             operand_ready();
-            if (issuer) {
-                tc_fence_after();
-                const unsigned wbase = sImg + (l == 1 ? kImgW1 : l == 2 ? kImgW2 : kImgW3);
-                const unsigned id = l == 3 ? id16 : id128;
-#pragma unroll 1
-                for (int ks = 0; ks < kHid / 16; ks++) {
-                    const unsigned long long bw = sdesc(wbase + 256 * ks, 128, kHid * 16);
-                    mma_bf16_ts(dslot, dslot + kAhiCol + 8 * ks, bw, id, ks > 0 ? 1u : 0u);
-                    mma_bf16_ts(dslot, dslot + kAloCol + 8 * ks, bw, id, 1u);
-                }
-                mma_commit(&bar[g]);
-            }
+            if (issuer) issue(l == 1 ? kImgW1 : l == 2 ? kImgW2 : kImgW3, kHid / 16, kHid * 16, l == 3 ? id16 : id128);
         }
         if (!ok || !slot_wait()) break;
         unsigned v[8];
@@ -397,7 +456,7 @@ int closure_infer_tc(const float *wq, const long *off_w, const long *off_b, cons
     pack_image<<<(kImgElems + 255) / 256, 256, 0, s>>>(wq, off_w[0], off_b[0], off_w[1], off_b[1], off_w[2], off_b[2],
                                                       off_w[3], off_b[3], stats, static_cast<unsigned char *>(image));
     const long ntiles = (n + kRows - 1) / kRows;
-    const long want = (ntiles + 1) / 2;
+    const long want = (ntiles + kSlots - 1) / kSlots;
     const int grid = (int)(want < nsm ? want : nsm);
     closure_mlp_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(static_cast<const uint4 *>(image), feats, n, ntiles, guard,
                                                        exact, tau, nfall, err);

@@ -12,7 +12,7 @@ BF16-rounded weights and the same standardisation:
   the exact stress returned at exactly those points.
 
 Tolerance (standardised units, relative to max |Y|): each activation keeps
-16 significant bits (|a - a_hi - a_lo| <= 2^-17 |a|), sums of 128 products
+16 significant bits (|a - a_hi - a_lo| <= 2^-16 |a|), sums of 128 products
 accumulate in FP32 (<= 128 * 2^-24 relative to the sum of magnitudes), and
 SiLU uses the fast exponential and division (a few ulp); four layers of
 that stay below 1e-5 of the output scale for weights of unit gain, so the
