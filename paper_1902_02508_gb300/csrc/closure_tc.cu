@@ -9,7 +9,7 @@
 // training kernels use) and enter the MMA exactly.  Every activation a is
 // split into a_hi = bf16(a) and a_lo = bf16(a - a_hi), both multiplied by the
 // weights with FP32 accumulation in TMEM, so an activation keeps 16
-// significant bits (|a - a_hi - a_lo| <= 2^-17 |a|): the served network is
+// significant bits (|a - a_hi - a_lo| <= 2^-16 |a|): the served network is
 // the FP32-activation network the training passes evaluate, to a few parts
 // in 10^6, not a BF16-activation approximation of it.
 //
@@ -29,6 +29,8 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "eles_internal.h"
 #include "fused_stage.cuh"
 
@@ -39,15 +41,15 @@ constexpr int kRows = 128;                  // points per tile (MMA M)
 constexpr int kHid = 128;                   // hidden width
 constexpr int kIn = 10, kOut = 6;
 constexpr int kK0 = 16;                     // first-layer K, padded
-constexpr int kN3 = 16;                     // last-layer N, padded (MMA N >= 16 for M = 128)
+constexpr int kW3Row = 8;                   // output-layer weights, FP32 [k][8] (6 used)
 
 // weight image (bytes); the same image is the device buffer and the head of shared memory
 constexpr int kImgW0 = 0;                                  // [128][16]
 constexpr int kImgW1 = kImgW0 + kHid * kK0 * 2;            // [128][128]
 constexpr int kImgW2 = kImgW1 + kHid * kHid * 2;           // [128][128]
-constexpr int kImgW3 = kImgW2 + kHid * kHid * 2;           // [16][128]
-constexpr int kImgBias = kImgW3 + kN3 * kHid * 2;          // float b0[128] b1[128] b2[128] b3[16]
-constexpr int kImgStats = kImgBias + 4 * (3 * kHid + kN3); // float mu[16] inv_sd[16] tmu[8] tsd[8]
+constexpr int kImgW3 = kImgW2 + kHid * kHid * 2;           // float [128][8]
+constexpr int kImgBias = kImgW3 + kHid * kW3Row * 4;       // float b0[128] b1[128] b2[128] b3[16]
+constexpr int kImgStats = kImgBias + 4 * (3 * kHid + 16);  // float mu[16] inv_sd[16] tmu[8] tsd[8]
 constexpr int kImgBytes = kImgStats + 4 * 48;
 static_assert(kImgBytes % 128 == 0, "image must keep the operand buffers 128-byte aligned");
 
@@ -55,7 +57,9 @@ constexpr int kSlots = 3;
 constexpr int kSmemSlots = 2;                              // slots 0, 1: A operand in shared memory
 constexpr int kOperandBytes = kRows * kHid * 2;            // one of a_hi, a_lo: 128 x 128 BF16
 constexpr int kAOff = kImgBytes;
-constexpr int kBarOff = kAOff + kSmemSlots * 2 * kOperandBytes;
+constexpr int kXOff = kAOff + kSmemSlots * 2 * kOperandBytes;   // output-layer partials exchanged by the halves
+constexpr int kXBytes = kSlots * 2 * kRows * 16;           // [slot][half][row][4] floats
+constexpr int kBarOff = kXOff + kXBytes;
 constexpr int kSmemBytes = kBarOff + 64;                   // 3 mbarriers, TMEM address, 3 abort flags
 constexpr int kSlotThreads = 256;                          // 8 warps per slot
 constexpr int kThreads = kSlots * kSlotThreads;
@@ -125,16 +129,6 @@ __device__ __forceinline__ void tmem_ld16_wait(unsigned (&v)[16])
                    "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
                  :: "memory");
 }
-__device__ __forceinline__ void tmem_ld8(unsigned taddr, unsigned (&v)[8])
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
-                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7])
-                 :: "memory");
-}
-
 __device__ __forceinline__ void tmem_st8(unsigned taddr, const unsigned (&v)[8])
 {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n"
@@ -189,7 +183,7 @@ __global__ void pack_image(const float *__restrict__ wq, long w0, long b0, long 
                            long w3, long b3, const double *__restrict__ stats, unsigned char *img)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nw = kHid * kK0 + 2 * kHid * kHid + kN3 * kHid;
+    const int nw = kHid * kK0 + 2 * kHid * kHid + kHid * kW3Row;
     auto bits = [&](float v) { return (unsigned short)(__float_as_uint(v) >> 16); };
     if (i < kHid * kK0) {                                       // W0 [128][16], k >= 10 zero
         const int r = i / kK0, k = i % kK0;
@@ -200,18 +194,17 @@ __global__ void pack_image(const float *__restrict__ wq, long w0, long b0, long 
         const int r = e / kHid, k = e % kHid;
         const float v = wq[(l ? w2 : w1) + (long)r * kHid + k];
         *reinterpret_cast<unsigned short *>(img + (l ? kImgW2 : kImgW1) + core_off(r, k, kHid)) = bits(v);
-    } else if (i < nw) {                                        // W3 [16][128], rows >= 6 zero
-        const int e = i - kHid * kK0 - 2 * kHid * kHid, r = e / kHid, k = e % kHid;
-        const float v = r < kOut ? wq[w3 + (long)r * kHid + k] : 0.f;
-        *reinterpret_cast<unsigned short *>(img + kImgW3 + core_off(r, k, kHid)) = bits(v);
-    } else if (i < nw + 3 * kHid + kN3) {                       // biases
+    } else if (i < nw) {                                        // W3 as FP32 [k][8], q >= 6 zero
+        const int e = i - kHid * kK0 - 2 * kHid * kHid, k = e / kW3Row, q = e % kW3Row;
+        reinterpret_cast<float *>(img + kImgW3)[e] = q < kOut ? wq[w3 + (long)q * kHid + k] : 0.f;
+    } else if (i < nw + 3 * kHid + 16) {                        // biases
         const int e = i - nw;
         float v;
         if (e < 3 * kHid) v = wq[(e < kHid ? b0 : e < 2 * kHid ? b1 : b2) + e % kHid];
         else v = e - 3 * kHid < kOut ? wq[b3 + e - 3 * kHid] : 0.f;
         reinterpret_cast<float *>(img + kImgBias)[e] = v;
-    } else if (i < nw + 3 * kHid + kN3 + 48) {                  // statistics
-        const int e = i - nw - 3 * kHid - kN3;
+    } else if (i < nw + 3 * kHid + 16 + 48) {                   // statistics
+        const int e = i - nw - 3 * kHid - 16;
         float v = 0.f;
         if (e < kIn) v = (float)stats[e];                                  // feature means
         else if (e >= 16 && e < 16 + kIn) v = (float)(1.0 / stats[10 + e - 16]);   // 1 / feature sd
@@ -220,7 +213,7 @@ __global__ void pack_image(const float *__restrict__ wq, long w0, long b0, long 
         reinterpret_cast<float *>(img + kImgStats)[e] = v;
     }
 }
-constexpr int kImgElems = kHid * kK0 + 2 * kHid * kHid + kN3 * kHid + 3 * kHid + kN3 + 48;
+constexpr int kImgElems = kHid * kK0 + 2 * kHid * kHid + kHid * kW3Row + 3 * kHid + 16 + 48;
 
 // ------------------------------------------------------------ the kernel --
 // Slot g (warps 8g .. 8g+7) handles tiles g, g + 3 G, ... of CTA b's
@@ -289,6 +282,47 @@ __device__ __forceinline__ void epilogue64(unsigned tl_d, unsigned tl_a, int c0,
     put(3);
 }
 
+// Epilogue of the last hidden layer fused with the output layer, on the CUDA
+// cores in FP32: y_q += sum over the thread's 64 columns k of W3[q][k] a_k
+// with the activations unsplit.  y holds (y0, y1), (y2, y3), (y4, y5).
+__device__ __forceinline__ void epilogue64_out(unsigned tl_d, int c0, const float2 *b2, const float *w3,
+                                               float2 (&y)[3])
+{
+    unsigned va[16], vb[16];
+    auto acc16 = [&](const unsigned (&v)[16], int piece) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const float2 z = __fadd2_rn(make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])),
+                                        b2[8 * piece + j]);
+            const float2 a = silu2(z);
+            const float *w = w3 + (c0 + 16 * piece + 2 * j) * kW3Row;
+#pragma unroll
+            for (int e = 0; e < 2; e++) {
+                const float ae = e ? a.y : a.x;
+                const float4 w0 = *reinterpret_cast<const float4 *>(w + e * kW3Row);
+                const float2 w1 = *reinterpret_cast<const float2 *>(w + e * kW3Row + 4);
+                const float2 aa = make_float2(ae, ae);
+                y[0] = __ffma2_rn(make_float2(w0.x, w0.y), aa, y[0]);
+                y[1] = __ffma2_rn(make_float2(w0.z, w0.w), aa, y[1]);
+                y[2] = __ffma2_rn(w1, aa, y[2]);
+            }
+        }
+    };
+    const unsigned src = tl_d + c0;
+    tmem_ld16_issue(src, va);
+    tmem_ld16_wait(va);
+    tmem_ld16_issue(src + 16, vb);
+    acc16(va, 0);
+    tmem_ld16_wait(vb);
+    tmem_ld16_issue(src + 32, va);
+    acc16(vb, 1);
+    tmem_ld16_wait(va);
+    tmem_ld16_issue(src + 48, vb);
+    acc16(va, 2);
+    tmem_ld16_wait(vb);
+    acc16(vb, 3);
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
 closure_mlp_tc_kernel(const uint4 *__restrict__ img, const float *__restrict__ feats, long n, long ntiles,
                       float guard, const float *__restrict__ exact, float *__restrict__ tau, int *nfall, int *err)
@@ -327,7 +361,9 @@ closure_mlp_tc_kernel(const uint4 *__restrict__ img, const float *__restrict__ f
     const bool issuer = (tid & (kSlotThreads - 1)) == 0;
     const int barid = 1 + g;
     const unsigned sA_hi = fz::smem_u32(Ahi), sA_lo = fz::smem_u32(Alo), sImg = fz::smem_u32(sm);
-    constexpr unsigned id128 = idesc_bf16(kRows, kHid), id16 = idesc_bf16(kRows, kN3);
+    constexpr unsigned id128 = idesc_bf16(kRows, kHid);
+    const float *w3 = reinterpret_cast<const float *>(sm + kImgW3);
+    float *xch = reinterpret_cast<float *>(sm + kXOff) + (size_t)g * 2 * kRows * 4;   // [half][row][4]
     unsigned phase = 0;
 
     auto slot_sync = [&]() { asm volatile("bar.sync %0, %1;\n" ::"r"(barid), "r"(kSlotThreads) : "memory"); };
@@ -347,18 +383,24 @@ closure_mlp_tc_kernel(const uint4 *__restrict__ img, const float *__restrict__ f
         tc_fence_before();
         slot_sync();
     };
-    // one layer's MMAs: K = 16 ks-steps of hi and of lo, B from the image
-    auto issue = [&](unsigned wofs, int ksteps, unsigned sbo, unsigned id) {
+    // One layer's MMAs over KS k-steps of 16, hi and lo, B from the image.
+    // A k-step advances a descriptor's start address by 256 bytes (16 in its
+    // encoded low field) and a TMEM operand by 8 columns; the base
+    // descriptors are fixed for the kernel.
+    const unsigned long long dA0hi = sdesc(sA_hi, 128, kK0 * 16), dA0lo = sdesc(sA_lo, 128, kK0 * 16);
+    const unsigned long long dAhi = sdesc(sA_hi, 128, kHid * 16), dAlo = sdesc(sA_lo, 128, kHid * 16);
+    const unsigned long long dW0 = sdesc(sImg + kImgW0, 128, kK0 * 16);
+    const unsigned long long dW1 = sdesc(sImg + kImgW1, 128, kHid * 16), dW2 = sdesc(sImg + kImgW2, 128, kHid * 16);
+    auto issue = [&](auto ksteps, unsigned long long bw, unsigned long long ahi, unsigned long long alo) {
         tc_fence_after();
-#pragma unroll 1
-        for (int ks = 0; ks < ksteps; ks++) {
-            const unsigned long long bw = sdesc(sImg + wofs + 256 * ks, 128, sbo);
+#pragma unroll
+        for (int ks = 0; ks < decltype(ksteps)::value; ks++) {
             if (tmemA) {
-                mma_bf16_ts(dslot, tmem + kAhiCol + 8 * ks, bw, id, ks > 0 ? 1u : 0u);
-                mma_bf16_ts(dslot, tmem + kAloCol + 8 * ks, bw, id, 1u);
+                mma_bf16_ts(dslot, tmem + kAhiCol + 8 * ks, bw + 16 * ks, id128, ks > 0 ? 1u : 0u);
+                mma_bf16_ts(dslot, tmem + kAloCol + 8 * ks, bw + 16 * ks, id128, 1u);
             } else {
-                mma_bf16_ss(dslot, sdesc(sA_hi + 256 * ks, 128, sbo), bw, id, ks > 0 ? 1u : 0u);
-                mma_bf16_ss(dslot, sdesc(sA_lo + 256 * ks, 128, sbo), bw, id, 1u);
+                mma_bf16_ss(dslot, ahi + 16 * ks, bw + 16 * ks, id128, ks > 0 ? 1u : 0u);
+                mma_bf16_ss(dslot, alo + 16 * ks, bw + 16 * ks, id128, 1u);
             }
         }
         mma_commit(&bar[g]);
@@ -401,10 +443,10 @@ closure_mlp_tc_kernel(const uint4 *__restrict__ img, const float *__restrict__ f
             if (lane == 0 && ballot) atomicAdd(nfall, __popc(ballot));
         }
         operand_ready();
-        if (issuer) issue(kImgW0, 1, kK0 * 16, id128);
+        if (issuer) issue(std::integral_constant<int, 1>(), dW0, dA0hi, dA0lo);
         load_feats(feats, (t + (long)kSlots * gridDim.x) * kRows + r, n, f);   // the next tile's, in flight meanwhile
         bool ok = true;
-        for (int l = 1; l < 4 && ok; l++) {
+        for (int l = 1; l < 3 && ok; l++) {
             ok = slot_wait();
             if (!ok) break;
             // epilogue of hidden layer l - 1: bias, SiLU, split into the next A operand
@@ -412,18 +454,29 @@ closure_mlp_tc_kernel(const uint4 *__restrict__ img, const float *__restrict__ f
             if (tmemA) epilogue64<true>(tlane, tlane_a, 64 * half, b2, Ahi, Alo, r);
             else epilogue64<false>(tlane, tlane_a, 64 * half, b2, Ahi, Alo, r);
             operand_ready();
-            if (issuer) issue(l == 1 ? kImgW1 : l == 2 ? kImgW2 : kImgW3, kHid / 16, kHid * 16, l == 3 ? id16 : id128);
+            if (issuer) issue(std::integral_constant<int, kHid / 16>(), l == 1 ? dW1 : dW2, dAhi, dAlo);
         }
         if (!ok || !slot_wait()) break;
-        unsigned v[8];
-        tmem_ld8(tlane, v);
-        if (valid) {
-            const bool fall = out && exact != nullptr;
+        // last hidden layer and the output layer; the halves exchange their
+        // partial sums: half h finishes outputs 3h .. 3h + 2
+        float2 y[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        epilogue64_out(tlane, 64 * half, reinterpret_cast<const float2 *>(bias + 2 * kHid) + 32 * half, w3, y);
+        {
+            const float ys[6] = {y[0].x, y[0].y, y[1].x, y[1].y, y[2].x, y[2].y};
+            float *mine = xch + ((size_t)half * kRows + r) * 4;          // the other half's outputs
+            mine[0] = ys[half ? 0 : 3];
+            mine[1] = ys[half ? 1 : 4];
+            mine[2] = ys[half ? 2 : 5];
+            slot_sync();
+            const float *theirs = xch + ((size_t)(1 - half) * kRows + r) * 4;
+            if (valid) {
+                const bool fall = out && exact != nullptr;
 #pragma unroll
-            for (int qq = 0; qq < kOut; qq++) {
-                if (qq / 3 != half) continue;
-                const float y = __uint_as_float(v[qq]) + bias[3 * kHid + qq];
-                tau[qq * n + p] = fall ? __ldg(exact + qq * n + p) : fmaf(st[40 + qq], y, st[32 + qq]);
+                for (int j = 0; j < 3; j++) {
+                    const int qq = 3 * half + j;
+                    const float yq = (half ? ys[3 + j] : ys[j]) + theirs[j] + bias[3 * kHid + qq];
+                    tau[qq * n + p] = fall ? __ldg(exact + qq * n + p) : fmaf(st[40 + qq], yq, st[32 + qq]);
+                }
             }
         }
     }
