@@ -163,6 +163,15 @@ def oracle_time(dns, les, delta, snaps, budget_s=10.0):
     return pts / dt, O.num_threads(), f"{done} whole snapshot(s) of the workload, {dt:.1f} s"
 
 
+def min_eigenvalue(tau):
+    """Smallest eigenvalue of the symmetric 3 x 3 T_ij over all LES points."""
+    T = np.empty(tau.shape[1:] + (3, 3))
+    for q, (i, j) in enumerate(((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))):
+        T[..., i, j] = tau[q]
+        T[..., j, i] = tau[q]
+    return float(np.linalg.eigvalsh(T.reshape(-1, 3, 3)).min())
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -410,7 +419,10 @@ def main():
         got = tau[0].double().cpu().numpy()
         err = {"tau_max_abs_err_utau2": [float(x) for x in np.abs(got - tau_ref).max(axis=(1, 2, 3))],
                "tau_order": ["11", "12", "13", "22", "23", "33"],
-               "ubar_max_abs_err": float(np.abs(ub[0].double().cpu().numpy() - ub_ref).max())}
+               "ubar_max_abs_err": float(np.abs(ub[0].double().cpu().numpy() - ub_ref).max()),
+               "tau_min_eigenvalue": {"path": min_eigenvalue(got), "oracle": min_eigenvalue(tau_ref),
+                                      "note": "T is a weighted covariance for a positive kernel (PSD); "
+                                              "u_tau^2 units"}}
         if not args.no_cpu_baseline and world == 1:
             v, cores, sample = oracle_time(dns, les, delta, snaps)
             cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
