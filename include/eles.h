@@ -62,8 +62,18 @@ typedef enum {
  * piecewise-linear interpolant of the extended field (EF_KERNEL_GAUSSIAN_HAT:
  * the quadrature alternative Sec. 3 names for the commutation error; it
  * reproduces linear profiles exactly away from the walls).  x and z use the
- * trapezoid rule in both.  The differential filter of Sec. 3 is not built. */
-enum { EF_KERNEL_GAUSSIAN = 0, EF_KERNEL_GAUSSIAN_HAT = 1 };
+ * trapezoid rule in both.
+ * EF_KERNEL_DIFFERENTIAL is the filter of the paper's simulations (Sec. 3):
+ * the Green's function of (1 - a^2 lap), i.e. ubar solves
+ * (1 - a^2 lap) ubar = u on the extended domain, with the second-order
+ * finite-difference Laplacian on the DNS nodes (three-point periodic in x
+ * and z, three-point non-uniform in y with mirror ghosts of each field's
+ * parity at both walls) and a^2 = Delta_f^2 / 40 (`delta` is Delta_f).  It
+ * needs EF_PREC_FP64, an extension (Eq. 7 or Eq. 9), nx and nz of the form
+ * 2^p 3^q (at most 1024), and LES nodes that are DNS nodes (nx, nz
+ * multiples of nlx, nlz; LES y nodes among the DNS y nodes); otherwise
+ * ef_filter_setup returns EF_ERR_SHAPE / EF_ERR_ARG / EF_ERR_UNSUPPORTED. */
+enum { EF_KERNEL_GAUSSIAN = 0, EF_KERNEL_GAUSSIAN_HAT = 1, EF_KERNEL_DIFFERENTIAL = 2 };
 
 /* Wall treatment. */
 enum {
@@ -101,8 +111,10 @@ typedef struct ef_plan ef_plan;
  *  dns, les   grids (host structs; y arrays are copied).  les must span the
  *             same box: les->Lx == dns->Lx, les->Lz == dns->Lz, les->y within
  *             [-1, 1] ascending with les->y[0] = -1 and les->y[nly-1] = +1.
- *  delta      filter width, > 0; 2.5 delta must be < Lx/2, Lz/2 and < 2.
- *  kernel     EF_KERNEL_GAUSSIAN or EF_KERNEL_GAUSSIAN_HAT.
+ *  delta      filter width, > 0; for the Gaussian kernels 2.5 delta must be
+ *             < Lx/2, Lz/2 and < 2.
+ *  kernel     EF_KERNEL_GAUSSIAN, EF_KERNEL_GAUSSIAN_HAT or
+ *             EF_KERNEL_DIFFERENTIAL.
  *  extension  EF_EXT_*.
  *  precision  EF_PREC_*.
  *  out        receives the plan (owned by the caller, free with

@@ -115,6 +115,7 @@ int ef_batch_run(ef_batch *b, const void *const *u, void *const *ubar, void *con
 int ef_plan_autotune(ef_plan *p, const void *u, void *ubar, void *tau, int reps, int *choice, float *best_ms)
 {
     if (!p || !u || !ubar || !tau) { set_error("ef_plan_autotune: NULL argument"); return EF_ERR_ARG; }
+    if (p->diff) { set_error("ef_plan_autotune: the differential filter has one variant"); return EF_ERR_UNSUPPORTED; }
     if (reps < 1) reps = 3;
     struct Cand { bool fused; int xv; int P; };
     std::vector<Cand> cands;
@@ -188,6 +189,7 @@ int ef_plan_autotune(ef_plan *p, const void *u, void *ubar, void *tau, int reps,
 int ef_plan_set_variant(ef_plan *p, int choice)
 {
     if (!p) { set_error("ef_plan_set_variant: NULL plan"); return EF_ERR_ARG; }
+    if (p->diff) { set_error("ef_plan_set_variant: the differential filter has one variant"); return EF_ERR_UNSUPPORTED; }
     const int v = choice / 16, P = choice % 16;
     if (P < 1 || (P & (P - 1)) || P > 8) { set_error("ef_plan_set_variant: bad column count"); return EF_ERR_ARG; }
     if (v == 0) {

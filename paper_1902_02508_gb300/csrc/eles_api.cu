@@ -94,6 +94,10 @@ int prof_begin(ef_plan *p, PhaseEvents *pe)
 int plan_reserve(ef_plan *p, int nsnap)
 {
     if (nsnap < 1) { set_error("reserve: nsnap must be >= 1"); return EF_ERR_ARG; }
+    if (p->diff) {                  // the differential filter runs snapshots one after another
+        if (nsnap > p->reserve) p->reserve = nsnap;
+        return EF_OK;
+    }
     if (nsnap <= p->reserve) return EF_OK;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "reserve");
@@ -164,6 +168,7 @@ void ef_plan_destroy(ef_plan *p)
     cudaFree(p->d_yfrag);
     cudaFree(p->d_zfrag);
     cudaFree(p->d_err);
+    diff_destroy(p->diff);
     for (int t = 0; t < ef_plan::kProfSlots; t++)
         for (int k = 0; k < ef_plan::kProfEvents; k++)
             if (p->prof_ev[t][k]) cudaEventDestroy(p->prof_ev[t][k]);
@@ -179,10 +184,11 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
     int rc;
     if ((rc = check_grid(dns, "dns")) || (rc = check_grid(les, "les"))) return rc;
     if (!(delta > 0) || !isfinite(delta)) { set_error("delta must be finite and > 0"); return EF_ERR_ARG; }
-    if (kernel != EF_KERNEL_GAUSSIAN && kernel != EF_KERNEL_GAUSSIAN_HAT) {
-        set_error("only the Gaussian kernel is implemented (trapezoid or hat quadrature in y)");
+    if (kernel != EF_KERNEL_GAUSSIAN && kernel != EF_KERNEL_GAUSSIAN_HAT && kernel != EF_KERNEL_DIFFERENTIAL) {
+        set_error("unknown filter kernel %d", kernel);
         return EF_ERR_UNSUPPORTED;
     }
+    const bool differential = kernel == EF_KERNEL_DIFFERENTIAL;
     if (extension < EF_EXT_EVEN_ODD || extension > EF_EXT_NONE) { set_error("unknown extension %d", extension); return EF_ERR_ARG; }
     if (precision != EF_PREC_FP64 && precision != EF_PREC_FP32 && precision != EF_PREC_BF16X3) {
         set_error("precision %d not implemented", precision);
@@ -190,7 +196,7 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
     }
     if (les->Lx != dns->Lx || les->Lz != dns->Lz) { set_error("LES and DNS boxes differ"); return EF_ERR_SHAPE; }
     if (les->nx > dns->nx || les->nz > dns->nz || les->ny > dns->ny) { set_error("LES grid finer than DNS grid"); return EF_ERR_SHAPE; }
-    if (2.5 * delta >= 0.5 * dns->Lx || 2.5 * delta >= 0.5 * dns->Lz || 2.5 * delta >= 2.0) {
+    if (!differential && (2.5 * delta >= 0.5 * dns->Lx || 2.5 * delta >= 0.5 * dns->Lz || 2.5 * delta >= 2.0)) {
         set_error("filter support 2.5 delta must be below half of Lx, Lz and below 2");
         return EF_ERR_ARG;
     }
@@ -204,7 +210,13 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
     if (extension == EF_EXT_ODD_EVEN) { p->par[0] = -1; p->par[1] = 1; p->par[2] = -1; }
     cudaError_t e;
 #define CK(x, what) do { if ((e = (x)) != cudaSuccess) { rc = cuda_fail(e, what); goto fail; } } while (0)
-    {
+    if (differential) {
+        if ((rc = diff_setup(p, dns->y, les->y))) goto fail;
+        p->reserve = 1;
+        CK(cudaMalloc(&p->d_err, sizeof(int)), "cudaMalloc error word");
+        CK(cudaMemset(p->d_err, 0, sizeof(int)), "clear error word");
+        CK(cudaDeviceSynchronize(), "setup");
+    } else {
         CK(cudaMalloc(&p->d_ygrid, sizeof(double) * p->ny), "cudaMalloc y");
         CK(cudaMemcpy(p->d_ygrid, dns->y, sizeof(double) * p->ny, cudaMemcpyHostToDevice), "copy y");
         if ((rc = build_periodic_band(p->nx, p->Lx, p->nlx, delta, &p->bx))) goto fail;
@@ -387,6 +399,7 @@ int ef_plan_info(const ef_plan *p, int what, long *value)
     case 11: *value = p->fused ? 1 : 0; break;
     case 12: *value = p->reserve; break;
     case 13: *value = p->ytc_ok ? 1 : 0; break;
+    case 14: *value = p->diff ? 1 : 0; break;
     default: set_error("ef_plan_info: unknown index %d", what); return EF_ERR_ARG;
     }
     return EF_OK;
@@ -395,6 +408,7 @@ int ef_plan_info(const ef_plan *p, int what, long *value)
 int ef_plan_weights(const ef_plan *p, int which, double *dst)
 {
     if (!p || !dst) { set_error("ef_plan_weights: NULL argument"); return EF_ERR_ARG; }
+    if (p->diff) { set_error("ef_plan_weights: the differential filter has no banded operators"); return EF_ERR_UNSUPPORTED; }
     cudaError_t e;
     if (which == 0 || which == 1) {
         const Band &b = which == 0 ? p->bx : p->bz;

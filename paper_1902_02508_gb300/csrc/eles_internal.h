@@ -139,12 +139,15 @@ cudaError_t launch_ypass(const YArgs<T> &a, int nsnap, cudaStream_t st);
 
 }  // namespace eles
 
+namespace eles { struct DiffPlan; }
+
 struct ef_plan {
     int device = 0;
     int nx = 0, ny = 0, nz = 0, nlx = 0, nly = 0, nlz = 0;
     double Lx = 0, Lz = 0, delta = 0;
     int ext = 0, prec = 0;
     int yquad = 0;                // y quadrature: 0 trapezoid, 1 hat (EF_KERNEL_GAUSSIAN_HAT)
+    eles::DiffPlan *diff = nullptr;   // EF_KERNEL_DIFFERENTIAL: its transforms and scratch
     int par[3] = {1, -1, 1};      // wall parity of u1, u2, u3 (Eq. 7 or Eq. 9)
     eles::Band bx, bz;            // x and z operators
     eles::Ring rx, rz;            // their strided-convolution tables (if ok)
@@ -216,6 +219,12 @@ int plan_reserve(ef_plan *p, int nsnap);
 // device buffer of closure_tc_image_bytes() that the call repacks from the
 // working weights and statistics; nfall counts guarded points; err receives
 // EF_ERR_TIMEOUT if a wait ran out.
+// differential.cu: the differential filter (EF_KERNEL_DIFFERENTIAL, FP64)
+int diff_setup(ef_plan *p, const double *dns_y, const double *les_y);
+void diff_destroy(DiffPlan *d);
+int diff_run(ef_plan *p, int nsnap, const void *u, void *ubar, void *tau, double *plane_mean, bool stress,
+             cudaStream_t s);
+
 size_t closure_tc_image_bytes();
 int closure_infer_tc(const float *wq, const long *off_w, const long *off_b, const double *stats, void *image,
                      const float *feats, long n, float guard, const float *exact, float *tau, int *nfall, int *err,

@@ -537,6 +537,7 @@ int run_typed(ef_plan *p, int nsnap, const T *u, T *ubar, T *tau, double *plane_
 int run_filter(ef_plan *p, int nsnap, const void *u, void *ubar, void *tau, double *plane_mean, bool stress,
                cudaStream_t s, const PhaseEvents *pe)
 {
+    if (p->diff) return diff_run(p, nsnap, u, ubar, tau, plane_mean, stress, s);
     if (p->prec == EF_PREC_FP64)
         return run_typed<double>(p, nsnap, static_cast<const double *>(u), static_cast<double *>(ubar),
                                  static_cast<double *>(tau), plane_mean, stress, s, pe);

@@ -24,6 +24,7 @@ STATUS = {0: "EF_OK", 1: "EF_ERR_ARG", 2: "EF_ERR_SHAPE", 3: "EF_ERR_CUDA", 4: "
           5: "EF_ERR_TIMEOUT", 6: "EF_ERR_OOM", 7: "EF_ERR_UNSUPPORTED"}
 KERNEL_GAUSSIAN = 0
 KERNEL_GAUSSIAN_HAT = 1      # y integral exact against the piecewise-linear interpolant
+KERNEL_DIFFERENTIAL = 2      # (1 - a^2 lap) ubar = u, a^2 = delta^2 / 40 (FP64)
 EXT_EVEN_ODD, EXT_ODD_EVEN, EXT_NONE = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_TF32X2, PREC_BF16X3 = 0, 1, 2, 3
 
