@@ -186,7 +186,8 @@ int ef_check_device_error(ef_plan *plan, void *stream);
  * row, 10 x-contraction variant (0 generic, 1 banded ring on CUDA cores,
  * 2 tensor cores, 3 tensor cores with warp-specialised producer, x and z
  * roles), 11 x and z fused in one kernel (0/1), 12 reserved snapshots,
- * 13 y-contraction variant (0 CUDA cores, 1 tensor cores, EF_PREC_BF16X3).
+ * 13 y-contraction variant (0 CUDA cores, 1 tensor cores, EF_PREC_BF16X3),
+ * 14 differential-filter plan (0/1).
  * Returns EF_ERR_ARG for an unknown index. */
 int ef_plan_info(const ef_plan *plan, int what, long *value);
 
@@ -249,6 +250,26 @@ int ef_error_field(ef_stats *st, const void *a, const void *b, int component, do
                    double *err, void *stream);
 int ef_error_profile(ef_stats *st, const double *pa, const double *pb, double utau_a, double utau_b, double *err,
                      void *stream);
+
+/*
+ * ef_differential_unfilter -- the inverse of the differential filter
+ * (EF_KERNEL_DIFFERENTIAL) on one grid: out = (1 - a^2 lap) in, a^2 =
+ * delta^2 / 40, with the same second-order stencils (three-point periodic in
+ * x and z, three-point non-uniform in y with mirror ghosts of each
+ * component's parity at the walls).  Sec. 4 compares LES and DNS velocities
+ * after reversing the filter on the LES field; with grid = the LES grid this
+ * is that reversal, with grid = the DNS grid it undoes ef_filter_fields of a
+ * differential plan whose LES grid is the DNS grid.
+ *  grid       host struct (y copied, stream-ordered temporary)
+ *  extension  EF_EXT_EVEN_ODD or EF_EXT_ODD_EVEN (component parities)
+ *  in, out    device double [3][ny][nz][nx]; distinct buffers.  An odd
+ *             component's wall rows are copied (its filtered values there
+ *             are zero).
+ * Errors: EF_ERR_ARG (NULL, in == out, no extension, delta <= 0),
+ * EF_ERR_SHAPE (grid), EF_ERR_CUDA.
+ */
+int ef_differential_unfilter(const ef_grid *grid, double delta, int extension, const double *in, double *out,
+                             void *stream);
 
 /* ------------------------------------------------------------------------
  * Host buffers.  The same computation as ef_subfilter_stress_batch (Eq. 6

@@ -288,6 +288,37 @@ __global__ void diff_stress(const double *fld, long n, double *ubar, double *tau
         for (int q = 0; q < 6; q++) tau[q * n + i] = fld[(3 + q) * n + i] - f[pi[q]] * f[pj[q]];
 }
 
+// (1 - a^2 lap) of a velocity field on one grid, the stencils of the filter.
+__global__ void unfilter_kernel(const double *__restrict__ in, double *__restrict__ out, const double *__restrict__ y,
+                                int nx, int ny, int nz, double ihx2, double ihz2, double a2, int p0, int p1, int p2)
+{
+    const long n = (long)nx * ny * nz;
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 3 * n) return;
+    const int c = (int)(idx / n);
+    const long r = idx - (long)c * n;
+    const int i = (int)(r % nx), k = (int)((r / nx) % nz), j = (int)(r / ((long)nx * nz));
+    const int parity = c == 0 ? p0 : c == 1 ? p1 : p2;
+    const double *f = in + (long)c * n;
+    const long row = ((long)j * nz + k) * nx;
+    const double v = f[row + i];
+    if (parity < 0 && (j == 0 || j == ny - 1)) { out[idx] = v; return; }
+    const double lx = (f[row + (i + 1 == nx ? 0 : i + 1)] - 2.0 * v + f[row + (i == 0 ? nx - 1 : i - 1)]) * ihx2;
+    const long plane = (long)nz * nx;
+    const long kp = (long)(k + 1 == nz ? 0 : k + 1) * nx, km = (long)(k == 0 ? nz - 1 : k - 1) * nx;
+    const double lz = (f[(long)j * plane + kp + i] - 2.0 * v + f[(long)j * plane + km + i]) * ihz2;
+    double ly;
+    if (j > 0 && j < ny - 1) {
+        const double hm = y[j] - y[j - 1], hp = y[j + 1] - y[j];
+        ly = 2.0 / (hm + hp) * ((f[row + plane + i] - v) / hp - (v - f[row - plane + i]) / hm);
+    } else {
+        const double h = j == 0 ? y[1] - y[0] : y[ny - 1] - y[ny - 2];
+        const double inner = f[row + (j == 0 ? plane : -plane) + i];
+        ly = 2.0 * (inner - v) / (h * h);
+    }
+    out[idx] = v - a2 * (lx + lz + ly);
+}
+
 bool factor23(int n, int *rad, int *nrad)
 {
     *nrad = 0;
@@ -450,3 +481,33 @@ int diff_run(ef_plan *p, int nsnap, const void *u_, void *ubar_, void *tau_, dou
 }
 
 }  // namespace eles
+
+using namespace eles;
+
+extern "C" int ef_differential_unfilter(const ef_grid *g, double delta, int extension, const double *in, double *out,
+                                        void *stream)
+{
+    if (!g || !g->y || !in || !out || in == out) {
+        set_error("ef_differential_unfilter: NULL or aliased argument");
+        return EF_ERR_ARG;
+    }
+    if (!(delta > 0) || (extension != EF_EXT_EVEN_ODD && extension != EF_EXT_ODD_EVEN)) {
+        set_error("ef_differential_unfilter: needs delta > 0 and a wall extension (Eq. 7 or Eq. 9)");
+        return EF_ERR_ARG;
+    }
+    if (g->nx < 3 || g->nz < 3 || g->ny < 3) { set_error("ef_differential_unfilter: grid too small"); return EF_ERR_SHAPE; }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *dy = nullptr;
+    cudaError_t e = cudaMallocAsync(&dy, sizeof(double) * g->ny, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dy, g->y, sizeof(double) * g->ny, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ef_differential_unfilter");
+    const double hx = g->Lx / g->nx, hz = g->Lz / g->nz, a2 = delta * delta / 40.0;
+    const int flip = extension == EF_EXT_ODD_EVEN;
+    const long n3 = 3L * g->nx * g->ny * g->nz;
+    unfilter_kernel<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(in, out, dy, g->nx, g->ny, g->nz, 1.0 / (hx * hx),
+                                                                1.0 / (hz * hz), a2, flip ? -1 : 1, flip ? 1 : -1,
+                                                                flip ? -1 : 1);
+    e = cudaGetLastError();
+    cudaFreeAsync(dy, s);
+    return e == cudaSuccess ? EF_OK : cuda_fail(e, "ef_differential_unfilter");
+}

@@ -140,3 +140,30 @@ def test_setup_refusals():
     with pytest.raises(eles.EFError) as e:
         eles.filter_setup(dns, off, 0.5, kernel=K, precision=eles.PREC_FP64)
     assert e.value.code == 2
+
+
+def test_unfilter_inverts_filter_and_matches_operator():
+    """ef_differential_unfilter is (1 - a^2 lap): it undoes the filter on the
+    DNS grid (the LES grid taken equal to it) and equals the reference
+    operator on an arbitrary field."""
+    dns = I.dns_grid(24, 33, 18, 2 * math.pi, math.pi)
+    delta = 0.8
+    dev = torch.device("cuda")
+    u = I.channel_velocity(dns, 9)
+    plan = eles.filter_setup(dns, dns, delta, kernel=eles.KERNEL_DIFFERENTIAL, precision=eles.PREC_FP64)
+    ud = torch.from_numpy(u).to(dev)
+    ub = torch.empty_like(ud)
+    eles.filter_fields(plan, ud, ub)
+    back = torch.empty_like(ud)
+    eles.differential_unfilter(dns, delta, ub, back)
+    torch.cuda.synchronize()
+    assert np.abs(back.cpu().numpy() - u).max() <= 1e-11 * np.abs(u).max()
+    v = np.random.default_rng(4).standard_normal(u.shape)
+    v[1, 0] = 0.0
+    v[1, -1] = 0.0
+    out = torch.empty_like(ud)
+    eles.differential_unfilter(dns, delta, torch.from_numpy(v).to(dev), out)
+    a = D.filter_parameter(delta)
+    p = D.parities(D.EXT_EVEN_ODD)
+    ref = np.stack([D.apply_operator(v[c], dns.y, dns.Lx, dns.Lz, a, p[c]) for c in range(3)])
+    assert np.abs(out.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
