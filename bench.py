@@ -387,6 +387,9 @@ def main():
            "api": "ef_subfilter_stress_host (pinned host buffers, 1-snapshot groups)"}
     io.close()
 
+    from_json = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+
     # --- plain FP64 GPU filter on the same workload (the metric's comparator)
     fp64 = None
     if not args.no_fp64 and prec != 0:
@@ -398,12 +401,22 @@ def main():
         k64 = max(2, args.steps // 4)
         ms64 = timed(lambda: step(p64, u64, b64, t64, pm), k64, 1)
         fp64 = {"value": world * pts_step * k64 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64 / k64}
+        # FP64 arithmetic bound: algorithmic flops per DNS point from the plan's tap counts (9 fields
+        # formed; x, z and y contractions; the y pass also contracts the 9 cross-term fields) against
+        # the FP64 FMA rate measured on this GB300 (1.68 DFMA per SM per clock, independent chains)
+        tx, tz, ty = (eles.plan_info(p64, i) for i in (7, 8, 9))
+        fpp = (9 + 18 * les.nx * tx / dns.nx + 18 * les.nz * tz / dns.nz * les.nx / dns.nx
+               + 36 * les.ny * ty / dns.ny * les.nx * les.nz / (dns.nx * dns.nz))
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        dpeak = 1.68 * 2 * nsm * from_json.get("sm_max_mhz", 2070.0) * 1e6
+        ach = fp64["value"] / world * fpp
+        fp64["roofline"] = {"bound": "alu", "achieved": ach / 1e12, "peak": dpeak / 1e12, "unit": "TFLOP/s",
+                            "frac": ach / dpeak, "flop_per_point": fpp,
+                            "peak_source": "FP64 FMA rate measured on GB300 (1.68 per SM per clock) x SMs x max clock"}
         del u64
         p64.close()
 
     # --- the learned closure (trained on this workload's exact stress)
-    from_json = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     closure = None
     if not args.no_closure and ns >= 2:
         closure = closure_measure(eles, torch, les, ub, tau, stream, timed,

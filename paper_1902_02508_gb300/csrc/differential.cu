@@ -40,7 +40,8 @@ struct DiffPlan {
     int rx = 1, rz = 1;                   // DNS nodes per LES node in x and z
     int zcols = 4;                        // columns per CTA in the z transforms
     double2 *spec = nullptr;              // [ny][nz][nxh] spectrum of one field
-    double *cp = nullptr;                 // [ny][nz][nxh] Thomas coefficients
+    double *fcp = nullptr;                // [2][ny][nz][nxh] Thomas factors per parity (even, odd):
+    double *finv = nullptr;               //   modified upper diagonal and pivot reciprocal
     double2 *lesz = nullptr;              // [nly][nlz][nxh]
     double *fld = nullptr;                // [9][nly][nlz][nlx] filtered fields of one snapshot
 };
@@ -68,13 +69,15 @@ __device__ double2 *smem_fft(double2 *b0, double2 *b1, int N, int ncol, const in
             const double2 *x = b0 + c * N;
             double2 *yv = b1 + c * N;
             const int d = (j / Ns) * Ns * R + k;
-            double2 v0 = x[j], v1 = cmul(x[j + NR], tw[tstride * k]);
+            double2 v0 = x[j], v1 = x[j + NR];
+            if (Ns > 1) v1 = cmul(v1, tw[tstride * k]);      // the first stage's twiddles are 1
             if (R == 2) {
                 yv[d] = make_double2(v0.x + v1.x, v0.y + v1.y);
                 yv[d + Ns] = make_double2(v0.x - v1.x, v0.y - v1.y);
             } else {
                 // radix 3: w = exp(-2 pi i / 3); y1,2 = v0 - (v1 + v2) / 2 -/+ i (sqrt 3 / 2)(v1 - v2)
-                const double2 v2 = cmul(x[j + 2 * NR], tw[2 * tstride * k]);
+                double2 v2 = x[j + 2 * NR];
+                if (Ns > 1) v2 = cmul(v2, tw[2 * tstride * k]);
                 const double2 t1 = make_double2(v1.x + v2.x, v1.y + v2.y);
                 const double2 t2 = make_double2(v1.x - v2.x, v1.y - v2.y);
                 const double h = 0.86602540378443864676;     // sqrt(3) / 2
@@ -104,24 +107,35 @@ struct DxFwdArgs {
     double2 *spec;                        // [ny][nz][nxh]
 };
 
-// One CTA per (z row k, y row j): the field along x, its transform.
+// One CTA per (pair of z rows k0 = 2 b, k0 + 1; y row j): the two real rows
+// are transformed together as z = f_k0 + i f_k1, and separated by the
+// symmetry of real transforms: F_k0[m] = (Z[m] + conj Z[N-m]) / 2,
+// F_k1[m] = (Z[m] - conj Z[N-m]) / (2i).
 __global__ void __launch_bounds__(kDiffThreads) dx_forward(const DxFwdArgs a)
 {
     extern __shared__ double2 sbuf[];
-    const int k = blockIdx.x, j = blockIdx.y, N = a.nx;
+    const int k0 = 2 * blockIdx.x, j = blockIdx.y, N = a.nx;
+    const bool two = k0 + 1 < a.nz;
     double2 *b0 = sbuf, *b1 = sbuf + N;
     const size_t plane = (size_t)a.ny * a.nz * a.nx;
-    const size_t row = ((size_t)j * a.nz + k) * a.nx;
+    const size_t row = ((size_t)j * a.nz + k0) * a.nx;
     const bool zero = a.odd && (j == 0 || j == a.ny - 1);
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        double v = a.u[a.ca * plane + row + i];
-        if (a.cb >= 0) v *= a.u[a.cb * plane + row + i];
-        b0[i] = make_double2(zero ? 0.0 : v, 0.0);
+        double v0 = a.u[a.ca * plane + row + i], v1 = two ? a.u[a.ca * plane + row + N + i] : 0.0;
+        if (a.cb >= 0) {
+            v0 *= a.u[a.cb * plane + row + i];
+            if (two) v1 *= a.u[a.cb * plane + row + N + i];
+        }
+        b0[i] = zero ? make_double2(0.0, 0.0) : make_double2(v0, v1);
     }
     __syncthreads();
     const double2 *X = smem_fft(b0, b1, N, 1, a.rad, a.nrad, a.tw);
-    double2 *out = a.spec + ((size_t)j * a.nz + k) * a.nxh;
-    for (int m = threadIdx.x; m < a.nxh; m += blockDim.x) out[m] = X[m];
+    double2 *out = a.spec + ((size_t)j * a.nz + k0) * a.nxh;
+    for (int m = threadIdx.x; m < a.nxh; m += blockDim.x) {
+        const double2 zm = X[m], zc = X[m == 0 ? 0 : N - m];       // conj taken below
+        out[m] = make_double2(0.5 * (zm.x + zc.x), 0.5 * (zm.y - zc.y));
+        if (two) out[a.nxh + m] = make_double2(0.5 * (zm.y + zc.y), -0.5 * (zm.x - zc.x));
+    }
 }
 
 struct DzArgs {
@@ -182,51 +196,65 @@ __global__ void __launch_bounds__(kDiffThreads) dz_inverse(const DzArgs a)
 
 struct DyArgs {
     double2 *spec;                        // [ny][nz][nxh], in place
-    double *cp;                           // [ny][nz][nxh]
+    const double *fcp, *finv;             // this parity's Thomas factors [ny][nz][nxh]
     const double *k2x, *k2z, *dyy;        // a^2 k~^2 tables; D_yy [3][ny]
     double a2;
     int ny, nz, nxh, odd;
 };
 
-// Thomas algorithm per (kz, kx): rows
+// The tridiagonal rows for (kz, kx):
 //   -a^2 lo_j v_{j-1} + (1 + a^2 (kx~^2 + kz~^2) - a^2 ce_j) v_j - a^2 up_j v_{j+1} = f_j,
-// identity rows on the walls for an odd field.  Threads run along kx
-// (coalesced); the modified upper diagonal is kept in cp.
-__global__ void __launch_bounds__(kDiffThreads) dy_solve(const DyArgs a)
+// identity rows on the walls for an odd field.
+__device__ __forceinline__ void dy_row(const DyArgs &a, double lam, int j, double &sub, double &dia, double &sup)
+{
+    if (a.odd && (j == 0 || j == a.ny - 1)) { sub = 0.0; dia = 1.0; sup = 0.0; return; }
+    sub = -a.a2 * a.dyy[j];
+    dia = 1.0 + lam - a.a2 * a.dyy[a.ny + j];
+    sup = -a.a2 * a.dyy[2 * a.ny + j];
+}
+
+// Set-up: the LU factors of the Thomas algorithm per line (they depend on
+// the mode and the parity only, not on the field): c_j = sup_j / den_j and
+// 1 / den_j with den_j = dia_j - sub_j c_{j-1}.
+__global__ void __launch_bounds__(kDiffThreads) dy_factor(DyArgs a, double *fcp, double *finv)
 {
     const long line = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const long nline = (long)a.nz * a.nxh;
     if (line >= nline) return;
     const int kz = (int)(line / a.nxh), kx = (int)(line - (long)kz * a.nxh);
     const double lam = a.k2x[kx] + a.k2z[kz];
-    const double *lo = a.dyy, *ce = a.dyy + a.ny, *up = a.dyy + 2 * a.ny;
-    auto row = [&](int j, double &sub, double &dia, double &sup) {
-        if (a.odd && (j == 0 || j == a.ny - 1)) { sub = 0.0; dia = 1.0; sup = 0.0; return; }
-        sub = -a.a2 * lo[j];
-        dia = 1.0 + lam - a.a2 * ce[j];
-        sup = -a.a2 * up[j];
-    };
-    double sub, dia, sup;
-    row(0, sub, dia, sup);
-    double c = sup / dia;
-    double2 d = a.spec[line];
-    d = make_double2(d.x / dia, d.y / dia);
-    a.cp[line] = c;
-    a.spec[line] = d;
-    for (int j = 1; j < a.ny; j++) {
-        row(j, sub, dia, sup);
+    double c = 0.0;
+    for (int j = 0; j < a.ny; j++) {
+        double sub, dia, sup;
+        dy_row(a, lam, j, sub, dia, sup);
+        const double inv = 1.0 / (dia - sub * c);
+        c = sup * inv;
+        fcp[(size_t)j * nline + line] = c;
+        finv[(size_t)j * nline + line] = inv;
+    }
+}
+
+// Thomas algorithm per (kz, kx) with the precomputed factors: forward
+// d_j = (f_j - sub_j d_{j-1}) / den_j, backward v_j = d_j - c_j v_{j+1}.
+// Threads run along kx (coalesced).
+__global__ void __launch_bounds__(kDiffThreads) dy_solve(const DyArgs a)
+{
+    const long line = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long nline = (long)a.nz * a.nxh;
+    if (line >= nline) return;
+    double2 d = make_double2(0.0, 0.0);
+    for (int j = 0; j < a.ny; j++) {
         const size_t o = (size_t)j * nline + line;
-        const double den = dia - sub * c;
+        const double sub = (a.odd && j == a.ny - 1) ? 0.0 : -a.a2 * a.dyy[j];
+        const double inv = a.finv[o];
         const double2 f = a.spec[o];
-        c = sup / den;
-        d = make_double2((f.x - sub * d.x) / den, (f.y - sub * d.y) / den);
-        a.cp[o] = c;
+        d = make_double2((f.x - sub * d.x) * inv, (f.y - sub * d.y) * inv);
         a.spec[o] = d;
     }
     double2 v = d;
     for (int j = a.ny - 2; j >= 0; j--) {
         const size_t o = (size_t)j * nline + line;
-        const double cj = a.cp[o];
+        const double cj = a.fcp[o];
         const double2 dj = a.spec[o];
         v = make_double2(dj.x - cj * v.x, dj.y - cj * v.y);
         a.spec[o] = v;
@@ -407,7 +435,8 @@ int diff_setup(ef_plan *p, const double *dns_y, const double *les_y)
     DK(cudaMalloc(&d->dyy, sizeof(double) * dyy.size()));
     DK(cudaMalloc(&d->jy, sizeof(int) * p->nly));
     DK(cudaMalloc(&d->spec, sizeof(double2) * nspec));
-    DK(cudaMalloc(&d->cp, sizeof(double) * nspec));
+    DK(cudaMalloc(&d->fcp, sizeof(double) * 2 * nspec));
+    DK(cudaMalloc(&d->finv, sizeof(double) * 2 * nspec));
     DK(cudaMalloc(&d->lesz, sizeof(double2) * (size_t)p->nly * p->nlz * d->nxh));
     DK(cudaMalloc(&d->fld, sizeof(double) * 9 * (size_t)p->nly * p->nlz * p->nlx));
     DK(cudaMemcpy(d->twx, twx.data(), sizeof(double2) * p->nx, cudaMemcpyHostToDevice));
@@ -419,6 +448,16 @@ int diff_setup(ef_plan *p, const double *dns_y, const double *les_y)
     const int zsm = (int)(2 * sizeof(double2) * (size_t)p->nz * d->zcols);
     DK(cudaFuncSetAttribute(dz_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
     DK(cudaFuncSetAttribute(dz_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
+    for (int q = 0; q < 2 && e == cudaSuccess; q++) {
+        DyArgs ya = {};
+        ya.k2x = d->k2x; ya.k2z = d->k2z; ya.dyy = d->dyy; ya.a2 = a2;
+        ya.ny = ny; ya.nz = p->nz; ya.nxh = d->nxh; ya.odd = q;
+        const long nline = (long)p->nz * d->nxh;
+        dy_factor<<<(unsigned)((nline + kDiffThreads - 1) / kDiffThreads), kDiffThreads>>>(ya, d->fcp + q * nspec,
+                                                                                          d->finv + q * nspec);
+        e = cudaGetLastError();
+    }
+    DK(cudaDeviceSynchronize());
 #undef DK
     if (e != cudaSuccess) return cuda_fail(e, "differential filter setup");
     return EF_OK;
@@ -428,7 +467,7 @@ void diff_destroy(DiffPlan *d)
 {
     if (!d) return;
     cudaFree(d->twx); cudaFree(d->twz); cudaFree(d->k2x); cudaFree(d->k2z); cudaFree(d->dyy); cudaFree(d->jy);
-    cudaFree(d->spec); cudaFree(d->cp); cudaFree(d->lesz); cudaFree(d->fld);
+    cudaFree(d->spec); cudaFree(d->fcp); cudaFree(d->finv); cudaFree(d->lesz); cudaFree(d->fld);
     delete d;
 }
 
@@ -450,7 +489,7 @@ int diff_run(ef_plan *p, int nsnap, const void *u_, void *ubar_, void *tau_, dou
             xa.nx = p->nx; xa.ny = p->ny; xa.nz = p->nz; xa.nxh = d->nxh;
             memcpy(xa.rad, d->radx, sizeof xa.rad); xa.nrad = d->nradx;
             xa.tw = d->twx; xa.spec = d->spec;
-            dx_forward<<<dim3(p->nz, p->ny), kDiffThreads, xsm, s>>>(xa);
+            dx_forward<<<dim3((p->nz + 1) / 2, p->ny), kDiffThreads, xsm, s>>>(xa);
             DzArgs za;
             za.spec = d->spec; za.nz = p->nz; za.nxh = d->nxh; za.ncol = d->zcols;
             memcpy(za.rad, d->radz, sizeof za.rad); za.nrad = d->nradz;
@@ -461,7 +500,10 @@ int diff_run(ef_plan *p, int nsnap, const void *u_, void *ubar_, void *tau_, dou
                 plane_mean_from_spec<<<(p->ny + 127) / 128, 128, 0, s>>>(
                     d->spec, p->ny, p->nz, d->nxh, 1.0 / ((double)p->nx * p->nz), plane_mean + (sn * 3 + f) * p->ny);
             DyArgs ya;
-            ya.spec = d->spec; ya.cp = d->cp; ya.k2x = d->k2x; ya.k2z = d->k2z; ya.dyy = d->dyy;
+            const size_t nspec = (size_t)p->ny * p->nz * d->nxh;
+            ya.spec = d->spec; ya.k2x = d->k2x; ya.k2z = d->k2z; ya.dyy = d->dyy;
+            ya.fcp = d->fcp + (parity < 0 ? nspec : 0);
+            ya.finv = d->finv + (parity < 0 ? nspec : 0);
             ya.a2 = d->a * d->a; ya.ny = p->ny; ya.nz = p->nz; ya.nxh = d->nxh; ya.odd = parity < 0;
             const long nline = (long)p->nz * d->nxh;
             dy_solve<<<(unsigned)((nline + kDiffThreads - 1) / kDiffThreads), kDiffThreads, 0, s>>>(ya);
