@@ -19,7 +19,9 @@ bandwidth.  `cpu_baseline` times the CPU oracle on a bounded sample.
 `closure` reports the learned closure on the same workload: trained on the
 exact T_ij of snapshot 0, its error against the exact T_ij of snapshot 1 (a
 field of another seed), and tensor-core inference on 2^20 LES points with its
-roofline against the measured bf16 tensor peak.
+roofline against the measured bf16 tensor peak.  `differential` times the
+paper's own filter (Sec. 3, a = 0.1) on one snapshot in FP64 against the FP64
+arithmetic bound.
 
 Multi-GPU: one process per GPU; snapshots are independent, so every rank
 filters its own snapshots with no collective on the data path (weak
@@ -222,6 +224,40 @@ def traffic_from_profile(kernel_tag, points_per_launch, kind="xz"):
     return None
 
 
+def differential_measure(eles, torch, dns, les, u0, stream, timed, peaks):
+    """EF_KERNEL_DIFFERENTIAL (FP64) on one snapshot, against the FP64 arithmetic
+    bound.  Algorithmic flops: 5 N log2 N per complex transform of length N
+    (two real x rows per transform), 10 per Thomas row, for the 9 fields."""
+    delta_f = 0.1 * math.sqrt(40.0)                    # a = 0.1 (Sec. 3), a^2 = Delta_f^2 / 40
+    plan = eles.filter_setup(dns, les, delta_f, kernel=eles.KERNEL_DIFFERENTIAL, precision=0)
+    with torch.cuda.stream(stream):
+        ud = u0.double().contiguous()
+        ub = torch.empty((3, les.ny, les.nz, les.nx), device=ud.device, dtype=torch.float64)
+        tau = torch.empty((6, les.ny, les.nz, les.nx), device=ud.device, dtype=torch.float64)
+    torch.cuda.synchronize()
+    k = 3
+    ms = timed(lambda: eles.subfilter_stress(plan, ud, ub, tau, stream=stream), k, 1) / k
+    assert eles.check_device_error(plan, stream) == 0
+    plan.close()
+    nxh = dns.nx // 2 + 1
+    lg = math.log2
+    flop = 9 * (dns.ny * (dns.nz / 2) * 5 * dns.nx * lg(dns.nx)        # forward x, two rows per transform
+                + dns.ny * nxh * 5 * dns.nz * lg(dns.nz)                  # forward z
+                + dns.nz * nxh * dns.ny * 10                              # Thomas
+                + les.ny * nxh * 5 * dns.nz * lg(dns.nz)                  # inverse z on the LES rows
+                + les.ny * les.nz * 5 * dns.nx * lg(dns.nx))              # inverse x on the LES rows
+    nsm = torch.cuda.get_device_properties(ud.device).multi_processor_count
+    dpeak = 1.68 * 2 * nsm * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    ach = flop / (ms / 1e3)
+    return {"workload": f"differential filter (1 - a^2 lap)^-1, a = 0.1, one {dns.nx}x{dns.ny}x{dns.nz} snapshot "
+                        f"-> {les.nx}x{les.ny}x{les.nz}, ubar and T, FP64",
+            "ms_per_snapshot": ms, "value": dns.npts / (ms / 1e3), "unit": UNIT,
+            "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": dpeak / 1e12, "unit": "TFLOP/s",
+                         "frac": ach / dpeak, "flop_per_snapshot": flop,
+                         "peak_source": "FP64 FMA rate measured on GB300 (1.68 per SM per clock) x SMs x max clock"},
+            "gpu_launches_per_snapshot": 9 * 5 + 3 + 1}
+
+
 CLOSURE_FLOP_PER_POINT = 2 * (10 * 128 + 128 * 128 + 128 * 128 + 128 * 6)   # 69,632: the four layers' MACs
 CLOSURE_POINTS = 1 << 20
 # The SiLU of the 384 hidden activations per point takes one ex2.approx and one
@@ -416,6 +452,11 @@ def main():
         del u64
         p64.close()
 
+    # --- the differential filter of Sec. 3 (the paper's own kernel, a = 0.1) on snapshot 0, FP64
+    differential = None
+    if not args.no_fp64:
+        differential = differential_measure(eles, torch, dns, les, u[0], stream, timed, from_json)
+
     # --- the learned closure (trained on this workload's exact stress)
     closure = None
     if not args.no_closure and ns >= 2:
@@ -468,7 +509,7 @@ def main():
                 "data": "synthetic (seeded solenoidal channel fields, Reichardt mean profile)",
                 "config": workload_config(args.workload, args.precision),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64,
-                "accuracy": err, "closure": closure, "clocks": clk.summary(),
+                "accuracy": err, "closure": closure, "differential": differential, "clocks": clk.summary(),
                 "gpu_launches": per_call_launches * args.steps,
                 "x_variant": eles.plan_info(plan, 10)}
         print(json.dumps(line), flush=True)
