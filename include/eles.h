@@ -181,6 +181,18 @@ int ef_plan_reserve(ef_plan *plan, int max_snapshots);
  */
 int ef_check_device_error(ef_plan *plan, void *stream);
 
+/*
+ * ef_selftest_wait -- failure-detection self-test.  A one-thread kernel waits
+ * on an mbarrier with the bounded wait every kernel of the library uses
+ * (their limit is about 2 s of SM clocks).  complete = 0: nothing arrives,
+ * the wait gives up after limit_cycles SM clocks and records EF_ERR_TIMEOUT
+ * in the plan's error word (read it with ef_check_device_error); the
+ * context stays usable.  complete = 1: the barrier phase completes first and
+ * nothing is recorded.  Errors: EF_ERR_ARG (NULL plan, limit outside
+ * 1 .. 4e9), EF_ERR_CUDA.
+ */
+int ef_selftest_wait(ef_plan *plan, long long limit_cycles, int complete, void *stream);
+
 /* Plan facts for callers and tests.  ints: 0 nx, 1 ny, 2 nz, 3 nlx, 4 nly,
  * 5 nlz, 6 precision, 7 x-taps per row, 8 z-taps per row, 9 max y-taps per
  * row, 10 x-contraction variant (0 generic, 1 banded ring on CUDA cores,

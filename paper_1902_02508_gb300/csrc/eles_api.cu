@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "eles_internal.h"
+#include "fused_stage.cuh"
 
 namespace eles {
 
@@ -318,6 +319,7 @@ int ef_plan_reserve(ef_plan *p, int max_snapshots)
 
 int ef_filter_fields(ef_plan *p, const void *u, void *ubar, void *stream)
 {
+    NvtxRange nv("ef_filter_fields");
     int rc = hot_args(p, u, ubar, "ef_filter_fields");
     if (rc) return rc;
     PhaseEvents pe;
@@ -329,6 +331,7 @@ int ef_filter_fields(ef_plan *p, const void *u, void *ubar, void *stream)
 int ef_subfilter_stress_batch(ef_plan *p, int nsnap, const void *u, void *ubar, void *tau, double *plane_mean,
                               void *stream)
 {
+    NvtxRange nv("ef_subfilter_stress");
     int rc = hot_args(p, u, ubar, "ef_subfilter_stress");
     if (rc) return rc;
     if (!tau) { set_error("ef_subfilter_stress: tau is NULL"); return EF_ERR_ARG; }
@@ -366,6 +369,35 @@ int ef_profile_read(ef_plan *p, double *ms, long *calls)
     for (int k = 0; k < 4; k++) ms[k] = p->prof_ms[k];
     if (calls) *calls = p->prof_calls;
     return EF_OK;
+}
+
+// Failure-detection self-test: thread 0 waits on an mbarrier with the
+// bounded wait every kernel of the library uses.  With complete = 0 nothing
+// arrives on it, so the wait gives up after `limit` SM clocks and records
+// EF_ERR_TIMEOUT in the error word; with complete = 1 the phase completes
+// first and nothing is recorded.  No copy is in flight and no TMEM is held.
+namespace {
+__global__ void selftest_wait_kernel(int *err, long long limit, int complete)
+{
+    __shared__ unsigned long long bar;
+    if (threadIdx.x != 0) return;
+    fz::mbar_init(&bar, 1);
+    fz::mbar_fence_init();
+    if (complete) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(fz::smem_u32(&bar)) : "memory");
+    fz::mbar_wait_for(&bar, 0, err, limit);
+}
+}  // namespace
+
+int ef_selftest_wait(ef_plan *p, long long limit_cycles, int complete, void *stream)
+{
+    if (!p) { set_error("ef_selftest_wait: NULL plan"); return EF_ERR_ARG; }
+    if (limit_cycles < 1 || limit_cycles > 4000000000LL) {
+        set_error("ef_selftest_wait: limit must be 1 .. 4e9 SM clocks");
+        return EF_ERR_ARG;
+    }
+    selftest_wait_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(p->d_err, limit_cycles, complete ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? EF_OK : cuda_fail(e, "ef_selftest_wait");
 }
 
 int ef_check_device_error(ef_plan *p, void *stream)

@@ -141,6 +141,15 @@ cudaError_t launch_ypass(const YArgs<T> &a, int nsnap, cudaStream_t st);
 
 namespace eles { struct DiffPlan; }
 
+// NVTX range over a host-side scope (visible to profilers; free otherwise).
+#include <nvtx3/nvToolsExt.h>
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 struct ef_plan {
     int device = 0;
     int nx = 0, ny = 0, nz = 0, nlx = 0, nly = 0, nlz = 0;

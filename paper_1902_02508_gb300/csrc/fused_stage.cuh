@@ -173,15 +173,20 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
                  : "memory");
     return ok != 0;
 }
-// Bounded wait; returns false (and flags the plan) if the phase never completed.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *err)
+// Bounded wait of at most `limit` SM clocks; returns false (and flags the
+// plan) if the phase never completed.
+__device__ __forceinline__ bool mbar_wait_for(unsigned long long *bar, unsigned parity, int *err, long long limit)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
-    while (clock64() - t0 < kWaitCycles)
+    while (clock64() - t0 < limit)
         if (mbar_try_wait(bar, parity)) return true;
     if (err) atomicCAS(err, 0, (int)EF_ERR_TIMEOUT);
     return false;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *err)
+{
+    return mbar_wait_for(bar, parity, err, kWaitCycles);
 }
 __device__ __forceinline__ void tma_load3(void *dst, const CUtensorMap *map, unsigned long long *bar, int x, int y, int z)
 {

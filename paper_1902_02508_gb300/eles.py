@@ -37,7 +37,7 @@ EXPORTED = ("ef_filter_setup", "ef_plan_destroy", "ef_filter_fields", "ef_subfil
             "ef_closure_gradients", "ef_closure_param_count", "ef_closure_get_params", "ef_closure_set_params",
             "ef_closure_save", "ef_closure_load", "ef_batch_create", "ef_batch_run", "ef_batch_destroy",
             "ef_plan_autotune", "ef_plan_set_variant", "ef_closure_features_static", "ef_io_create",
-            "ef_closure_check_device_error", "ef_differential_unfilter",
+            "ef_closure_check_device_error", "ef_differential_unfilter", "ef_selftest_wait",
             "ef_io_destroy", "ef_subfilter_stress_host", "ef_stats_create", "ef_stats_destroy", "ef_plane_stats",
             "ef_error_field", "ef_error_profile")
 
@@ -110,6 +110,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             lib.ef_closure_train.restype = i
             lib.ef_closure_infer.argtypes = [vp, vp, vp, L, vp, ctypes.POINTER(L), vp]
             lib.ef_closure_infer.restype = i
+            lib.ef_selftest_wait.argtypes = [vp, ctypes.c_longlong, i, vp]
+            lib.ef_selftest_wait.restype = i
             lib.ef_differential_unfilter.argtypes = [ctypes.POINTER(_Grid), d, i, vp, vp, vp]
             lib.ef_differential_unfilter.restype = i
             lib.ef_closure_check_device_error.argtypes = [vp, vp]
@@ -371,6 +373,11 @@ def closure_infer(cl: Closure, feats, tau_out, exact_tau=None, stream=None, coun
                                    _field(exact_tau, (6, n), torch.float32, "exact_tau"),
                                    ctypes.byref(nf) if count else None, _stream(stream)))
     return nf.value if count else None
+
+
+def selftest_wait(plan: Plan, limit_cycles: int, complete: bool = False, stream=None):
+    """Run the bounded-wait self-test on the plan's error word (asynchronous)."""
+    _check(load().ef_selftest_wait(plan.handle, int(limit_cycles), 1 if complete else 0, _stream(stream)))
 
 
 def differential_unfilter(grid, delta: float, u, out, extension: int = EXT_EVEN_ODD, stream=None):
