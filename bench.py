@@ -73,17 +73,40 @@ def parse():
     return ap.parse_args()
 
 
+def snapshot_recipe(rank, ns):
+    """(seed, x shift, z shift) of each of a rank's ns snapshots: two seeded
+    fields per rank, the rest periodic shifts of them.  Ranks never share a
+    seed, so the ranks filter disjoint snapshots (no collective on the data)."""
+    nbase = min(ns, 2)
+    return [(1000 + rank * 1000 + s % nbase, 0 if s < nbase else 7 * s, 0 if s < nbase else 5 * s)
+            for s in range(ns)]
+
+
+def max_over_ranks(ms, device, world):
+    """The step time of the job: the slowest rank's."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank_step, steps, ms):
+    """Units all ranks processed per second (weak scaling: every rank its own)."""
+    return world * units_per_rank_step * steps / (ms / 1e3)
+
+
 def make_workload(name, rank=0):
     from paper_1902_02508_gb300 import inputs as I
     nx, ny, nz, Lx, Lz, nlx, nly, nlz, dfrac, ns = WORKLOADS[name]
     dns = I.dns_grid(nx, ny, nz, Lx, Lz)
     les = I.les_grid(dns, nlx, nly, nlz)
     delta = dfrac * Lx
-    base = [I.channel_velocity(dns, 1000 + rank * 1000 + s) for s in range(min(ns, 2))]
-    snaps = []
-    for s in range(ns):
-        b = base[s % len(base)]
-        snaps.append(b if s < len(base) else I.shifted(b, 7 * s, 5 * s))
+    recipe = snapshot_recipe(rank, ns)
+    base = {seed: I.channel_velocity(dns, seed) for seed, sx, sz in recipe if sx == 0 and sz == 0}
+    snaps = [base[seed] if (sx, sz) == (0, 0) else I.shifted(base[seed], sx, sz) for seed, sx, sz in recipe]
     return dns, les, delta, snaps
 
 
@@ -378,12 +401,7 @@ def main():
                 fn()
             e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1), dev, world)
 
     # --- device-resident throughput, with phase timing and clocks
     with torch.cuda.stream(stream):
@@ -399,7 +417,7 @@ def main():
     # a second pass without the phase events, for the headline number
     ms = min(ms, timed(lambda: step(plan, u, ub, tau, pm), args.steps, 1))
     pts_step = ns * dns.npts
-    value = world * pts_step * args.steps / (ms / 1e3)
+    value = whole_job_rate(world, pts_step, args.steps, ms)
 
     # --- end to end: pinned host in, results back to pinned host
     hu = torch.stack([torch.from_numpy(s) for s in snaps]).to(dt).pin_memory()
