@@ -68,8 +68,11 @@ typedef enum {
  * (1 - a^2 lap) ubar = u on the extended domain, with the second-order
  * finite-difference Laplacian on the DNS nodes (three-point periodic in x
  * and z, three-point non-uniform in y with mirror ghosts of each field's
- * parity at both walls) and a^2 = Delta_f^2 / 40 (`delta` is Delta_f).  It
- * needs EF_PREC_FP64, an extension (Eq. 7 or Eq. 9), nx and nz of the form
+ * parity at both walls) and a^2 = Delta_f^2 / 40 (`delta` is Delta_f).
+ * EF_PREC_FP64 filters u and u u directly.  EF_PREC_FP32 transforms the
+ * fluctuations about the FP64 plane-mean profile (u', u'u' and U u') in FP32
+ * and solves the profile terms and forms ubar and T in FP64.  It needs one
+ * of these precisions, an extension (Eq. 7 or Eq. 9), nx and nz of the form
  * 2^p 3^q (at most 1024), and LES nodes that are DNS nodes (nx, nz
  * multiples of nlx, nlz; LES y nodes among the DNS y nodes); otherwise
  * ef_filter_setup returns EF_ERR_SHAPE / EF_ERR_ARG / EF_ERR_UNSUPPORTED. */

@@ -1,4 +1,4 @@
-// The differential filter of Sec. 3 on the GPU, in FP64.
+// The differential filter of Sec. 3 on the GPU, in FP64 or FP32.
 //
 // The filter the paper's simulations use is the Green's function of
 // (1 - a^2 lap): ubar solves (1 - a^2 lap) ubar = u on the domain extended
@@ -7,19 +7,29 @@
 // periodic in x and z, the three-point non-uniform stencil in y with mirror
 // ghosts of the field's parity at both walls), and a^2 = Delta_f^2 / 40.
 // The kernel is not a product of one-dimensional kernels, so this path does
-// not share the separable contractions of the Gaussian filter:
-//   1. form the field (u_a or u_a u_b) and transform each (y, z) row in x;
+// not share the separable contractions of the Gaussian filter.  Per field:
+//   1. form the field and transform each (y, z) row in x (two real rows per
+//      complex transform);
 //   2. transform each (y, kx) column in z (the periodic stencils become
 //      diagonal: lap -> -(2 - 2 cos(k h)) / h^2);
-//   3. solve the tridiagonal system in y for every (kx, kz) (Thomas);
+//   3. solve the tridiagonal system in y for every (kx, kz) (Thomas, with the
+//      factors precomputed per parity);
 //   4. transform back in z only on the LES rows, keeping the LES z nodes;
 //   5. transform back in x on those, keeping the LES x nodes (the LES nodes
-//      are DNS nodes, so the linear interpolation of Sec. 3 is the identity);
-//   6. T_ab = bar(u_a u_b) - ubar_a ubar_b (Eq. 6).
-// The transforms are mixed-radix (2 and 3) Stockham FFTs in shared memory
-// (the decimation-in-time formulation for GPUs of Govindaraju et al.,
-// SC 2008), one row or a few columns per CTA; the inverse is the forward
-// transform of the conjugate.  The plane means of u_c are the zero modes.
+//      are DNS nodes, so the linear interpolation of Sec. 3 is the identity).
+// FP64 plans filter u_a and u_a u_b and form T_ab = bar(u_a u_b) - ubar_a
+// ubar_b (Eq. 6) directly.  FP32 plans (the FP64 rate of GB300 is about a
+// seventieth of its FP32 rate) filter fluctuations about the plane-mean
+// profile U_c(y) so that no FP32 sum carries the mean: with u = U + u',
+//   ubar_a = F(U_a) + F(u'_a),
+//   T_ab = [F(U_a U_b) - F(U_a) F(U_b)] + [F(U_a u'_b) - F(U_a) F(u'_b)]
+//        + [F(U_b u'_a) - F(U_b) F(u'_a)] + [F(u'_a u'_b) - F(u'_a) F(u'_b)],
+// an identity of the linear filter.  The profiles' terms are one-dimensional
+// (the kx = kz = 0 system) and solved in FP64, the eighteen fluctuation
+// fields go through the FP32 transforms, and the brackets are formed in
+// FP64.  The transforms are mixed-radix (2 and 3) Stockham FFTs in shared
+// memory (the decimation-in-time formulation for GPUs of Govindaraju et al.,
+// SC 2008); the inverse is the forward transform of the conjugate.
 #include <math.h>
 #include <string.h>
 
@@ -30,139 +40,200 @@
 namespace eles {
 
 struct DiffPlan {
+    int fp32 = 0;                         // FP32 transforms with the profile decomposition
     double a = 0;
     int nxh = 0;                          // nx / 2 + 1 kept x modes (real input)
-    int radx[32] = {}, nradx = 0, radz[32] = {}, nradz = 0;
-    double2 *twx = nullptr, *twz = nullptr;   // exp(-2 pi i m / N), m < N
+    int n4x = 0, n2x = 0, n3x = 0, n4z = 0, n2z = 0, n3z = 0;   // radix-4, -2, -3 stages per axis
+    void *twx = nullptr, *twz = nullptr;  // exp(-2 pi i m / N), m < N (plan precision)
     double *k2x = nullptr, *k2z = nullptr;    // a^2 (2 - 2 cos(2 pi m / N)) / h^2
     double *dyy = nullptr;                // [3][ny]: D_yy lower, centre, upper (interior and even walls)
     int *jy = nullptr;                    // [nly]: DNS row of each LES row
     int rx = 1, rz = 1;                   // DNS nodes per LES node in x and z
     int zcols = 4;                        // columns per CTA in the z transforms
-    double2 *spec = nullptr;              // [ny][nz][nxh] spectrum of one field
-    double *fcp = nullptr;                // [2][ny][nz][nxh] Thomas factors per parity (even, odd):
-    double *finv = nullptr;               //   modified upper diagonal and pivot reciprocal
-    double2 *lesz = nullptr;              // [nly][nlz][nxh]
-    double *fld = nullptr;                // [9][nly][nlz][nlx] filtered fields of one snapshot
+    int nfield = 9;                       // filtered fields per snapshot
+    void *spec = nullptr;                 // [ny][nz][nxh] spectrum of one field
+    void *fcp = nullptr, *finv = nullptr; // [2][ny][nz][nxh] Thomas factors per parity (even, odd)
+    void *lesz = nullptr;                 // [nly][nlz][nxh]
+    void *fld = nullptr;                  // [nfield][nly][nlz][nlx] filtered fields of one snapshot
+    // FP32 plans: profile U_c(y) (FP64), its filtered terms at the LES rows, solver scratch
+    double *U = nullptr;                  // [3][ny]
+    double *FU = nullptr, *FUU = nullptr; // [3][nly], [6][nly]
+    double *pscr = nullptr;               // [9][2][ny]
 };
 
 namespace {
 
 constexpr int kDiffThreads = 256;
+constexpr int kXThreads = 128;             // x transforms: N/4 butterflies per radix-4 stage
 constexpr int kDiffMaxN = 1024;
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+template <typename R> struct Cx;
+template <> struct Cx<double> { using T = double2; };
+template <> struct Cx<float> { using T = float2; };
+template <typename R> using cx = typename Cx<R>::T;
+
+template <typename C> __device__ __forceinline__ C mk(double x, double y);
+template <> __device__ __forceinline__ double2 mk<double2>(double x, double y) { return make_double2(x, y); }
+template <> __device__ __forceinline__ float2 mk<float2>(double x, double y) { return make_float2((float)x, (float)y); }
+
+template <typename C> __device__ __forceinline__ C cmul(C a, C b)
 {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
 }
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
 
 // Stockham stages over ncol independent transforms of length N held column
-// by column (column c at b + c * N).  Returns the buffer holding the result.
-__device__ double2 *smem_fft(double2 *b0, double2 *b1, int N, int ncol, const int *rad, int nrad,
-                             const double2 *__restrict__ tw)
+// by column (column c at b + c * N): n4 radix-4 stages, n2 radix-2 stages,
+// then n3 radix-3 stages, so that the sub-transform length Ns is a power of
+// two while it matters for the index arithmetic (shifts and masks).  Returns
+// the buffer holding the result.
+template <typename C>
+__device__ C *smem_fft(C *b0, C *b1, int N, int ncol, int n4, int n2, int n3, const C *__restrict__ tw)
 {
-    int Ns = 1;
-    for (int s = 0; s < nrad; s++) {
-        const int R = rad[s], NR = N / R, tstride = N / (Ns * R);
+    using Rt = decltype(b0->x);
+    int Ns = 1, lg = 0;
+    const int nst = n4 + n2 + n3;
+    for (int s = 0; s < nst; s++) {
+        const int R = s < n4 ? 4 : s < n4 + n2 ? 2 : 3;
+        const int NR = N / R, tstride = N / (Ns * R);
+        const bool p2 = R != 3 || (Ns & (Ns - 1)) == 0;
         for (int t = threadIdx.x; t < NR * ncol; t += blockDim.x) {
-            const int c = t / NR, j = t - c * NR, k = j % Ns;
-            const double2 *x = b0 + c * N;
-            double2 *yv = b1 + c * N;
-            const int d = (j / Ns) * Ns * R + k;
-            double2 v0 = x[j], v1 = x[j + NR];
+            const int c = ncol == 1 ? 0 : t / NR, j = t - c * NR;
+            const int k = p2 ? (j & (Ns - 1)) : j % Ns, jq = p2 ? (j >> lg) : j / Ns;
+            const C *x = b0 + c * N;
+            C *yv = b1 + c * N;
+            const int d = jq * Ns * R + k;
+            C v0 = x[j], v1 = x[j + NR];
             if (Ns > 1) v1 = cmul(v1, tw[tstride * k]);      // the first stage's twiddles are 1
-            if (R == 2) {
-                yv[d] = make_double2(v0.x + v1.x, v0.y + v1.y);
-                yv[d + Ns] = make_double2(v0.x - v1.x, v0.y - v1.y);
+            if (R == 4) {
+                C v2 = x[j + 2 * NR], v3 = x[j + 3 * NR];
+                if (Ns > 1) {
+                    v2 = cmul(v2, tw[2 * tstride * k]);
+                    v3 = cmul(v3, tw[3 * tstride * k]);
+                }
+                // radix 4: w = -i
+                const C a0 = cadd(v0, v2), a1 = csub(v0, v2), c0 = cadd(v1, v3), c1 = csub(v1, v3);
+                C mc1;
+                mc1.x = c1.y; mc1.y = -c1.x;                            // -i c1
+                yv[d] = cadd(a0, c0);
+                yv[d + Ns] = cadd(a1, mc1);
+                yv[d + 2 * Ns] = csub(a0, c0);
+                yv[d + 3 * Ns] = csub(a1, mc1);
+            } else if (R == 2) {
+                yv[d] = cadd(v0, v1);
+                yv[d + Ns] = csub(v0, v1);
             } else {
                 // radix 3: w = exp(-2 pi i / 3); y1,2 = v0 - (v1 + v2) / 2 -/+ i (sqrt 3 / 2)(v1 - v2)
-                double2 v2 = x[j + 2 * NR];
+                C v2 = x[j + 2 * NR];
                 if (Ns > 1) v2 = cmul(v2, tw[2 * tstride * k]);
-                const double2 t1 = make_double2(v1.x + v2.x, v1.y + v2.y);
-                const double2 t2 = make_double2(v1.x - v2.x, v1.y - v2.y);
-                const double h = 0.86602540378443864676;     // sqrt(3) / 2
-                const double2 m = make_double2(h * t2.y, -h * t2.x); // -i h t2
-                const double2 base = make_double2(v0.x - 0.5 * t1.x, v0.y - 0.5 * t1.y);
-                yv[d] = make_double2(v0.x + t1.x, v0.y + t1.y);
-                yv[d + Ns] = make_double2(base.x + m.x, base.y + m.y);
-                yv[d + 2 * Ns] = make_double2(base.x - m.x, base.y - m.y);
+                const C t1 = cadd(v1, v2), t2 = csub(v1, v2);
+                const Rt h = (Rt)0.86602540378443864676;               // sqrt(3) / 2
+                C m, base;
+                m.x = h * t2.y; m.y = -h * t2.x;                        // -i h t2
+                base.x = v0.x - (Rt)0.5 * t1.x;
+                base.y = v0.y - (Rt)0.5 * t1.y;
+                yv[d] = cadd(v0, t1);
+                yv[d + Ns] = cadd(base, m);
+                yv[d + 2 * Ns] = csub(base, m);
             }
         }
         __syncthreads();
-        double2 *tmp = b0;
+        C *tmp = b0;
         b0 = b1;
         b1 = tmp;
         Ns *= R;
+        lg += R == 4 ? 2 : R == 2 ? 1 : 0;
     }
     return b0;
 }
 
+template <typename R>
 struct DxFwdArgs {
-    const double *u;                      // [3][ny][nz][nx]
-    int ca, cb;                           // the field is u_ca (cb < 0) or u_ca u_cb
+    const R *u;                           // [3][ny][nz][nx]
+    int ca, cb;                           // the field is u_ca (cb < 0) or u_ca u_cb ...
+    int pa;                               // ... times the profile U_pa(y) (pa >= 0, FP32 plans)
+    const double *U;                      // [3][ny] profile subtracted from u (NULL: none)
     int odd;                              // its parity is odd: zero on the walls
     int nx, ny, nz, nxh;
-    int rad[32], nrad;
-    const double2 *tw;
-    double2 *spec;                        // [ny][nz][nxh]
+    int n4, n2, n3;                       // radix-4, -2, -3 stages
+    const cx<R> *tw;
+    cx<R> *spec;                          // [ny][nz][nxh]
 };
 
 // One CTA per (pair of z rows k0 = 2 b, k0 + 1; y row j): the two real rows
 // are transformed together as z = f_k0 + i f_k1, and separated by the
 // symmetry of real transforms: F_k0[m] = (Z[m] + conj Z[N-m]) / 2,
 // F_k1[m] = (Z[m] - conj Z[N-m]) / (2i).
-__global__ void __launch_bounds__(kDiffThreads) dx_forward(const DxFwdArgs a)
+template <typename R>
+__global__ void __launch_bounds__(kXThreads) dx_forward(const DxFwdArgs<R> a)
 {
-    extern __shared__ double2 sbuf[];
+    using C = cx<R>;
+    extern __shared__ __align__(16) unsigned char sraw[];
+    C *b0 = reinterpret_cast<C *>(sraw), *b1 = b0 + a.nx;
     const int k0 = 2 * blockIdx.x, j = blockIdx.y, N = a.nx;
     const bool two = k0 + 1 < a.nz;
-    double2 *b0 = sbuf, *b1 = sbuf + N;
     const size_t plane = (size_t)a.ny * a.nz * a.nx;
     const size_t row = ((size_t)j * a.nz + k0) * a.nx;
     const bool zero = a.odd && (j == 0 || j == a.ny - 1);
+    const R Ua = a.U ? (R)a.U[a.ca * a.ny + j] : (R)0;
+    const R Ub = (a.U && a.cb >= 0) ? (R)a.U[a.cb * a.ny + j] : (R)0;
+    const R Pf = a.pa >= 0 ? (R)a.U[a.pa * a.ny + j] : (R)1;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        double v0 = a.u[a.ca * plane + row + i], v1 = two ? a.u[a.ca * plane + row + N + i] : 0.0;
+        R v0 = a.u[a.ca * plane + row + i] - Ua, v1 = two ? a.u[a.ca * plane + row + N + i] - Ua : (R)0;
         if (a.cb >= 0) {
-            v0 *= a.u[a.cb * plane + row + i];
-            if (two) v1 *= a.u[a.cb * plane + row + N + i];
+            v0 *= a.u[a.cb * plane + row + i] - Ub;
+            if (two) v1 *= a.u[a.cb * plane + row + N + i] - Ub;
         }
-        b0[i] = zero ? make_double2(0.0, 0.0) : make_double2(v0, v1);
+        C z;
+        z.x = zero ? (R)0 : v0 * Pf;
+        z.y = zero ? (R)0 : v1 * Pf;
+        b0[i] = z;
     }
     __syncthreads();
-    const double2 *X = smem_fft(b0, b1, N, 1, a.rad, a.nrad, a.tw);
-    double2 *out = a.spec + ((size_t)j * a.nz + k0) * a.nxh;
+    const C *X = smem_fft(b0, b1, N, 1, a.n4, a.n2, a.n3, a.tw);
+    C *out = a.spec + ((size_t)j * a.nz + k0) * a.nxh;
     for (int m = threadIdx.x; m < a.nxh; m += blockDim.x) {
-        const double2 zm = X[m], zc = X[m == 0 ? 0 : N - m];       // conj taken below
-        out[m] = make_double2(0.5 * (zm.x + zc.x), 0.5 * (zm.y - zc.y));
-        if (two) out[a.nxh + m] = make_double2(0.5 * (zm.y + zc.y), -0.5 * (zm.x - zc.x));
+        const C zm = X[m], zc = X[m == 0 ? 0 : N - m];       // conj taken below
+        C p, q;
+        p.x = (R)0.5 * (zm.x + zc.x); p.y = (R)0.5 * (zm.y - zc.y);
+        q.x = (R)0.5 * (zm.y + zc.y); q.y = (R)-0.5 * (zm.x - zc.x);
+        out[m] = p;
+        if (two) out[a.nxh + m] = q;
     }
 }
 
+template <typename R>
 struct DzArgs {
-    double2 *spec;                        // [ny][nz][nxh]
+    cx<R> *spec;                          // [ny][nz][nxh]
     int nz, nxh, ncol;
-    int rad[32], nrad;
-    const double2 *tw;
+    int n4, n2, n3;                       // radix-4, -2, -3 stages
+    const cx<R> *tw;
     // inverse only: LES rows and output
     const int *jy;
     int rz, nlz;
-    double2 *lesz;                        // [nly][nlz][nxh]
+    cx<R> *lesz;                          // [nly][nlz][nxh]
 };
 
 // Forward z transform in place: one CTA per (group of ncol x modes, y row).
-__global__ void __launch_bounds__(kDiffThreads) dz_forward(const DzArgs a)
+template <typename R>
+__global__ void __launch_bounds__(kDiffThreads) dz_forward(const DzArgs<R> a)
 {
-    extern __shared__ double2 sbuf[];
+    using C = cx<R>;
+    extern __shared__ __align__(16) unsigned char sraw[];
     const int N = a.nz, c0 = blockIdx.x * a.ncol, j = blockIdx.y;
     const int nc = min(a.ncol, a.nxh - c0);
-    double2 *b0 = sbuf, *b1 = sbuf + (size_t)N * a.ncol;
-    double2 *base = a.spec + (size_t)j * N * a.nxh + c0;
+    C *b0 = reinterpret_cast<C *>(sraw), *b1 = b0 + (size_t)N * a.ncol;
+    C *base = a.spec + (size_t)j * N * a.nxh + c0;
     for (int t = threadIdx.x; t < N * a.ncol; t += blockDim.x) {
         const int k = t / a.ncol, c = t - k * a.ncol;
-        b0[c * N + k] = c < nc ? base[(size_t)k * a.nxh + c] : make_double2(0.0, 0.0);
+        b0[c * N + k] = c < nc ? base[(size_t)k * a.nxh + c] : mk<C>(0.0, 0.0);
     }
     __syncthreads();
-    const double2 *Z = smem_fft(b0, b1, N, a.ncol, a.rad, a.nrad, a.tw);
+    const C *Z = smem_fft(b0, b1, N, a.ncol, a.n4, a.n2, a.n3, a.tw);
     for (int t = threadIdx.x; t < N * a.ncol; t += blockDim.x) {
         const int k = t / a.ncol, c = t - k * a.ncol;
         if (c < nc) base[(size_t)k * a.nxh + c] = Z[c * N + k];
@@ -172,51 +243,59 @@ __global__ void __launch_bounds__(kDiffThreads) dz_forward(const DzArgs a)
 // Inverse z transform of the LES rows (conjugate, forward transform,
 // conjugate; the 1/(nx nz) scaling is applied at the end), keeping the LES
 // z nodes.  One CTA per (group of x modes, LES row).
-__global__ void __launch_bounds__(kDiffThreads) dz_inverse(const DzArgs a)
+template <typename R>
+__global__ void __launch_bounds__(kDiffThreads) dz_inverse(const DzArgs<R> a)
 {
-    extern __shared__ double2 sbuf[];
+    using C = cx<R>;
+    extern __shared__ __align__(16) unsigned char sraw[];
     const int N = a.nz, c0 = blockIdx.x * a.ncol, J = blockIdx.y, j = a.jy[J];
     const int nc = min(a.ncol, a.nxh - c0);
-    double2 *b0 = sbuf, *b1 = sbuf + (size_t)N * a.ncol;
-    const double2 *base = a.spec + (size_t)j * N * a.nxh + c0;
+    C *b0 = reinterpret_cast<C *>(sraw), *b1 = b0 + (size_t)N * a.ncol;
+    const C *base = a.spec + (size_t)j * N * a.nxh + c0;
     for (int t = threadIdx.x; t < N * a.ncol; t += blockDim.x) {
         const int k = t / a.ncol, c = t - k * a.ncol;
-        const double2 v = c < nc ? base[(size_t)k * a.nxh + c] : make_double2(0.0, 0.0);
-        b0[c * N + k] = make_double2(v.x, -v.y);
+        C v = c < nc ? base[(size_t)k * a.nxh + c] : mk<C>(0.0, 0.0);
+        v.y = -v.y;
+        b0[c * N + k] = v;
     }
     __syncthreads();
-    const double2 *Z = smem_fft(b0, b1, N, a.ncol, a.rad, a.nrad, a.tw);
-    double2 *out = a.lesz + (size_t)J * a.nlz * a.nxh + c0;
+    const C *Z = smem_fft(b0, b1, N, a.ncol, a.n4, a.n2, a.n3, a.tw);
+    C *out = a.lesz + (size_t)J * a.nlz * a.nxh + c0;
     for (int t = threadIdx.x; t < a.nlz * a.ncol; t += blockDim.x) {
         const int K = t / a.ncol, c = t - K * a.ncol;
-        const double2 v = Z[c * N + K * a.rz];
-        if (c < nc) out[(size_t)K * a.nxh + c] = make_double2(v.x, -v.y);
+        C v = Z[c * N + K * a.rz];
+        v.y = -v.y;
+        if (c < nc) out[(size_t)K * a.nxh + c] = v;
     }
 }
 
+template <typename R>
 struct DyArgs {
-    double2 *spec;                        // [ny][nz][nxh], in place
-    const double *fcp, *finv;             // this parity's Thomas factors [ny][nz][nxh]
+    cx<R> *spec;                          // [ny][nz][nxh], in place
+    const R *fcp, *finv;                  // this parity's Thomas factors [ny][nz][nxh]
     const double *k2x, *k2z, *dyy;        // a^2 k~^2 tables; D_yy [3][ny]
     double a2;
     int ny, nz, nxh, odd;
 };
 
-// The tridiagonal rows for (kz, kx):
-//   -a^2 lo_j v_{j-1} + (1 + a^2 (kx~^2 + kz~^2) - a^2 ce_j) v_j - a^2 up_j v_{j+1} = f_j,
+// The tridiagonal rows for (kz, kx), lam = a^2 (kx~^2 + kz~^2):
+//   -a^2 lo_j v_{j-1} + (1 + lam - a^2 ce_j) v_j - a^2 up_j v_{j+1} = f_j,
 // identity rows on the walls for an odd field.
-__device__ __forceinline__ void dy_row(const DyArgs &a, double lam, int j, double &sub, double &dia, double &sup)
+__device__ __forceinline__ void dy_row(const double *dyy, double a2, int ny, int odd, double lam, int j, double &sub,
+                                       double &dia, double &sup)
 {
-    if (a.odd && (j == 0 || j == a.ny - 1)) { sub = 0.0; dia = 1.0; sup = 0.0; return; }
-    sub = -a.a2 * a.dyy[j];
-    dia = 1.0 + lam - a.a2 * a.dyy[a.ny + j];
-    sup = -a.a2 * a.dyy[2 * a.ny + j];
+    if (odd && (j == 0 || j == ny - 1)) { sub = 0.0; dia = 1.0; sup = 0.0; return; }
+    sub = -a2 * dyy[j];
+    dia = 1.0 + lam - a2 * dyy[ny + j];
+    sup = -a2 * dyy[2 * ny + j];
 }
 
-// Set-up: the LU factors of the Thomas algorithm per line (they depend on
-// the mode and the parity only, not on the field): c_j = sup_j / den_j and
-// 1 / den_j with den_j = dia_j - sub_j c_{j-1}.
-__global__ void __launch_bounds__(kDiffThreads) dy_factor(DyArgs a, double *fcp, double *finv)
+// Set-up, in FP64: the LU factors of the Thomas algorithm per line (they
+// depend on the mode and the parity only, not on the field): c_j = sup_j /
+// den_j and 1 / den_j with den_j = dia_j - sub_j c_{j-1}; stored in the
+// plan's precision.
+template <typename R>
+__global__ void __launch_bounds__(kDiffThreads) dy_factor(DyArgs<R> a, R *fcp, R *finv)
 {
     const long line = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const long nline = (long)a.nz * a.nxh;
@@ -226,82 +305,166 @@ __global__ void __launch_bounds__(kDiffThreads) dy_factor(DyArgs a, double *fcp,
     double c = 0.0;
     for (int j = 0; j < a.ny; j++) {
         double sub, dia, sup;
-        dy_row(a, lam, j, sub, dia, sup);
+        dy_row(a.dyy, a.a2, a.ny, a.odd, lam, j, sub, dia, sup);
         const double inv = 1.0 / (dia - sub * c);
         c = sup * inv;
-        fcp[(size_t)j * nline + line] = c;
-        finv[(size_t)j * nline + line] = inv;
+        fcp[(size_t)j * nline + line] = (R)c;
+        finv[(size_t)j * nline + line] = (R)inv;
     }
 }
 
 // Thomas algorithm per (kz, kx) with the precomputed factors: forward
 // d_j = (f_j - sub_j d_{j-1}) / den_j, backward v_j = d_j - c_j v_{j+1}.
-// Threads run along kx (coalesced).
-__global__ void __launch_bounds__(kDiffThreads) dy_solve(const DyArgs a)
+// Threads run along kx (coalesced).  Rows go in blocks of kTb whose loads are
+// issued together (the solve is latency-bound: one line per thread).
+constexpr int kTb = 8;
+
+template <typename R>
+__global__ void __launch_bounds__(kDiffThreads) dy_solve(const DyArgs<R> a)
 {
+    using C = cx<R>;
     const long line = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const long nline = (long)a.nz * a.nxh;
     if (line >= nline) return;
-    double2 d = make_double2(0.0, 0.0);
-    for (int j = 0; j < a.ny; j++) {
-        const size_t o = (size_t)j * nline + line;
-        const double sub = (a.odd && j == a.ny - 1) ? 0.0 : -a.a2 * a.dyy[j];
-        const double inv = a.finv[o];
-        const double2 f = a.spec[o];
-        d = make_double2((f.x - sub * d.x) * inv, (f.y - sub * d.y) * inv);
-        a.spec[o] = d;
+    C d = mk<C>(0.0, 0.0);
+    for (int j0 = 0; j0 < a.ny; j0 += kTb) {
+        C f[kTb];
+        R inv[kTb];
+#pragma unroll
+        for (int i = 0; i < kTb; i++)
+            if (j0 + i < a.ny) {
+                const size_t o = (size_t)(j0 + i) * nline + line;
+                f[i] = a.spec[o];
+                inv[i] = a.finv[o];
+            }
+#pragma unroll
+        for (int i = 0; i < kTb; i++) {
+            const int j = j0 + i;
+            if (j < a.ny) {
+                const R sub = (a.odd && j == a.ny - 1) ? (R)0 : (R)(-a.a2 * a.dyy[j]);
+                d.x = (f[i].x - sub * d.x) * inv[i];
+                d.y = (f[i].y - sub * d.y) * inv[i];
+                a.spec[(size_t)j * nline + line] = d;
+            }
+        }
     }
-    double2 v = d;
-    for (int j = a.ny - 2; j >= 0; j--) {
-        const size_t o = (size_t)j * nline + line;
-        const double cj = a.fcp[o];
-        const double2 dj = a.spec[o];
-        v = make_double2(dj.x - cj * v.x, dj.y - cj * v.y);
-        a.spec[o] = v;
+    C v = d;
+    for (int j0 = a.ny - 2; j0 >= 0; j0 -= kTb) {
+        C dj[kTb];
+        R cj[kTb];
+#pragma unroll
+        for (int i = 0; i < kTb; i++)
+            if (j0 - i >= 0) {
+                const size_t o = (size_t)(j0 - i) * nline + line;
+                dj[i] = a.spec[o];
+                cj[i] = a.fcp[o];
+            }
+#pragma unroll
+        for (int i = 0; i < kTb; i++) {
+            const int j = j0 - i;
+            if (j >= 0) {
+                v.x = dj[i].x - cj[i] * v.x;
+                v.y = dj[i].y - cj[i] * v.y;
+                a.spec[(size_t)j * nline + line] = v;
+            }
+        }
     }
 }
 
+template <typename R>
 struct DxInvArgs {
-    const double2 *lesz;                  // [nly][nlz][nxh]
-    double *out;                          // [nly][nlz][nlx]
+    const cx<R> *lesz;                    // [nly][nlz][nxh]
+    R *out;                               // [nly][nlz][nlx]
     int nx, nxh, rx, nlx;
     double scale;                         // 1 / (nx nz)
-    int rad[32], nrad;
-    const double2 *tw;
+    int n4, n2, n3;                       // radix-4, -2, -3 stages
+    const cx<R> *tw;
 };
 
 // Inverse x transform of one (LES row, LES z node): the Hermitian spectrum
 // completed from the kept modes, conjugated, transformed, real part at the
 // LES x nodes.
-__global__ void __launch_bounds__(kDiffThreads) dx_inverse(const DxInvArgs a)
+template <typename R>
+__global__ void __launch_bounds__(kXThreads) dx_inverse(const DxInvArgs<R> a)
 {
-    extern __shared__ double2 sbuf[];
+    using C = cx<R>;
+    extern __shared__ __align__(16) unsigned char sraw[];
+    C *b0 = reinterpret_cast<C *>(sraw), *b1 = b0 + a.nx;
     const int K = blockIdx.x, J = blockIdx.y, N = a.nx, nlz = gridDim.x;
-    double2 *b0 = sbuf, *b1 = sbuf + N;
-    const double2 *X = a.lesz + ((size_t)J * nlz + K) * a.nxh;
+    const C *X = a.lesz + ((size_t)J * nlz + K) * a.nxh;
     for (int m = threadIdx.x; m < N; m += blockDim.x) {
-        double2 v;
-        if (m < a.nxh) v = X[m];
-        else {
-            const double2 w = X[N - m];
-            v = make_double2(w.x, -w.y);
-        }
-        b0[m] = make_double2(v.x, -v.y);
+        C v;
+        if (m < a.nxh) { v = X[m]; v.y = -v.y; }
+        else v = X[N - m];                                    // conj of the conjugate-symmetric mode
+        b0[m] = v;
     }
     __syncthreads();
-    const double2 *Y = smem_fft(b0, b1, N, 1, a.rad, a.nrad, a.tw);
-    double *o = a.out + ((size_t)J * nlz + K) * a.nlx;
-    for (int X0 = threadIdx.x; X0 < a.nlx; X0 += blockDim.x) o[X0] = Y[X0 * a.rx].x * a.scale;
+    const C *Y = smem_fft(b0, b1, N, 1, a.n4, a.n2, a.n3, a.tw);
+    R *o = a.out + ((size_t)J * nlz + K) * a.nlx;
+    for (int X0 = threadIdx.x; X0 < a.nlx; X0 += blockDim.x) o[X0] = (R)(Y[X0 * a.rx].x * a.scale);
 }
 
-// Plane means of a velocity component: the zero mode of each y row.
+// Plane means of a velocity component: the zero mode of each y row (FP64 plans).
 __global__ void plane_mean_from_spec(const double2 *spec, int ny, int nz, int nxh, double scale, double *pm)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < ny) pm[j] = spec[(size_t)j * nz * nxh].x * scale;
 }
 
-// ubar_c = F(u_c); T_q = F(u_i u_j) - F(u_i) F(u_j).
+// Plane means U_c(y_j) in FP64 (FP32 plans): one CTA per (j, c), fixed order.
+__global__ void __launch_bounds__(256) plane_mean_sum(const float *__restrict__ u, int ny, int nxz, double *U)
+{
+    __shared__ double sh[256];
+    const int j = blockIdx.x, c = blockIdx.y;
+    const float *row = u + ((size_t)c * ny + j) * nxz;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nxz; i += blockDim.x) s += (double)row[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) U[c * ny + j] = sh[0] / nxz;
+}
+
+// The profiles' filtered terms, FP64: F(U_c) (q < 3) and F(U_a U_b) (q >= 3)
+// solve the kx = kz = 0 system; sampled at the LES rows.
+__global__ void profile_filter(const double *__restrict__ U, const double *__restrict__ dyy, double a2, int ny,
+                               const int *__restrict__ jy, int nly, int p0, int p1, int p2, double *scr, double *FU,
+                               double *FUU)
+{
+    const int q = threadIdx.x;
+    if (q >= 9) return;
+    const int pi[9] = {0, 1, 2, 0, 0, 0, 1, 1, 2}, pj[9] = {-1, -1, -1, 0, 1, 2, 1, 2, 2};
+    const int par[3] = {p0, p1, p2};
+    const int odd = (pj[q] < 0 ? par[pi[q]] : par[pi[q]] * par[pj[q]]) < 0;
+    double *cp = scr + (size_t)q * 2 * ny, *dp = cp + ny;
+    double c = 0.0, d = 0.0;
+    for (int j = 0; j < ny; j++) {
+        double sub, dia, sup;
+        dy_row(dyy, a2, ny, odd, 0.0, j, sub, dia, sup);
+        double f = U[pi[q] * ny + j] * (pj[q] < 0 ? 1.0 : U[pj[q] * ny + j]);
+        if (odd && (j == 0 || j == ny - 1)) f = 0.0;
+        const double inv = 1.0 / (dia - sub * c);
+        c = sup * inv;
+        d = (f - sub * d) * inv;
+        cp[j] = c;
+        dp[j] = d;
+    }
+    double v = d;
+    for (int j = ny - 2; j >= 0; j--) {
+        v = dp[j] - cp[j] * v;
+        dp[j] = v;
+    }
+    for (int J = 0; J < nly; J++) {
+        const double val = dp[jy[J]];
+        if (q < 3) FU[q * nly + J] = val;
+        else FUU[(q - 3) * nly + J] = val;
+    }
+}
+
+// FP64 plans: ubar_c = F(u_c); T_q = F(u_i u_j) - F(u_i) F(u_j).
 __global__ void diff_stress(const double *fld, long n, double *ubar, double *tau)
 {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -314,6 +477,32 @@ __global__ void diff_stress(const double *fld, long n, double *ubar, double *tau
     }
     if (tau)
         for (int q = 0; q < 6; q++) tau[q * n + i] = fld[(3 + q) * n + i] - f[pi[q]] * f[pj[q]];
+}
+
+// FP32 plans: the decomposition's brackets in FP64.  Fields: 0-2 u'_c,
+// 3-8 u'_a u'_b (pair order), 9 + 3a + b U_a u'_b.
+__global__ void diff_recover32(const float *__restrict__ fld, long n, int nplane, const double *__restrict__ FU,
+                               const double *__restrict__ FUU, int nly, float *ubar, float *tau)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int J = (int)(i / nplane);
+    const int pi[6] = {0, 0, 0, 1, 1, 2}, pj[6] = {0, 1, 2, 1, 2, 2};
+    double fu[3], fp[3];
+    for (int c = 0; c < 3; c++) {
+        fu[c] = FU[c * nly + J];
+        fp[c] = (double)fld[c * n + i];
+        ubar[c * n + i] = (float)(fu[c] + fp[c]);
+    }
+    if (!tau) return;
+    for (int q = 0; q < 6; q++) {
+        const int a = pi[q], b = pj[q];
+        const double t = (FUU[q * nly + J] - fu[a] * fu[b])
+                       + ((double)fld[(9 + 3 * a + b) * n + i] - fu[a] * fp[b])
+                       + ((double)fld[(9 + 3 * b + a) * n + i] - fu[b] * fp[a])
+                       + ((double)fld[(3 + q) * n + i] - fp[a] * fp[b]);
+        tau[q * n + i] = (float)t;
+    }
 }
 
 // (1 - a^2 lap) of a velocity field on one grid, the stencils of the filter.
@@ -347,30 +536,118 @@ __global__ void unfilter_kernel(const double *__restrict__ in, double *__restric
     out[idx] = v - a2 * (lx + lz + ly);
 }
 
-bool factor23(int n, int *rad, int *nrad)
+// n = 4^n4 2^n2 3^n3 with n2 <= 1; false if n has another prime factor.
+bool factor423(int n, int *n4, int *n2, int *n3)
 {
-    *nrad = 0;
-    while (n % 3 == 0) { rad[(*nrad)++] = 3; n /= 3; }
-    while (n % 2 == 0) { rad[(*nrad)++] = 2; n /= 2; }
-    return n == 1 && *nrad <= 32;
+    *n4 = *n2 = *n3 = 0;
+    while (n % 4 == 0) { (*n4)++; n /= 4; }
+    while (n % 2 == 0) { (*n2)++; n /= 2; }
+    while (n % 3 == 0) { (*n3)++; n /= 3; }
+    return n == 1;
 }
 
-std::vector<double2> twiddles(int n)
+template <typename C>
+std::vector<C> twiddles(int n)
 {
-    std::vector<double2> t(n);
+    std::vector<C> t(n);
     for (int m = 0; m < n; m++) {
         const long double ang = -2.0L * 3.141592653589793238462643383279503L * m / n;
-        t[m] = make_double2((double)cosl(ang), (double)sinl(ang));
+        t[m].x = (decltype(t[m].x))cosl(ang);
+        t[m].y = (decltype(t[m].x))sinl(ang);
     }
     return t;
+}
+
+template <typename R>
+int diff_setup_typed(ef_plan *p, DiffPlan *d)
+{
+    using C = cx<R>;
+    const int ny = p->ny;
+    const size_t nspec = (size_t)ny * p->nz * d->nxh;
+    const size_t nles = (size_t)p->nly * p->nlz * p->nlx;
+    const auto twx = twiddles<C>(p->nx), twz = twiddles<C>(p->nz);
+    cudaError_t e = cudaSuccess;
+#define DK(x) if (e == cudaSuccess) e = (x)
+    DK(cudaMalloc(&d->twx, sizeof(C) * p->nx));
+    DK(cudaMalloc(&d->twz, sizeof(C) * p->nz));
+    DK(cudaMalloc(&d->spec, sizeof(C) * nspec));
+    DK(cudaMalloc(&d->fcp, sizeof(R) * 2 * nspec));
+    DK(cudaMalloc(&d->finv, sizeof(R) * 2 * nspec));
+    DK(cudaMalloc(&d->lesz, sizeof(C) * (size_t)p->nly * p->nlz * d->nxh));
+    DK(cudaMalloc(&d->fld, sizeof(R) * d->nfield * nles));
+    DK(cudaMemcpy(d->twx, twx.data(), sizeof(C) * p->nx, cudaMemcpyHostToDevice));
+    DK(cudaMemcpy(d->twz, twz.data(), sizeof(C) * p->nz, cudaMemcpyHostToDevice));
+    const int zsm = (int)(2 * sizeof(C) * (size_t)p->nz * d->zcols);
+    DK(cudaFuncSetAttribute(dz_forward<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
+    DK(cudaFuncSetAttribute(dz_inverse<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
+    for (int q = 0; q < 2 && e == cudaSuccess; q++) {
+        DyArgs<R> ya = {};
+        ya.k2x = d->k2x; ya.k2z = d->k2z; ya.dyy = d->dyy; ya.a2 = d->a * d->a;
+        ya.ny = ny; ya.nz = p->nz; ya.nxh = d->nxh; ya.odd = q;
+        const long nline = (long)p->nz * d->nxh;
+        dy_factor<R><<<(unsigned)((nline + kDiffThreads - 1) / kDiffThreads), kDiffThreads>>>(
+            ya, static_cast<R *>(d->fcp) + q * nspec, static_cast<R *>(d->finv) + q * nspec);
+        e = cudaGetLastError();
+    }
+    if (d->fp32) {
+        DK(cudaMalloc(&d->U, sizeof(double) * 3 * ny));
+        DK(cudaMalloc(&d->FU, sizeof(double) * 3 * p->nly));
+        DK(cudaMalloc(&d->FUU, sizeof(double) * 6 * p->nly));
+        DK(cudaMalloc(&d->pscr, sizeof(double) * 18 * ny));
+    }
+    DK(cudaDeviceSynchronize());
+#undef DK
+    if (e != cudaSuccess) return cuda_fail(e, "differential filter setup");
+    return EF_OK;
+}
+
+// One field through the five transform/solve steps into fld row `slot`.
+template <typename R>
+void run_field(ef_plan *p, DiffPlan *d, const R *u, int ca, int cb, int pa, const double *U, int parity, int slot,
+               double *plane_mean_row, cudaStream_t s)
+{
+    using C = cx<R>;
+    const size_t nles = (size_t)p->nlx * p->nly * p->nlz;
+    const size_t nspec = (size_t)p->ny * p->nz * d->nxh;
+    const int xsm = (int)(2 * sizeof(C) * p->nx);
+    const int zsm = (int)(2 * sizeof(C) * (size_t)p->nz * d->zcols);
+    DxFwdArgs<R> xa;
+    xa.u = u; xa.ca = ca; xa.cb = cb; xa.pa = pa; xa.U = U; xa.odd = parity < 0;
+    xa.nx = p->nx; xa.ny = p->ny; xa.nz = p->nz; xa.nxh = d->nxh;
+    xa.n4 = d->n4x; xa.n2 = d->n2x; xa.n3 = d->n3x;
+    xa.tw = static_cast<const C *>(d->twx); xa.spec = static_cast<C *>(d->spec);
+    dx_forward<R><<<dim3((p->nz + 1) / 2, p->ny), kXThreads, xsm, s>>>(xa);
+    DzArgs<R> za;
+    za.spec = static_cast<C *>(d->spec); za.nz = p->nz; za.nxh = d->nxh; za.ncol = d->zcols;
+    za.n4 = d->n4z; za.n2 = d->n2z; za.n3 = d->n3z;
+    za.tw = static_cast<const C *>(d->twz); za.jy = d->jy; za.rz = d->rz; za.nlz = p->nlz;
+    za.lesz = static_cast<C *>(d->lesz);
+    const int zgroups = (d->nxh + d->zcols - 1) / d->zcols;
+    dz_forward<R><<<dim3(zgroups, p->ny), kDiffThreads, zsm, s>>>(za);
+    if (plane_mean_row)
+        plane_mean_from_spec<<<(p->ny + 127) / 128, 128, 0, s>>>(static_cast<const double2 *>(d->spec), p->ny, p->nz,
+                                                                 d->nxh, 1.0 / ((double)p->nx * p->nz), plane_mean_row);
+    DyArgs<R> ya;
+    ya.spec = static_cast<C *>(d->spec); ya.k2x = d->k2x; ya.k2z = d->k2z; ya.dyy = d->dyy;
+    ya.fcp = static_cast<const R *>(d->fcp) + (parity < 0 ? nspec : 0);
+    ya.finv = static_cast<const R *>(d->finv) + (parity < 0 ? nspec : 0);
+    ya.a2 = d->a * d->a; ya.ny = p->ny; ya.nz = p->nz; ya.nxh = d->nxh; ya.odd = parity < 0;
+    const long nline = (long)p->nz * d->nxh;
+    dy_solve<R><<<(unsigned)((nline + kDiffThreads - 1) / kDiffThreads), kDiffThreads, 0, s>>>(ya);
+    dz_inverse<R><<<dim3(zgroups, p->nly), kDiffThreads, zsm, s>>>(za);
+    DxInvArgs<R> ia;
+    ia.lesz = static_cast<const C *>(d->lesz); ia.out = static_cast<R *>(d->fld) + slot * nles;
+    ia.nx = p->nx; ia.nxh = d->nxh; ia.rx = d->rx; ia.nlx = p->nlx; ia.scale = 1.0 / ((double)p->nx * p->nz);
+    ia.n4 = d->n4x; ia.n2 = d->n2x; ia.n3 = d->n3x; ia.tw = static_cast<const C *>(d->twx);
+    dx_inverse<R><<<dim3(p->nlz, p->nly), kXThreads, xsm, s>>>(ia);
 }
 
 }  // namespace
 
 int diff_setup(ef_plan *p, const double *dns_y, const double *les_y)
 {
-    if (p->prec != EF_PREC_FP64) {
-        set_error("the differential filter is implemented in FP64 (EF_PREC_FP64)");
+    if (p->prec != EF_PREC_FP64 && p->prec != EF_PREC_FP32) {
+        set_error("the differential filter is implemented in FP64 and FP32 (EF_PREC_FP64, EF_PREC_FP32)");
         return EF_ERR_UNSUPPORTED;
     }
     if (p->ext != EF_EXT_EVEN_ODD && p->ext != EF_EXT_ODD_EVEN) {
@@ -379,8 +656,8 @@ int diff_setup(ef_plan *p, const double *dns_y, const double *les_y)
     }
     DiffPlan *d = new DiffPlan();
     p->diff = d;
-    if (!factor23(p->nx, d->radx, &d->nradx) || !factor23(p->nz, d->radz, &d->nradz) || p->nx > kDiffMaxN ||
-        p->nz > kDiffMaxN) {
+    if (!factor423(p->nx, &d->n4x, &d->n2x, &d->n3x) || !factor423(p->nz, &d->n4z, &d->n2z, &d->n3z) ||
+        p->nx > kDiffMaxN || p->nz > kDiffMaxN) {
         set_error("the differential filter needs nx and nz of the form 2^p 3^q, at most %d", kDiffMaxN);
         return EF_ERR_SHAPE;
     }
@@ -397,11 +674,14 @@ int diff_setup(ef_plan *p, const double *dns_y, const double *les_y)
         }
         jy[J] = j;
     }
+    d->fp32 = p->prec == EF_PREC_FP32;
+    d->nfield = d->fp32 ? 18 : 9;
     d->a = p->delta / sqrt(40.0);
     d->nxh = p->nx / 2 + 1;
     d->rx = p->nx / p->nlx;
     d->rz = p->nz / p->nlz;
-    d->zcols = p->nz <= 512 ? 4 : 2;
+    // z columns per CTA: shared memory 2 N zcols complex values (<= 48 KB FP32, 96 KB FP64)
+    d->zcols = p->prec == EF_PREC_FP32 ? (p->nz <= 384 ? 8 : 4) : (p->nz <= 512 ? 4 : 2);
     const double a2 = d->a * d->a, hx = p->Lx / p->nx, hz = p->Lz / p->nz;
     std::vector<double> k2x(d->nxh), k2z(p->nz), dyy(3 * (size_t)p->ny, 0.0);
     for (int m = 0; m < d->nxh; m++) k2x[m] = a2 * (2.0 - 2.0 * cos(2.0 * M_PI * m / p->nx)) / (hx * hx);
@@ -424,43 +704,16 @@ int diff_setup(ef_plan *p, const double *dns_y, const double *les_y)
         dyy[ny + j] = ce;
         dyy[2 * ny + j] = up;
     }
-    const auto twx = twiddles(p->nx), twz = twiddles(p->nz);
-    const size_t nspec = (size_t)ny * p->nz * d->nxh;
-    cudaError_t e = cudaSuccess;
-#define DK(x) if (e == cudaSuccess) e = (x)
-    DK(cudaMalloc(&d->twx, sizeof(double2) * p->nx));
-    DK(cudaMalloc(&d->twz, sizeof(double2) * p->nz));
-    DK(cudaMalloc(&d->k2x, sizeof(double) * d->nxh));
-    DK(cudaMalloc(&d->k2z, sizeof(double) * p->nz));
-    DK(cudaMalloc(&d->dyy, sizeof(double) * dyy.size()));
-    DK(cudaMalloc(&d->jy, sizeof(int) * p->nly));
-    DK(cudaMalloc(&d->spec, sizeof(double2) * nspec));
-    DK(cudaMalloc(&d->fcp, sizeof(double) * 2 * nspec));
-    DK(cudaMalloc(&d->finv, sizeof(double) * 2 * nspec));
-    DK(cudaMalloc(&d->lesz, sizeof(double2) * (size_t)p->nly * p->nlz * d->nxh));
-    DK(cudaMalloc(&d->fld, sizeof(double) * 9 * (size_t)p->nly * p->nlz * p->nlx));
-    DK(cudaMemcpy(d->twx, twx.data(), sizeof(double2) * p->nx, cudaMemcpyHostToDevice));
-    DK(cudaMemcpy(d->twz, twz.data(), sizeof(double2) * p->nz, cudaMemcpyHostToDevice));
-    DK(cudaMemcpy(d->k2x, k2x.data(), sizeof(double) * d->nxh, cudaMemcpyHostToDevice));
-    DK(cudaMemcpy(d->k2z, k2z.data(), sizeof(double) * p->nz, cudaMemcpyHostToDevice));
-    DK(cudaMemcpy(d->dyy, dyy.data(), sizeof(double) * dyy.size(), cudaMemcpyHostToDevice));
-    DK(cudaMemcpy(d->jy, jy.data(), sizeof(int) * p->nly, cudaMemcpyHostToDevice));
-    const int zsm = (int)(2 * sizeof(double2) * (size_t)p->nz * d->zcols);
-    DK(cudaFuncSetAttribute(dz_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
-    DK(cudaFuncSetAttribute(dz_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm));
-    for (int q = 0; q < 2 && e == cudaSuccess; q++) {
-        DyArgs ya = {};
-        ya.k2x = d->k2x; ya.k2z = d->k2z; ya.dyy = d->dyy; ya.a2 = a2;
-        ya.ny = ny; ya.nz = p->nz; ya.nxh = d->nxh; ya.odd = q;
-        const long nline = (long)p->nz * d->nxh;
-        dy_factor<<<(unsigned)((nline + kDiffThreads - 1) / kDiffThreads), kDiffThreads>>>(ya, d->fcp + q * nspec,
-                                                                                          d->finv + q * nspec);
-        e = cudaGetLastError();
-    }
-    DK(cudaDeviceSynchronize());
-#undef DK
+    cudaError_t e = cudaMalloc(&d->k2x, sizeof(double) * d->nxh);
+    if (e == cudaSuccess) e = cudaMalloc(&d->k2z, sizeof(double) * p->nz);
+    if (e == cudaSuccess) e = cudaMalloc(&d->dyy, sizeof(double) * dyy.size());
+    if (e == cudaSuccess) e = cudaMalloc(&d->jy, sizeof(int) * p->nly);
+    if (e == cudaSuccess) e = cudaMemcpy(d->k2x, k2x.data(), sizeof(double) * d->nxh, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d->k2z, k2z.data(), sizeof(double) * p->nz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d->dyy, dyy.data(), sizeof(double) * dyy.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d->jy, jy.data(), sizeof(int) * p->nly, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "differential filter setup");
-    return EF_OK;
+    return d->fp32 ? diff_setup_typed<float>(p, d) : diff_setup_typed<double>(p, d);
 }
 
 void diff_destroy(DiffPlan *d)
@@ -468,55 +721,52 @@ void diff_destroy(DiffPlan *d)
     if (!d) return;
     cudaFree(d->twx); cudaFree(d->twz); cudaFree(d->k2x); cudaFree(d->k2z); cudaFree(d->dyy); cudaFree(d->jy);
     cudaFree(d->spec); cudaFree(d->fcp); cudaFree(d->finv); cudaFree(d->lesz); cudaFree(d->fld);
+    cudaFree(d->U); cudaFree(d->FU); cudaFree(d->FUU); cudaFree(d->pscr);
     delete d;
 }
 
 int diff_run(ef_plan *p, int nsnap, const void *u_, void *ubar_, void *tau_, double *plane_mean, bool stress,
              cudaStream_t s)
 {
+    NvtxRange nv("differential filter");
     DiffPlan *d = p->diff;
-    const int nfield = stress ? 9 : 3;
     const size_t npt = (size_t)p->nx * p->ny * p->nz, nles = (size_t)p->nlx * p->nly * p->nlz;
-    const int pi[9] = {0, 1, 2, 0, 0, 0, 1, 1, 2}, pj[9] = {-1, -1, -1, 0, 1, 2, 1, 2, 2};
-    const int xsm = (int)(2 * sizeof(double2) * p->nx);
-    const int zsm = (int)(2 * sizeof(double2) * (size_t)p->nz * d->zcols);
+    const int pi[6] = {0, 0, 0, 1, 1, 2}, pj[6] = {0, 1, 2, 1, 2, 2};
     for (int sn = 0; sn < nsnap; sn++) {
-        const double *u = static_cast<const double *>(u_) + sn * 3 * npt;
-        for (int f = 0; f < nfield; f++) {
-            const int parity = pj[f] < 0 ? p->par[pi[f]] : p->par[pi[f]] * p->par[pj[f]];
-            DxFwdArgs xa;
-            xa.u = u; xa.ca = pi[f]; xa.cb = pj[f]; xa.odd = parity < 0;
-            xa.nx = p->nx; xa.ny = p->ny; xa.nz = p->nz; xa.nxh = d->nxh;
-            memcpy(xa.rad, d->radx, sizeof xa.rad); xa.nrad = d->nradx;
-            xa.tw = d->twx; xa.spec = d->spec;
-            dx_forward<<<dim3((p->nz + 1) / 2, p->ny), kDiffThreads, xsm, s>>>(xa);
-            DzArgs za;
-            za.spec = d->spec; za.nz = p->nz; za.nxh = d->nxh; za.ncol = d->zcols;
-            memcpy(za.rad, d->radz, sizeof za.rad); za.nrad = d->nradz;
-            za.tw = d->twz; za.jy = d->jy; za.rz = d->rz; za.nlz = p->nlz; za.lesz = d->lesz;
-            const int zgroups = (d->nxh + d->zcols - 1) / d->zcols;
-            dz_forward<<<dim3(zgroups, p->ny), kDiffThreads, zsm, s>>>(za);
-            if (f < 3 && plane_mean)
-                plane_mean_from_spec<<<(p->ny + 127) / 128, 128, 0, s>>>(
-                    d->spec, p->ny, p->nz, d->nxh, 1.0 / ((double)p->nx * p->nz), plane_mean + (sn * 3 + f) * p->ny);
-            DyArgs ya;
-            const size_t nspec = (size_t)p->ny * p->nz * d->nxh;
-            ya.spec = d->spec; ya.k2x = d->k2x; ya.k2z = d->k2z; ya.dyy = d->dyy;
-            ya.fcp = d->fcp + (parity < 0 ? nspec : 0);
-            ya.finv = d->finv + (parity < 0 ? nspec : 0);
-            ya.a2 = d->a * d->a; ya.ny = p->ny; ya.nz = p->nz; ya.nxh = d->nxh; ya.odd = parity < 0;
-            const long nline = (long)p->nz * d->nxh;
-            dy_solve<<<(unsigned)((nline + kDiffThreads - 1) / kDiffThreads), kDiffThreads, 0, s>>>(ya);
-            dz_inverse<<<dim3(zgroups, p->nly), kDiffThreads, zsm, s>>>(za);
-            DxInvArgs ia;
-            ia.lesz = d->lesz; ia.out = d->fld + f * nles; ia.nx = p->nx; ia.nxh = d->nxh; ia.rx = d->rx;
-            ia.nlx = p->nlx; ia.scale = 1.0 / ((double)p->nx * p->nz);
-            memcpy(ia.rad, d->radx, sizeof ia.rad); ia.nrad = d->nradx; ia.tw = d->twx;
-            dx_inverse<<<dim3(p->nlz, p->nly), kDiffThreads, xsm, s>>>(ia);
+        if (!d->fp32) {
+            const double *u = static_cast<const double *>(u_) + sn * 3 * npt;
+            for (int c = 0; c < 3; c++)
+                run_field<double>(p, d, u, c, -1, -1, nullptr, p->par[c], c,
+                                  plane_mean ? plane_mean + (sn * 3 + c) * p->ny : nullptr, s);
+            if (stress)
+                for (int q = 0; q < 6; q++)
+                    run_field<double>(p, d, u, pi[q], pj[q], -1, nullptr, p->par[pi[q]] * p->par[pj[q]], 3 + q,
+                                      nullptr, s);
+            double *ubar = static_cast<double *>(ubar_) + sn * 3 * nles;
+            double *tau = stress ? static_cast<double *>(tau_) + sn * 6 * nles : nullptr;
+            diff_stress<<<(unsigned)((nles + 255) / 256), 256, 0, s>>>(static_cast<const double *>(d->fld), (long)nles,
+                                                                      ubar, tau);
+        } else {
+            const float *u = static_cast<const float *>(u_) + sn * 3 * npt;
+            plane_mean_sum<<<dim3(p->ny, 3), 256, 0, s>>>(u, p->ny, p->nx * p->nz, d->U);
+            if (plane_mean)
+                cudaMemcpyAsync(plane_mean + sn * 3 * p->ny, d->U, sizeof(double) * 3 * p->ny,
+                                cudaMemcpyDeviceToDevice, s);
+            profile_filter<<<1, 32, 0, s>>>(d->U, d->dyy, d->a * d->a, p->ny, d->jy, p->nly, p->par[0], p->par[1],
+                                            p->par[2], d->pscr, d->FU, d->FUU);
+            for (int c = 0; c < 3; c++) run_field<float>(p, d, u, c, -1, -1, d->U, p->par[c], c, nullptr, s);
+            if (stress) {
+                for (int q = 0; q < 6; q++)
+                    run_field<float>(p, d, u, pi[q], pj[q], -1, d->U, p->par[pi[q]] * p->par[pj[q]], 3 + q, nullptr, s);
+                for (int a = 0; a < 3; a++)
+                    for (int b = 0; b < 3; b++)       // U_a u'_b
+                        run_field<float>(p, d, u, b, -1, a, d->U, p->par[a] * p->par[b], 9 + 3 * a + b, nullptr, s);
+            }
+            float *ubar = static_cast<float *>(ubar_) + sn * 3 * nles;
+            float *tau = stress ? static_cast<float *>(tau_) + sn * 6 * nles : nullptr;
+            diff_recover32<<<(unsigned)((nles + 255) / 256), 256, 0, s>>>(
+                static_cast<const float *>(d->fld), (long)nles, p->nlx * p->nlz, d->FU, d->FUU, p->nly, ubar, tau);
         }
-        double *ubar = static_cast<double *>(ubar_) + sn * 3 * nles;
-        double *tau = stress ? static_cast<double *>(tau_) + sn * 6 * nles : nullptr;
-        diff_stress<<<(unsigned)((nles + 255) / 256), 256, 0, s>>>(d->fld, (long)nles, ubar, tau);
     }
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EF_OK : cuda_fail(e, "differential filter");

@@ -100,6 +100,52 @@ def test_channel_192_paper_filter():
     assert np.abs(ub[1, 0]).max() == 0.0 and np.abs(ub[1, -1]).max() == 0.0
 
 
+TOL32 = 1e-4                     # u_tau^2, the bar of the FP32 and tensor-core paths
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("ext", [eles.EXT_EVEN_ODD, eles.EXT_ODD_EVEN])
+def test_fp32_matches_reference(name, ext):
+    """FP32 transforms of the fluctuations about the plane means, FP64 profile
+    terms and recovery, against the FP64 reference."""
+    nx, ny, nz, Lx, Lz, nlx, nly, nlz, delta = CASES[name]
+    dns = I.dns_grid(nx, ny, nz, Lx, Lz)
+    les = I.les_grid(dns, nlx, nly, nlz)
+    u = I.channel_velocity(dns, 78)
+    plan = eles.filter_setup(dns, les, delta, kernel=eles.KERNEL_DIFFERENTIAL, extension=ext,
+                             precision=eles.PREC_FP32)
+    dev = torch.device("cuda")
+    ub = torch.empty((3, nly, nlz, nlx), device=dev)
+    tau = torch.empty((6, nly, nlz, nlx), device=dev)
+    pm = torch.zeros((3, ny), device=dev, dtype=torch.float64)
+    uf = torch.from_numpy(u).to(dev, torch.float32)
+    eles.subfilter_stress(plan, uf, ub, tau, pm)
+    torch.cuda.synchronize()
+    ub_ref, tau_ref = D.subfilter_stress(dns, les, delta, uf.double().cpu().numpy(), ext=ext)
+    eu = np.abs(ub.double().cpu().numpy() - ub_ref).max(axis=(1, 2, 3))
+    et = np.abs(tau.double().cpu().numpy() - tau_ref).max(axis=(1, 2, 3))
+    print(f"{name} ext {ext}: max |ubar err| {eu.max():.2e}, max |T err| per component {et}")
+    assert eu.max() <= TOL32 and et.max() <= TOL32
+    assert np.abs(pm.cpu().numpy() - uf.double().cpu().numpy().mean(axis=(2, 3))).max() <= 1e-12 * np.abs(u).max()
+
+
+def test_fp32_channel_192():
+    dns = I.dns_grid(192, 129, 192, 4 * math.pi, 2 * math.pi)
+    les = I.les_grid(dns, 32, 33, 32)
+    u = I.channel_velocity(dns, 1000)
+    plan = eles.filter_setup(dns, les, DELTA_PAPER, kernel=eles.KERNEL_DIFFERENTIAL, precision=eles.PREC_FP32)
+    dev = torch.device("cuda")
+    uf = torch.from_numpy(u).to(dev, torch.float32)
+    ub = torch.empty((3, 33, 32, 32), device=dev)
+    tau = torch.empty((6, 33, 32, 32), device=dev)
+    eles.subfilter_stress(plan, uf, ub, tau)
+    torch.cuda.synchronize()
+    ub_ref, tau_ref = D.subfilter_stress(dns, les, DELTA_PAPER, uf.double().cpu().numpy())
+    et = np.abs(tau.double().cpu().numpy() - tau_ref).max(axis=(1, 2, 3))
+    print(f"192 channel FP32: max |T err| per component {et}")
+    assert np.abs(ub.double().cpu().numpy() - ub_ref).max() <= TOL32 and et.max() <= TOL32
+
+
 def test_batch_and_filter_fields():
     nx, ny, nz, Lx, Lz, nlx, nly, nlz, delta = CASES["radix3"]
     dns = I.dns_grid(nx, ny, nz, Lx, Lz)
@@ -127,7 +173,7 @@ def test_setup_refusals():
     les = I.les_grid(dns, 8, 9, 6)
     K = eles.KERNEL_DIFFERENTIAL
     with pytest.raises(eles.EFError) as e:
-        eles.filter_setup(dns, les, 0.5, kernel=K, precision=eles.PREC_FP32)
+        eles.filter_setup(dns, les, 0.5, kernel=K, precision=eles.PREC_BF16X3)
     assert e.value.code == 7                                   # EF_ERR_UNSUPPORTED
     with pytest.raises(eles.EFError) as e:
         eles.filter_setup(dns, les, 0.5, kernel=K, extension=eles.EXT_NONE, precision=eles.PREC_FP64)
