@@ -262,6 +262,18 @@ def differential_measure(eles, torch, dns, les, u0, stream, timed, peaks):
     ms = timed(lambda: eles.subfilter_stress(plan, ud, ub, tau, stream=stream), k, 1) / k
     assert eles.check_device_error(plan, stream) == 0
     plan.close()
+    # the FP32 form: fluctuations about the plane means in FP32, profiles and recovery in FP64
+    p32 = eles.filter_setup(dns, les, delta_f, kernel=eles.KERNEL_DIFFERENTIAL, precision=1)
+    with torch.cuda.stream(stream):
+        uf = u0.float().contiguous()
+        ub32 = torch.empty((3, les.ny, les.nz, les.nx), device=ud.device)
+        tau32 = torch.empty((6, les.ny, les.nz, les.nx), device=ud.device)
+    torch.cuda.synchronize()
+    ms32 = timed(lambda: eles.subfilter_stress(p32, uf, ub32, tau32, stream=stream), k, 1) / k
+    p32.close()
+    with torch.cuda.stream(stream):
+        err32 = float((tau32.double() - tau).abs().max())
+    torch.cuda.synchronize()
     nxh = dns.nx // 2 + 1
     lg = math.log2
     flop = 9 * (dns.ny * (dns.nz / 2) * 5 * dns.nx * lg(dns.nx)        # forward x, two rows per transform
@@ -278,7 +290,11 @@ def differential_measure(eles, torch, dns, les, u0, stream, timed, peaks):
             "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": dpeak / 1e12, "unit": "TFLOP/s",
                          "frac": ach / dpeak, "flop_per_snapshot": flop,
                          "peak_source": "FP64 FMA rate measured on GB300 (1.68 per SM per clock) x SMs x max clock"},
-            "gpu_launches_per_snapshot": 9 * 5 + 3 + 1}
+            "gpu_launches_per_snapshot": 9 * 5 + 3 + 1,
+            "fp32": {"ms_per_snapshot": ms32, "value": dns.npts / (ms32 / 1e3), "unit": UNIT,
+                     "tau_max_abs_diff_vs_fp64_utau2": err32,
+                     "form": "u', u'u' and U u' (18 fields) through FP32 transforms; profiles and recovery in FP64",
+                     "gpu_launches_per_snapshot": 18 * 5 + 3}}
 
 
 CLOSURE_FLOP_PER_POINT = 2 * (10 * 128 + 128 * 128 + 128 * 128 + 128 * 6)   # 69,632: the four layers' MACs
