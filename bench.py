@@ -284,13 +284,24 @@ def differential_measure(eles, torch, dns, les, u0, stream, timed, peaks):
     nsm = torch.cuda.get_device_properties(ud.device).multi_processor_count
     dpeak = 1.68 * 2 * nsm * peaks.get("sm_max_mhz", 2070.0) * 1e6
     ach = flop / (ms / 1e3)
+    # the FP64 reference on a bounded sample: one 192 x 129 x 192 channel snapshot
+    from oracle import differential as D
+    from paper_1902_02508_gb300 import inputs as I
+    d2 = I.dns_grid(192, 129, 192, 4 * math.pi, 2 * math.pi)
+    l2 = I.les_grid(d2, 32, 33, 32)
+    u2 = I.channel_velocity(d2, 1000)
+    t0 = time.perf_counter()
+    D.subfilter_stress(d2, l2, delta_f, u2)
+    dt = time.perf_counter() - t0
+    cpu = {"value": d2.npts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"one 192x129x192 snapshot -> 32x33x32 (NumPy FFT + Thomas, FP64), {dt:.1f} s"}
     return {"workload": f"differential filter (1 - a^2 lap)^-1, a = 0.1, one {dns.nx}x{dns.ny}x{dns.nz} snapshot "
                         f"-> {les.nx}x{les.ny}x{les.nz}, ubar and T, FP64",
             "ms_per_snapshot": ms, "value": dns.npts / (ms / 1e3), "unit": UNIT,
             "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": dpeak / 1e12, "unit": "TFLOP/s",
                          "frac": ach / dpeak, "flop_per_snapshot": flop,
                          "peak_source": "FP64 FMA rate measured on GB300 (1.68 per SM per clock) x SMs x max clock"},
-            "gpu_launches_per_snapshot": 9 * 5 + 3 + 1,
+            "gpu_launches_per_snapshot": 9 * 5 + 3 + 1, "cpu_baseline": cpu,
             "fp32": {"ms_per_snapshot": ms32, "value": dns.npts / (ms32 / 1e3), "unit": UNIT,
                      "tau_max_abs_diff_vs_fp64_utau2": err32,
                      "form": "u', u'u' and U u' (18 fields) through FP32 transforms; profiles and recovery in FP64",
@@ -343,7 +354,18 @@ def closure_measure(eles, torch, les, ub, tau, stream, timed, exact_ms_per_les_p
     sm_hz = peaks.get("sm_max_mhz", 2070.0) * 1e6
     pts = CLOSURE_POINTS / (ms / 1e3)
     sfu_peak = nsm * sm_hz / CLOSURE_SFU_CLK_PER_POINT
+    # the FP64 reference forward pass on a bounded sample of the same features
+    from oracle import mlp as M
+    params, stats = eles.closure_get_params(cl)
     cl.close()
+    ncpu = 200000
+    Xs = f1m[:ncpu].double().cpu().numpy()
+    t0 = time.perf_counter()
+    M.forward([(W.astype(np.float64), b.astype(np.float64)) for W, b in eles.closure_unpack(params)],
+              (Xs - stats[:10]) / stats[10:20])
+    dt = time.perf_counter() - t0
+    cpu = {"value": ncpu / dt, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{ncpu} points, NumPy FP64 forward pass, {dt:.2f} s"}
     return {"workload": f"MLP 10-128-128-128-6 (SiLU) inference on {CLOSURE_POINTS} LES points "
                         f"(features of the held-out snapshot, repeated)",
             "ms_per_call": ms, "points_per_s": CLOSURE_POINTS / (ms / 1e3),
@@ -362,7 +384,7 @@ def closure_measure(eles, torch, les, ub, tau, stream, timed, exact_ms_per_les_p
                                "train": f"snapshot 0 ({n} LES points), {epochs} epochs, {train_s:.1f} s, "
                                         f"final loss {loss:.4f} (standardised)",
                                "test": "snapshot 1 (another seed)", "guarded_points": nfall},
-            "speedup_vs_exact_per_les_point": exact_ms_per_les_point / (ms / CLOSURE_POINTS),
+            "speedup_vs_exact_per_les_point": exact_ms_per_les_point / (ms / CLOSURE_POINTS), "cpu_baseline": cpu,
             "gpu_launches_per_call": 2}
 
 
