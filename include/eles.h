@@ -418,7 +418,9 @@ int ef_closure_train(ef_closure *closure, const float *feats, const float *tau, 
  * accumulation; standardisation, guard, SiLU and the fallback are fused.
  * A wait inside the kernel that ran out is recorded in the closure's error
  * word: returned here when n_fallback is requested, else read by
- * ef_closure_check_device_error.
+ * ef_closure_check_device_error.  Calls on one closure share its packed
+ * weight image and counters: issue them on one stream (they must not
+ * overlap on the GPU).  n may be any count >= 1 (persistent grid).
  */
 int ef_closure_infer(ef_closure *closure, const float *feats, float *tau_out, long n, const float *exact_tau,
                      long *n_fallback, void *stream);
