@@ -80,18 +80,23 @@ def test_stress_outputs(prec, geom):
     assert eles.check_device_error(plan) == 0
 
 
-def test_differential_outputs():
+@pytest.mark.parametrize("prec", [eles.PREC_FP64, eles.PREC_FP32])
+def test_differential_outputs(prec):
     dns, les = grids(24, 33, 18, 4 * math.pi, 2 * math.pi, 8, 17, 6)
-    plan = eles.filter_setup(dns, les, 0.8, kernel=eles.KERNEL_DIFFERENTIAL, precision=eles.PREC_FP64)
-    u = torch.from_numpy(I.channel_velocity(dns, 4)).cuda()
+    plan = eles.filter_setup(dns, les, 0.8, kernel=eles.KERNEL_DIFFERENTIAL, precision=prec)
+    dt = plan.dtype
+    u = torch.from_numpy(I.channel_velocity(dns, 4)).to("cuda", dt)
     lshape = (les.ny, les.nz, les.nx)
-    ub, tau, pm = Guarded((3,) + lshape, torch.float64), Guarded((6,) + lshape, torch.float64), \
-        Guarded((3, dns.ny), torch.float64)
+    ub, tau, pm = Guarded((3,) + lshape, dt), Guarded((6,) + lshape, dt), Guarded((3, dns.ny), torch.float64)
     eles.subfilter_stress(plan, u, ub.view, tau.view, pm.view)
     ub.check("ubar"), tau.check("tau"), pm.check("plane means")
-    out = Guarded((3, dns.ny, dns.nz, dns.nx), torch.float64)
-    eles.differential_unfilter(dns, 0.8, u, out.view)
-    out.check("unfilter")
+    ub1 = Guarded((3,) + lshape, dt)
+    eles.filter_fields(plan, u, ub1.view)
+    ub1.check("ubar (filter_fields)")
+    if prec == eles.PREC_FP64:
+        out = Guarded((3, dns.ny, dns.nz, dns.nx), torch.float64)
+        eles.differential_unfilter(dns, 0.8, u, out.view)
+        out.check("unfilter")
 
 
 def test_closure_outputs():
