@@ -301,11 +301,11 @@ def differential_measure(eles, torch, dns, les, u0, stream, timed, peaks):
             "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": dpeak / 1e12, "unit": "TFLOP/s",
                          "frac": ach / dpeak, "flop_per_snapshot": flop,
                          "peak_source": "FP64 FMA rate measured on GB300 (1.68 per SM per clock) x SMs x max clock"},
-            "gpu_launches_per_snapshot": 9 * 5 + 3 + 1, "cpu_baseline": cpu,
+            "gpu_launches_per_snapshot": 3 * 5 + 1, "cpu_baseline": cpu,       # 3 groups of 3 fields x 5 steps, stress
             "fp32": {"ms_per_snapshot": ms32, "value": dns.npts / (ms32 / 1e3), "unit": UNIT,
                      "tau_max_abs_diff_vs_fp64_utau2": err32,
                      "form": "u', u'u' and U u' (18 fields) through FP32 transforms; profiles and recovery in FP64",
-                     "gpu_launches_per_snapshot": 18 * 5 + 3}}
+                     "gpu_launches_per_snapshot": 2 + 3 * 5 + 1}}     # profile, 3 groups of 6 x 5 steps, recovery
 
 
 CLOSURE_FLOP_PER_POINT = 2 * (10 * 128 + 128 * 128 + 128 * 128 + 128 * 6)   # 69,632: the four layers' MACs

@@ -51,9 +51,10 @@ struct DiffPlan {
     int rx = 1, rz = 1;                   // DNS nodes per LES node in x and z
     int zcols = 4;                        // columns per CTA in the z transforms
     int nfield = 9;                       // filtered fields per snapshot
-    void *spec = nullptr;                 // [ny][nz][nxh] spectrum of one field
+    int group = 3;                        // fields transformed and solved together (one launch per step)
+    void *spec = nullptr;                 // [group][ny][nz][nxh] spectra of a group of fields
     void *fcp = nullptr, *finv = nullptr; // [2][ny][nz][nxh] Thomas factors per parity (even, odd)
-    void *lesz = nullptr;                 // [nly][nlz][nxh]
+    void *lesz = nullptr;                 // [group][nly][nlz][nxh]
     void *fld = nullptr;                  // [nfield][nly][nlz][nlx] filtered fields of one snapshot
     // FP32 plans: profile U_c(y) (FP64), its filtered terms at the LES rows, solver scratch
     double *U = nullptr;                  // [3][ny]
@@ -66,6 +67,15 @@ namespace {
 constexpr int kDiffThreads = 256;
 constexpr int kXThreads = 128;             // x transforms: N/4 butterflies per radix-4 stage
 constexpr int kDiffMaxN = 1024;
+constexpr int kMaxGroup = 6;
+
+// A group of fields handled by one launch per step (blockIdx.z = member):
+// member z is (u_ca - U_ca) [(u_cb - U_cb)] [U_pa] (profile terms on FP32
+// plans only), of odd parity or not, filtered into row slot of fld.
+struct FieldGroup {
+    int n;
+    int ca[kMaxGroup], cb[kMaxGroup], pa[kMaxGroup], odd[kMaxGroup], slot[kMaxGroup];
+};
 
 template <typename R> struct Cx;
 template <> struct Cx<double> { using T = double2; };
@@ -154,10 +164,8 @@ __device__ C *smem_fft(C *b0, C *b1, int N, int ncol, int n4, int n2, int n3, co
 template <typename R>
 struct DxFwdArgs {
     const R *u;                           // [3][ny][nz][nx]
-    int ca, cb;                           // the field is u_ca (cb < 0) or u_ca u_cb ...
-    int pa;                               // ... times the profile U_pa(y) (pa >= 0, FP32 plans)
+    FieldGroup grp;                       // the fields (member blockIdx.z)
     const double *U;                      // [3][ny] profile subtracted from u (NULL: none)
-    int odd;                              // its parity is odd: zero on the walls
     int nx, ny, nz, nxh;
     int n4, n2, n3;                       // radix-4, -2, -3 stages
     const cx<R> *tw;
@@ -174,19 +182,20 @@ __global__ void __launch_bounds__(kXThreads) dx_forward(const DxFwdArgs<R> a)
     using C = cx<R>;
     extern __shared__ __align__(16) unsigned char sraw[];
     C *b0 = reinterpret_cast<C *>(sraw), *b1 = b0 + a.nx;
-    const int k0 = 2 * blockIdx.x, j = blockIdx.y, N = a.nx;
+    const int k0 = 2 * blockIdx.x, j = blockIdx.y, N = a.nx, g = blockIdx.z;
+    const int ca = a.grp.ca[g], cb = a.grp.cb[g], pa = a.grp.pa[g];
     const bool two = k0 + 1 < a.nz;
     const size_t plane = (size_t)a.ny * a.nz * a.nx;
     const size_t row = ((size_t)j * a.nz + k0) * a.nx;
-    const bool zero = a.odd && (j == 0 || j == a.ny - 1);
-    const R Ua = a.U ? (R)a.U[a.ca * a.ny + j] : (R)0;
-    const R Ub = (a.U && a.cb >= 0) ? (R)a.U[a.cb * a.ny + j] : (R)0;
-    const R Pf = a.pa >= 0 ? (R)a.U[a.pa * a.ny + j] : (R)1;
+    const bool zero = a.grp.odd[g] && (j == 0 || j == a.ny - 1);
+    const R Ua = a.U ? (R)a.U[ca * a.ny + j] : (R)0;
+    const R Ub = (a.U && cb >= 0) ? (R)a.U[cb * a.ny + j] : (R)0;
+    const R Pf = pa >= 0 ? (R)a.U[pa * a.ny + j] : (R)1;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        R v0 = a.u[a.ca * plane + row + i] - Ua, v1 = two ? a.u[a.ca * plane + row + N + i] - Ua : (R)0;
-        if (a.cb >= 0) {
-            v0 *= a.u[a.cb * plane + row + i] - Ub;
-            if (two) v1 *= a.u[a.cb * plane + row + N + i] - Ub;
+        R v0 = a.u[ca * plane + row + i] - Ua, v1 = two ? a.u[ca * plane + row + N + i] - Ua : (R)0;
+        if (cb >= 0) {
+            v0 *= a.u[cb * plane + row + i] - Ub;
+            if (two) v1 *= a.u[cb * plane + row + N + i] - Ub;
         }
         C z;
         z.x = zero ? (R)0 : v0 * Pf;
@@ -195,7 +204,7 @@ __global__ void __launch_bounds__(kXThreads) dx_forward(const DxFwdArgs<R> a)
     }
     __syncthreads();
     const C *X = smem_fft(b0, b1, N, 1, a.n4, a.n2, a.n3, a.tw);
-    C *out = a.spec + ((size_t)j * a.nz + k0) * a.nxh;
+    C *out = a.spec + (size_t)g * a.ny * a.nz * a.nxh + ((size_t)j * a.nz + k0) * a.nxh;
     for (int m = threadIdx.x; m < a.nxh; m += blockDim.x) {
         const C zm = X[m], zc = X[m == 0 ? 0 : N - m];       // conj taken below
         C p, q;
@@ -208,17 +217,18 @@ __global__ void __launch_bounds__(kXThreads) dx_forward(const DxFwdArgs<R> a)
 
 template <typename R>
 struct DzArgs {
-    cx<R> *spec;                          // [ny][nz][nxh]
-    int nz, nxh, ncol;
+    cx<R> *spec;                          // [group][ny][nz][nxh]
+    int ny, nz, nxh, ncol;
     int n4, n2, n3;                       // radix-4, -2, -3 stages
     const cx<R> *tw;
     // inverse only: LES rows and output
     const int *jy;
     int rz, nlz;
-    cx<R> *lesz;                          // [nly][nlz][nxh]
+    cx<R> *lesz;                          // [group][nly][nlz][nxh]
+    int nly;
 };
 
-// Forward z transform in place: one CTA per (group of ncol x modes, y row).
+// Forward z transform in place: one CTA per (group of ncol x modes, y row, member).
 template <typename R>
 __global__ void __launch_bounds__(kDiffThreads) dz_forward(const DzArgs<R> a)
 {
@@ -227,7 +237,7 @@ __global__ void __launch_bounds__(kDiffThreads) dz_forward(const DzArgs<R> a)
     const int N = a.nz, c0 = blockIdx.x * a.ncol, j = blockIdx.y;
     const int nc = min(a.ncol, a.nxh - c0);
     C *b0 = reinterpret_cast<C *>(sraw), *b1 = b0 + (size_t)N * a.ncol;
-    C *base = a.spec + (size_t)j * N * a.nxh + c0;
+    C *base = a.spec + (size_t)blockIdx.z * a.ny * N * a.nxh + (size_t)j * N * a.nxh + c0;
     for (int t = threadIdx.x; t < N * a.ncol; t += blockDim.x) {
         const int k = t / a.ncol, c = t - k * a.ncol;
         b0[c * N + k] = c < nc ? base[(size_t)k * a.nxh + c] : mk<C>(0.0, 0.0);
@@ -251,7 +261,7 @@ __global__ void __launch_bounds__(kDiffThreads) dz_inverse(const DzArgs<R> a)
     const int N = a.nz, c0 = blockIdx.x * a.ncol, J = blockIdx.y, j = a.jy[J];
     const int nc = min(a.ncol, a.nxh - c0);
     C *b0 = reinterpret_cast<C *>(sraw), *b1 = b0 + (size_t)N * a.ncol;
-    const C *base = a.spec + (size_t)j * N * a.nxh + c0;
+    const C *base = a.spec + (size_t)blockIdx.z * a.ny * N * a.nxh + (size_t)j * N * a.nxh + c0;
     for (int t = threadIdx.x; t < N * a.ncol; t += blockDim.x) {
         const int k = t / a.ncol, c = t - k * a.ncol;
         C v = c < nc ? base[(size_t)k * a.nxh + c] : mk<C>(0.0, 0.0);
@@ -260,7 +270,7 @@ __global__ void __launch_bounds__(kDiffThreads) dz_inverse(const DzArgs<R> a)
     }
     __syncthreads();
     const C *Z = smem_fft(b0, b1, N, a.ncol, a.n4, a.n2, a.n3, a.tw);
-    C *out = a.lesz + (size_t)J * a.nlz * a.nxh + c0;
+    C *out = a.lesz + (size_t)blockIdx.z * a.nly * a.nlz * a.nxh + (size_t)J * a.nlz * a.nxh + c0;
     for (int t = threadIdx.x; t < a.nlz * a.ncol; t += blockDim.x) {
         const int K = t / a.ncol, c = t - K * a.ncol;
         C v = Z[c * N + K * a.rz];
@@ -271,11 +281,12 @@ __global__ void __launch_bounds__(kDiffThreads) dz_inverse(const DzArgs<R> a)
 
 template <typename R>
 struct DyArgs {
-    cx<R> *spec;                          // [ny][nz][nxh], in place
-    const R *fcp, *finv;                  // this parity's Thomas factors [ny][nz][nxh]
+    cx<R> *spec;                          // [group][ny][nz][nxh], in place
+    const R *fcp, *finv;                  // Thomas factors [2 parities][ny][nz][nxh]
     const double *k2x, *k2z, *dyy;        // a^2 k~^2 tables; D_yy [3][ny]
     double a2;
-    int ny, nz, nxh, odd;
+    int ny, nz, nxh, odd;                 // odd: the parity (set-up of the factors)
+    FieldGroup grp;                       // the solve: member blockIdx.y and its parity
 };
 
 // The tridiagonal rows for (kz, kx), lam = a^2 (kx~^2 + kz~^2):
@@ -320,12 +331,20 @@ __global__ void __launch_bounds__(kDiffThreads) dy_factor(DyArgs<R> a, R *fcp, R
 constexpr int kTb = 8;
 
 template <typename R>
-__global__ void __launch_bounds__(kDiffThreads) dy_solve(const DyArgs<R> a)
+__global__ void __launch_bounds__(kDiffThreads) dy_solve(const DyArgs<R> a0)
 {
     using C = cx<R>;
     const long line = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long nline = (long)a.nz * a.nxh;
+    const long nline = (long)a0.nz * a0.nxh;
     if (line >= nline) return;
+    // this member's spectrum and the factors of its parity
+    DyArgs<R> a = a0;
+    const int z = blockIdx.y;
+    const size_t nspec = (size_t)a0.ny * nline;
+    a.odd = a0.grp.odd[z];
+    a.spec = a0.spec + (size_t)z * nspec;
+    a.fcp = a0.fcp + (a.odd ? nspec : 0);
+    a.finv = a0.finv + (a.odd ? nspec : 0);
     C d = mk<C>(0.0, 0.0);
     for (int j0 = 0; j0 < a.ny; j0 += kTb) {
         C f[kTb];
@@ -373,8 +392,10 @@ __global__ void __launch_bounds__(kDiffThreads) dy_solve(const DyArgs<R> a)
 
 template <typename R>
 struct DxInvArgs {
-    const cx<R> *lesz;                    // [nly][nlz][nxh]
-    R *out;                               // [nly][nlz][nlx]
+    const cx<R> *lesz;                    // [group][nly][nlz][nxh]
+    R *out;                               // fld [nfield][nly][nlz][nlx]; member z writes row grp.slot[z]
+    FieldGroup grp;
+    int nly;
     int nx, nxh, rx, nlx;
     double scale;                         // 1 / (nx nz)
     int n4, n2, n3;                       // radix-4, -2, -3 stages
@@ -390,8 +411,8 @@ __global__ void __launch_bounds__(kXThreads) dx_inverse(const DxInvArgs<R> a)
     using C = cx<R>;
     extern __shared__ __align__(16) unsigned char sraw[];
     C *b0 = reinterpret_cast<C *>(sraw), *b1 = b0 + a.nx;
-    const int K = blockIdx.x, J = blockIdx.y, N = a.nx, nlz = gridDim.x;
-    const C *X = a.lesz + ((size_t)J * nlz + K) * a.nxh;
+    const int K = blockIdx.x, J = blockIdx.y, N = a.nx, nlz = gridDim.x, z = blockIdx.z;
+    const C *X = a.lesz + (size_t)z * a.nly * nlz * a.nxh + ((size_t)J * nlz + K) * a.nxh;
     for (int m = threadIdx.x; m < N; m += blockDim.x) {
         C v;
         if (m < a.nxh) { v = X[m]; v.y = -v.y; }
@@ -400,7 +421,7 @@ __global__ void __launch_bounds__(kXThreads) dx_inverse(const DxInvArgs<R> a)
     }
     __syncthreads();
     const C *Y = smem_fft(b0, b1, N, 1, a.n4, a.n2, a.n3, a.tw);
-    R *o = a.out + ((size_t)J * nlz + K) * a.nlx;
+    R *o = a.out + (size_t)a.grp.slot[z] * a.nly * nlz * a.nlx + ((size_t)J * nlz + K) * a.nlx;
     for (int X0 = threadIdx.x; X0 < a.nlx; X0 += blockDim.x) o[X0] = (R)(Y[X0 * a.rx].x * a.scale);
 }
 
@@ -570,10 +591,10 @@ int diff_setup_typed(ef_plan *p, DiffPlan *d)
 #define DK(x) if (e == cudaSuccess) e = (x)
     DK(cudaMalloc(&d->twx, sizeof(C) * p->nx));
     DK(cudaMalloc(&d->twz, sizeof(C) * p->nz));
-    DK(cudaMalloc(&d->spec, sizeof(C) * nspec));
+    DK(cudaMalloc(&d->spec, sizeof(C) * nspec * d->group));
     DK(cudaMalloc(&d->fcp, sizeof(R) * 2 * nspec));
     DK(cudaMalloc(&d->finv, sizeof(R) * 2 * nspec));
-    DK(cudaMalloc(&d->lesz, sizeof(C) * (size_t)p->nly * p->nlz * d->nxh));
+    DK(cudaMalloc(&d->lesz, sizeof(C) * (size_t)p->nly * p->nlz * d->nxh * d->group));
     DK(cudaMalloc(&d->fld, sizeof(R) * d->nfield * nles));
     DK(cudaMemcpy(d->twx, twx.data(), sizeof(C) * p->nx, cudaMemcpyHostToDevice));
     DK(cudaMemcpy(d->twz, twz.data(), sizeof(C) * p->nz, cudaMemcpyHostToDevice));
@@ -601,45 +622,75 @@ int diff_setup_typed(ef_plan *p, DiffPlan *d)
     return EF_OK;
 }
 
-// One field through the five transform/solve steps into fld row `slot`.
+// A group of fields through the five transform/solve steps, one launch per
+// step for the whole group (member = blockIdx.z; blockIdx.y in the solve);
+// member m lands in fld row g.slot[m].  With plane_mean set, members 0..2
+// are the velocity components and their plane means are read from the zero
+// modes (FP64 plans).
 template <typename R>
-void run_field(ef_plan *p, DiffPlan *d, const R *u, int ca, int cb, int pa, const double *U, int parity, int slot,
-               double *plane_mean_row, cudaStream_t s)
+void run_group(ef_plan *p, DiffPlan *d, const R *u, const FieldGroup &g, const double *U, double *plane_mean,
+               cudaStream_t s)
 {
     using C = cx<R>;
-    const size_t nles = (size_t)p->nlx * p->nly * p->nlz;
     const size_t nspec = (size_t)p->ny * p->nz * d->nxh;
     const int xsm = (int)(2 * sizeof(C) * p->nx);
     const int zsm = (int)(2 * sizeof(C) * (size_t)p->nz * d->zcols);
     DxFwdArgs<R> xa;
-    xa.u = u; xa.ca = ca; xa.cb = cb; xa.pa = pa; xa.U = U; xa.odd = parity < 0;
+    xa.u = u; xa.grp = g; xa.U = U;
     xa.nx = p->nx; xa.ny = p->ny; xa.nz = p->nz; xa.nxh = d->nxh;
     xa.n4 = d->n4x; xa.n2 = d->n2x; xa.n3 = d->n3x;
     xa.tw = static_cast<const C *>(d->twx); xa.spec = static_cast<C *>(d->spec);
-    dx_forward<R><<<dim3((p->nz + 1) / 2, p->ny), kXThreads, xsm, s>>>(xa);
+    dx_forward<R><<<dim3((p->nz + 1) / 2, p->ny, g.n), kXThreads, xsm, s>>>(xa);
     DzArgs<R> za;
-    za.spec = static_cast<C *>(d->spec); za.nz = p->nz; za.nxh = d->nxh; za.ncol = d->zcols;
+    za.spec = static_cast<C *>(d->spec); za.ny = p->ny; za.nz = p->nz; za.nxh = d->nxh; za.ncol = d->zcols;
     za.n4 = d->n4z; za.n2 = d->n2z; za.n3 = d->n3z;
     za.tw = static_cast<const C *>(d->twz); za.jy = d->jy; za.rz = d->rz; za.nlz = p->nlz;
-    za.lesz = static_cast<C *>(d->lesz);
+    za.lesz = static_cast<C *>(d->lesz); za.nly = p->nly;
     const int zgroups = (d->nxh + d->zcols - 1) / d->zcols;
-    dz_forward<R><<<dim3(zgroups, p->ny), kDiffThreads, zsm, s>>>(za);
-    if (plane_mean_row)
-        plane_mean_from_spec<<<(p->ny + 127) / 128, 128, 0, s>>>(static_cast<const double2 *>(d->spec), p->ny, p->nz,
-                                                                 d->nxh, 1.0 / ((double)p->nx * p->nz), plane_mean_row);
-    DyArgs<R> ya;
+    dz_forward<R><<<dim3(zgroups, p->ny, g.n), kDiffThreads, zsm, s>>>(za);
+    if (plane_mean)
+        for (int c = 0; c < 3; c++)
+            plane_mean_from_spec<<<(p->ny + 127) / 128, 128, 0, s>>>(
+                static_cast<const double2 *>(d->spec) + c * nspec, p->ny, p->nz, d->nxh,
+                1.0 / ((double)p->nx * p->nz), plane_mean + c * p->ny);
+    DyArgs<R> ya = {};
     ya.spec = static_cast<C *>(d->spec); ya.k2x = d->k2x; ya.k2z = d->k2z; ya.dyy = d->dyy;
-    ya.fcp = static_cast<const R *>(d->fcp) + (parity < 0 ? nspec : 0);
-    ya.finv = static_cast<const R *>(d->finv) + (parity < 0 ? nspec : 0);
-    ya.a2 = d->a * d->a; ya.ny = p->ny; ya.nz = p->nz; ya.nxh = d->nxh; ya.odd = parity < 0;
+    ya.fcp = static_cast<const R *>(d->fcp);
+    ya.finv = static_cast<const R *>(d->finv);
+    ya.a2 = d->a * d->a; ya.ny = p->ny; ya.nz = p->nz; ya.nxh = d->nxh; ya.grp = g;
     const long nline = (long)p->nz * d->nxh;
-    dy_solve<R><<<(unsigned)((nline + kDiffThreads - 1) / kDiffThreads), kDiffThreads, 0, s>>>(ya);
-    dz_inverse<R><<<dim3(zgroups, p->nly), kDiffThreads, zsm, s>>>(za);
+    dy_solve<R><<<dim3((unsigned)((nline + kDiffThreads - 1) / kDiffThreads), g.n), kDiffThreads, 0, s>>>(ya);
+    dz_inverse<R><<<dim3(zgroups, p->nly, g.n), kDiffThreads, zsm, s>>>(za);
     DxInvArgs<R> ia;
-    ia.lesz = static_cast<const C *>(d->lesz); ia.out = static_cast<R *>(d->fld) + slot * nles;
+    ia.lesz = static_cast<const C *>(d->lesz); ia.out = static_cast<R *>(d->fld); ia.grp = g; ia.nly = p->nly;
     ia.nx = p->nx; ia.nxh = d->nxh; ia.rx = d->rx; ia.nlx = p->nlx; ia.scale = 1.0 / ((double)p->nx * p->nz);
     ia.n4 = d->n4x; ia.n2 = d->n2x; ia.n3 = d->n3x; ia.tw = static_cast<const C *>(d->twx);
-    dx_inverse<R><<<dim3(p->nlz, p->nly), kXThreads, xsm, s>>>(ia);
+    dx_inverse<R><<<dim3(p->nlz, p->nly, g.n), kXThreads, xsm, s>>>(ia);
+}
+
+// The fields of one snapshot, in fld row order: u'_c (rows 0..2), u'_a u'_b
+// (3..8, pairs (a, b) of the upper triangle) and, on FP32 plans, U_a u'_b
+// (9 + 3 a + b); split into groups of `group` members.  The parity of a
+// product is the product of the parities.
+int snapshot_groups(const ef_plan *p, bool fp32, bool stress, int group, FieldGroup *grp)
+{
+    const int pi[6] = {0, 0, 0, 1, 1, 2}, pj[6] = {0, 1, 2, 1, 2, 2};
+    int n = 0;
+    auto add = [&](int ca, int cb, int pa, int parity) {
+        FieldGroup &g = grp[n / group];
+        const int m = n % group;
+        g.n = m + 1;
+        g.ca[m] = ca; g.cb[m] = cb; g.pa[m] = pa; g.odd[m] = parity < 0; g.slot[m] = n;
+        n++;
+    };
+    for (int c = 0; c < 3; c++) add(c, -1, -1, p->par[c]);
+    if (stress) {
+        for (int q = 0; q < 6; q++) add(pi[q], pj[q], -1, p->par[pi[q]] * p->par[pj[q]]);
+        if (fp32)
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) add(b, -1, a, p->par[a] * p->par[b]);
+    }
+    return (n + group - 1) / group;
 }
 
 }  // namespace
@@ -676,6 +727,7 @@ int diff_setup(ef_plan *p, const double *dns_y, const double *les_y)
     }
     d->fp32 = p->prec == EF_PREC_FP32;
     d->nfield = d->fp32 ? 18 : 9;
+    d->group = d->fp32 ? 6 : 3;
     d->a = p->delta / sqrt(40.0);
     d->nxh = p->nx / 2 + 1;
     d->rx = p->nx / p->nlx;
@@ -731,17 +783,15 @@ int diff_run(ef_plan *p, int nsnap, const void *u_, void *ubar_, void *tau_, dou
     NvtxRange nv("differential filter");
     DiffPlan *d = p->diff;
     const size_t npt = (size_t)p->nx * p->ny * p->nz, nles = (size_t)p->nlx * p->nly * p->nlz;
-    const int pi[6] = {0, 0, 0, 1, 1, 2}, pj[6] = {0, 1, 2, 1, 2, 2};
+    // the first group holds the three velocity components (d->group >= 3)
+    FieldGroup grp[18 / 3];
+    const int ng = snapshot_groups(p, d->fp32, stress, d->group, grp);
     for (int sn = 0; sn < nsnap; sn++) {
         if (!d->fp32) {
             const double *u = static_cast<const double *>(u_) + sn * 3 * npt;
-            for (int c = 0; c < 3; c++)
-                run_field<double>(p, d, u, c, -1, -1, nullptr, p->par[c], c,
-                                  plane_mean ? plane_mean + (sn * 3 + c) * p->ny : nullptr, s);
-            if (stress)
-                for (int q = 0; q < 6; q++)
-                    run_field<double>(p, d, u, pi[q], pj[q], -1, nullptr, p->par[pi[q]] * p->par[pj[q]], 3 + q,
-                                      nullptr, s);
+            for (int k = 0; k < ng; k++)
+                run_group<double>(p, d, u, grp[k], nullptr, (k == 0 && plane_mean) ? plane_mean + sn * 3 * p->ny : nullptr,
+                                  s);
             double *ubar = static_cast<double *>(ubar_) + sn * 3 * nles;
             double *tau = stress ? static_cast<double *>(tau_) + sn * 6 * nles : nullptr;
             diff_stress<<<(unsigned)((nles + 255) / 256), 256, 0, s>>>(static_cast<const double *>(d->fld), (long)nles,
@@ -754,14 +804,7 @@ int diff_run(ef_plan *p, int nsnap, const void *u_, void *ubar_, void *tau_, dou
                                 cudaMemcpyDeviceToDevice, s);
             profile_filter<<<1, 32, 0, s>>>(d->U, d->dyy, d->a * d->a, p->ny, d->jy, p->nly, p->par[0], p->par[1],
                                             p->par[2], d->pscr, d->FU, d->FUU);
-            for (int c = 0; c < 3; c++) run_field<float>(p, d, u, c, -1, -1, d->U, p->par[c], c, nullptr, s);
-            if (stress) {
-                for (int q = 0; q < 6; q++)
-                    run_field<float>(p, d, u, pi[q], pj[q], -1, d->U, p->par[pi[q]] * p->par[pj[q]], 3 + q, nullptr, s);
-                for (int a = 0; a < 3; a++)
-                    for (int b = 0; b < 3; b++)       // U_a u'_b
-                        run_field<float>(p, d, u, b, -1, a, d->U, p->par[a] * p->par[b], 9 + 3 * a + b, nullptr, s);
-            }
+            for (int k = 0; k < ng; k++) run_group<float>(p, d, u, grp[k], d->U, nullptr, s);
             float *ubar = static_cast<float *>(ubar_) + sn * 3 * nles;
             float *tau = stress ? static_cast<float *>(tau_) + sn * 6 * nles : nullptr;
             diff_recover32<<<(unsigned)((nles + 255) / 256), 256, 0, s>>>(
