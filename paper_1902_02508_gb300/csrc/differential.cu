@@ -432,15 +432,45 @@ __global__ void plane_mean_from_spec(const double2 *spec, int ny, int nz, int nx
     if (j < ny) pm[j] = spec[(size_t)j * nz * nxh].x * scale;
 }
 
-// Plane means U_c(y_j) in FP64 (FP32 plans): one CTA per (j, c), fixed order.
+// Plane means U_c(y_j) in FP64 (FP32 plans): one CTA per (j, c), fixed
+// order.  A thread loads blocks of m = 8 of its values at once, sums each
+// in FP32 with the error-free transformation s + e = a + b (Knuth's
+// two-sum), carrying the rounding errors in e, and adds s and e to an FP64
+// total, so FP64 adds and conversions run once per 4 values (FP64
+// throughput, not bandwidth, bounded a plain FP64 sum).  Only the sum of the
+// errors is rounded: at most m^2 u_32^2 (about 2e-13) of the block's largest
+// partial sum.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
 __global__ void __launch_bounds__(256) plane_mean_sum(const float *__restrict__ u, int ny, int nxz, double *U)
 {
+    constexpr int kBlock = 8;
     __shared__ double sh[256];
-    const int j = blockIdx.x, c = blockIdx.y;
+    const int j = blockIdx.x, c = blockIdx.y, nt = blockDim.x;
     const float *row = u + ((size_t)c * ny + j) * nxz;
-    double s = 0.0;
-    for (int i = threadIdx.x; i < nxz; i += blockDim.x) s += (double)row[i];
-    sh[threadIdx.x] = s;
+    double acc = 0.0;
+    for (int i0 = threadIdx.x; i0 < nxz; i0 += kBlock * nt) {
+        float v[kBlock];
+#pragma unroll
+        for (int k = 0; k < kBlock; k++) {             // the block's loads are issued together
+            const int i = i0 + k * nt;
+            v[k] = i < nxz ? __ldg(row + i) : 0.f;
+        }
+        float s = v[0], e = 0.f;
+#pragma unroll
+        for (int k = 1; k < kBlock; k++) {
+            float err;
+            two_sum(s, v[k], s, err);
+            e = __fadd_rn(e, err);
+        }
+        acc += (double)s + (double)e;
+    }
+    sh[threadIdx.x] = acc;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
