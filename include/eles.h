@@ -75,7 +75,11 @@ typedef enum {
  * of these precisions, an extension (Eq. 7 or Eq. 9), nx and nz of the form
  * 2^p 3^q (at most 1024), and LES nodes that are DNS nodes (nx, nz
  * multiples of nlx, nlz; LES y nodes among the DNS y nodes); otherwise
- * ef_filter_setup returns EF_ERR_SHAPE / EF_ERR_ARG / EF_ERR_UNSUPPORTED. */
+ * ef_filter_setup returns EF_ERR_SHAPE / EF_ERR_ARG / EF_ERR_UNSUPPORTED.
+ * The fields of a snapshot are transformed and solved in groups (3 in FP64,
+ * 6 in FP32), so the plan holds the spectra of one group (16 or 8 bytes per
+ * mode, ny nz (nx/2 + 1) modes per field: about 1.2 GB at 512x257x384)
+ * and the Thomas factors of both parities (2 ny nz (nx/2 + 1) pairs). */
 enum { EF_KERNEL_GAUSSIAN = 0, EF_KERNEL_GAUSSIAN_HAT = 1, EF_KERNEL_DIFFERENTIAL = 2 };
 
 /* Wall treatment. */
