@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kDiffThreads) dz_forward(const DzArgs<R> a)
 
 // Inverse z transform of the LES rows (conjugate, forward transform,
 // conjugate; the 1/(nx nz) scaling is applied at the end), keeping the LES
-// z nodes.  One CTA per (group of x modes, LES row).
+// z nodes.  One CTA per (group of x modes, LES row, member).
 template <typename R>
 __global__ void __launch_bounds__(kDiffThreads) dz_inverse(const DzArgs<R> a)
 {
@@ -402,7 +402,7 @@ struct DxInvArgs {
     const cx<R> *tw;
 };
 
-// Inverse x transform of one (LES row, LES z node): the Hermitian spectrum
+// Inverse x transform of one (LES z node, LES row, member): the Hermitian spectrum
 // completed from the kept modes, conjugated, transformed, real part at the
 // LES x nodes.
 template <typename R>
