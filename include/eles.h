@@ -30,6 +30,11 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Calls are asynchronous on it.  Calls that share a plan must
  *    not overlap in time (they share its scratch): issue them on one stream.
+ *  - Host threads: plans are independent, but the first launch of each
+ *    kernel configuration raises that kernel's shared-memory limit through
+ *    an unlocked process-wide cache.  Make the first hot call of plans that
+ *    need different limits from one thread (later calls may come from any
+ *    thread).
  *  - Every call returns an ef_status.  On failure ef_last_error() returns a
  *    thread-local message.  Device-side problems (non-finite input, a wait
  *    that ran out) are recorded in the plan's error word and read back by
