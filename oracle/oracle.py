@@ -14,6 +14,9 @@ Citations are to the paper's sections and equations:
     evaluation of the product kernel;
   * ``direct3d_points`` -- the same quantities by direct three-dimensional
     summation of Eq. 2 at selected LES points;
+  * ``subfilter_stress_decomposed`` -- Eq. 6 again, decomposed about a given
+    profile U(y) (the bracket and deviation forms; a cross-check of the
+    algebra, evaluated with the same 1-D operators);
   * ``mlp_*`` (oracle/mlp.py) -- the learned closure of Sec. 2.1 / Sec. 5.
 """
 from __future__ import annotations
@@ -148,3 +151,56 @@ def direct3d_points(dns, les, delta: float, u, pts, ext: int = EXT_EVEN_ODD):
     if rc:
         raise ValueError(f"or_direct3d_points failed ({rc})")
     return ub, tau
+
+
+def subfilter_stress_decomposed(dns, les, delta: float, u, U, ext: int = EXT_EVEN_ODD, form: str = "bracket"):
+    """ubar and T of Eq. 6 written about a profile U[3][ny] (any profile).
+
+    With u_a = U_a(y) + u'_a, h_f = A_z A_x f for f = u'_a and u'_a u'_b, and
+    the wall-normal operators A^p of each parity p (Eq. 7 or Eq. 9):
+      q_f = A^{p_f} h_f,  AU_a = A^{p_a} U_a,  ubar_a = AU_a + q_a,
+      T_ab = [A^{p_ab}(U_a U_b) - AU_a AU_b] + [C_ab - AU_a q_b]
+           + [C_ba - AU_b q_a] + [q_ab - q_a q_b],
+      C_ab = A^{p_ab} (U_a h_b),  p_ab = p_a p_b,
+    which holds because A_x and A_z reproduce functions of y alone (rows
+    summing to one) and every operator is linear.  form="deviation" writes the
+    cross brackets as
+      C_ab - AU_a q_b = sum_j A^{p_ab}[J][j] (U_a(j) - AU_a(J)) h_b(j)
+                        + [p_a odd] AU_a(J) ((A^{-p_b} - A^{p_b}) h_b)(J).
+    """
+    if form not in ("bracket", "deviation"):
+        raise ValueError("form is 'bracket' or 'deviation'")
+    if ext not in (EXT_EVEN_ODD, EXT_ODD_EVEN):
+        raise ValueError("the decomposition needs a wall extension (Eq. 7 or Eq. 9)")
+    u, U = _f64(u), _f64(U)
+    assert u.shape == (3, dns.ny, dns.nz, dns.nx) and U.shape == (3, dns.ny)
+    Ax = op_periodic(dns.nx, dns.Lx, les.nx, delta)
+    Az = op_periodic(dns.nz, dns.Lz, les.nz, delta)
+    Ay = {p: op_wall(dns.y, les.y, delta, p) for p in (1, -1)}
+    par = (1, -1, 1) if ext == EXT_EVEN_ODD else (-1, 1, -1)
+    eye = np.eye(dns.ny)
+    up = u - U[:, :, None, None]
+    h = [apply_separable(up[a], Ax, eye, Az) for a in range(3)]                 # [ny][nlz][nlx]
+    hh = [apply_separable(up[a] * up[b], Ax, eye, Az) for a, b in PAIRS]
+    ycon = lambda A, f: np.einsum("Jj,jzx->Jzx", A, f)
+    AU = [Ay[par[a]] @ U[a] for a in range(3)]                                    # [nly]
+    q = [ycon(Ay[par[a]], h[a]) for a in range(3)]
+    ubar = np.stack([AU[a][:, None, None] + q[a] for a in range(3)])
+    tau = np.zeros((6, les.ny, les.nz, les.nx))
+    for k, (a, b) in enumerate(PAIRS):
+        pab = par[a] * par[b]
+        A = Ay[pab]
+        qab = ycon(A, hh[k])
+
+        def cross(c, d):                                                          # C_cd - AU_c q_d
+            if form == "bracket":
+                return ycon(A, U[c][:, None, None] * h[d]) - AU[c][:, None, None] * q[d]
+            dev = np.einsum("Jj,jzx->Jzx", A * (U[c][None, :] - AU[c][:, None]), h[d])
+            if par[c] < 0:
+                dev = dev + AU[c][:, None, None] * ycon(Ay[-par[d]] - Ay[par[d]], h[d])
+            return dev
+
+        prof = (A @ (U[a] * U[b]) - AU[a] * AU[b])[:, None, None]
+        tau[k] = prof + cross(a, b) + cross(b, a) + (qab - q[a] * q[b])
+    return ubar, tau
+

@@ -417,3 +417,24 @@ def test_generator_solenoidal_no_slip():
     dvdy = np.gradient(up[1], d.y, axis=0, edge_order=2)
     res = dudx + dvdy + dwdz
     assert np.abs(res[4:-4]).max() < 0.05 * np.abs(dudx).max()
+
+
+@pytest.mark.parametrize("ext", [O.EXT_EVEN_ODD, O.EXT_ODD_EVEN])
+@pytest.mark.parametrize("form", ["bracket", "deviation"])
+def test_decomposition_about_any_profile_matches_eq6(ext, form):
+    """Eq. 6 decomposed about a profile U(y) (the form the GPU recovery uses:
+    brackets of FP64 profile terms and fluctuation contractions, or the
+    deviation form of the tensor-core y pass) equals the plain evaluation to
+    1e-12 of max |T|, for the plane means, the mean of one z-row, and a
+    profile with no relation to the field (odd components nonzero on the walls)."""
+    dns = I.dns_grid(32, 33, 32, 2 * math.pi, math.pi)
+    les = I.les_grid(dns, 8, 9, 8)
+    u = I.channel_velocity(dns, 11)
+    delta = 2 * math.pi / 16
+    ub0, t0 = O.subfilter_stress(dns, les, delta, u, ext=ext)
+    profiles = [u.mean(axis=(2, 3)), u[:, :, 0, :].mean(axis=2),
+                np.stack([3 + 5 * dns.y ** 2, 0.3 * dns.y + 0.2, 1 - dns.y ** 4])]
+    for U in profiles:
+        ub, t = O.subfilter_stress_decomposed(dns, les, delta, u, U, ext=ext, form=form)
+        assert np.abs(ub - ub0).max() <= 1e-12 * np.abs(ub0).max()
+        assert np.abs(t - t0).max() <= 1e-12 * np.abs(t0).max()
