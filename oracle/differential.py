@@ -30,7 +30,9 @@ Functions:
   * ``filter_fft``       -- (D) by the discrete Fourier transform in x and z
     (which diagonalises the periodic stencils: lap -> -(2 - 2 cos(k h)) / h^2)
     and a tridiagonal solve in y per (kx, kz);
-  * ``subfilter_stress`` -- ubar_i and T_ij on the LES grid.
+  * ``subfilter_stress`` -- ubar_i and T_ij on the LES grid;
+  * ``subfilter_stress_decomposed`` -- the same, written about a profile
+    U(y) (a cross-check of the algebra of the fluctuation form).
 """
 from __future__ import annotations
 
@@ -203,3 +205,40 @@ def subfilter_stress(dns, les, delta_f: float, u, ext: int = EXT_EVEN_ODD, solve
         prod = sample(solver(u[i] * u[j], dns.y, dns.Lx, dns.Lz, a, p[i] * p[j]))
         tau[q] = prod - ub[i] * ub[j]
     return ub, tau
+
+
+def subfilter_stress_decomposed(dns, les, delta_f: float, u, U, ext: int = EXT_EVEN_ODD, solver=filter_fft):
+    """ubar and T of Eq. 6 written about a profile U[3][ny] (any profile).
+
+    With u_a = U_a(y) + u'_a and F the filter (linear; on a function of y
+    alone it is the kx = kz = 0 solve):
+      ubar_a = F(U_a) + F(u'_a),
+      T_ab = [F(U_a U_b) - F(U_a) F(U_b)] + [F(U_a u'_b) - F(U_a) F(u'_b)]
+           + [F(U_b u'_a) - F(U_b) F(u'_a)] + [F(u'_a u'_b) - F(u'_a) F(u'_b)],
+    each term filtered with the parity of its product.
+    """
+    u = np.asarray(u, dtype=np.float64)
+    U = np.asarray(U, dtype=np.float64)
+    assert U.shape == (3, dns.ny)
+    a = filter_parameter(delta_f)
+    p = parities(ext)
+    rx, jy, rz = les_indices(dns, les)
+
+    def F(f, parity):
+        return solver(f, dns.y, dns.Lx, dns.Lz, a, parity)[jy][:, ::rz, ::rx]
+
+    shape = u.shape[1:]
+    prof = [np.broadcast_to(U[c][:, None, None], shape) for c in range(3)]
+    up = u - U[:, :, None, None]
+    FU = [F(prof[c], p[c]) for c in range(3)]
+    Fu = [F(up[c], p[c]) for c in range(3)]
+    ub = np.stack([FU[c] + Fu[c] for c in range(3)])
+    tau = np.empty((6,) + ub.shape[1:])
+    for q, (i, j) in enumerate(PAIRS):
+        pij = p[i] * p[j]
+        tau[q] = ((F(prof[i] * prof[j], pij) - FU[i] * FU[j])
+                  + (F(prof[i] * up[j], pij) - FU[i] * Fu[j])
+                  + (F(prof[j] * up[i], pij) - FU[j] * Fu[i])
+                  + (F(up[i] * up[j], pij) - Fu[i] * Fu[j]))
+    return ub, tau
+

@@ -111,6 +111,21 @@ def test_tau_psd_and_filter_parameter():
     assert np.abs(tau2 - tau).max() <= 1e-11 * np.abs(tau).max()
 
 
+@pytest.mark.parametrize("ext", [D.EXT_EVEN_ODD, D.EXT_ODD_EVEN])
+def test_fluctuation_form_matches_eq6(ext):
+    """The fluctuation form of the FP32 path (u', u'u' and U u' filtered, the
+    profile terms solved in y alone) equals the plain evaluation to 1e-12 of
+    max |T|, about the plane means and about an unrelated profile."""
+    dns = I.dns_grid(16, 17, 12, 2 * math.pi, math.pi)
+    les = I.les_grid(dns, 8, 9, 6)
+    u = I.channel_velocity(dns, 13)
+    ub0, t0 = D.subfilter_stress(dns, les, 0.5, u, ext=ext)
+    for U in (u.mean(axis=(2, 3)), np.stack([2 + 4 * dns.y ** 2, 0.5 * dns.y + 0.1, 1 - dns.y ** 4])):
+        ub, t = D.subfilter_stress_decomposed(dns, les, 0.5, u, U, ext=ext)
+        assert np.abs(ub - ub0).max() <= 1e-12 * np.abs(ub0).max()
+        assert np.abs(t - t0).max() <= 1e-12 * np.abs(t0).max()
+
+
 # --- pins against the values Sec. 3 prints (tests/golden/differential_filter_sec3.txt)
 
 def _golden_sec3():
