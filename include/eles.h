@@ -336,6 +336,11 @@ typedef struct ef_batch ef_batch;
 int ef_batch_create(ef_plan *const *plans, const int *nsnap, int n, ef_batch **out);
 int ef_batch_run(ef_batch *batch, const void *const *u, void *const *ubar, void *const *tau, void *stream);
 void ef_batch_destroy(ef_batch *batch);
+/* Number of times the batch has captured its graph (a run re-captures when a
+ * field pointer changed or a plan's scratch or kernel choice changed since the
+ * last capture: ef_plan_reserve growing it, ef_io_create, a larger
+ * ef_batch_create, ef_plan_set_variant, ef_plan_autotune). */
+long ef_batch_captures(const ef_batch *batch);
 
 /*
  * ef_plan_autotune -- time the x-z kernel variants the plan supports (the
@@ -347,8 +352,15 @@ void ef_batch_destroy(ef_batch *batch);
  * tensor cores warp-specialised, which always parks two columns and ignores
  * the column count) and its time.  Synchronises the device.
  * ef_plan_set_variant applies a stored choice (EF_ERR_UNSUPPORTED if the
- * plan cannot run that variant).
+ * plan cannot run that variant).  For EF_PREC_BF16X3 plans the flag
+ * EF_VARIANT_CUDA_CORE_Y may be or-ed into the choice: the y contraction then
+ * runs on the CUDA cores (the pass such a plan takes when the banded
+ * tensor-core tiling does not fit its geometry) after the tensor-core x-z
+ * kernel; without the flag the tensor-core y pass is used where it fits.
+ * Either call invalidates batch graphs that hold the plan (they re-capture
+ * on their next run).
  */
+#define EF_VARIANT_CUDA_CORE_Y 256
 int ef_plan_autotune(ef_plan *plan, const void *u, void *ubar, void *tau, int reps, int *choice, float *best_ms);
 int ef_plan_set_variant(ef_plan *plan, int choice);
 

@@ -207,7 +207,11 @@ def subfilter_stress(dns, les, delta_f: float, u, ext: int = EXT_EVEN_ODD, solve
     return ub, tau
 
 
-def subfilter_stress_decomposed(dns, les, delta_f: float, u, U, ext: int = EXT_EVEN_ODD, solver=filter_fft):
+PLANTS = ("cross_parity", "drop_cross", "profile_parity")
+
+
+def subfilter_stress_decomposed(dns, les, delta_f: float, u, U, ext: int = EXT_EVEN_ODD, solver=filter_fft,
+                                plant=None):
     """ubar and T of Eq. 6 written about a profile U[3][ny] (any profile).
 
     With u_a = U_a(y) + u'_a and F the filter (linear; on a function of y
@@ -216,7 +220,15 @@ def subfilter_stress_decomposed(dns, les, delta_f: float, u, U, ext: int = EXT_E
       T_ab = [F(U_a U_b) - F(U_a) F(U_b)] + [F(U_a u'_b) - F(U_a) F(u'_b)]
            + [F(U_b u'_a) - F(U_b) F(u'_a)] + [F(u'_a u'_b) - F(u'_a) F(u'_b)],
     each term filtered with the parity of its product.
+
+    ``plant`` (tests only) names one deliberate mistake, to show that the
+    comparison with the plain evaluation catches it: "cross_parity" (U_a u'_b
+    filtered with the parity of u'_b instead of p_a p_b), "drop_cross" (the
+    [F(U_b u'_a) - F(U_b) F(u'_a)] bracket left out), "profile_parity"
+    (F(U_2) with the wrong parity).
     """
+    if plant is not None and plant not in PLANTS:
+        raise ValueError(f"plant is one of {PLANTS}")
     u = np.asarray(u, dtype=np.float64)
     U = np.asarray(U, dtype=np.float64)
     assert U.shape == (3, dns.ny)
@@ -230,15 +242,17 @@ def subfilter_stress_decomposed(dns, les, delta_f: float, u, U, ext: int = EXT_E
     shape = u.shape[1:]
     prof = [np.broadcast_to(U[c][:, None, None], shape) for c in range(3)]
     up = u - U[:, :, None, None]
-    FU = [F(prof[c], p[c]) for c in range(3)]
+    FU = [F(prof[c], -p[c] if (plant == "profile_parity" and c == 1) else p[c]) for c in range(3)]
     Fu = [F(up[c], p[c]) for c in range(3)]
     ub = np.stack([FU[c] + Fu[c] for c in range(3)])
     tau = np.empty((6,) + ub.shape[1:])
     for q, (i, j) in enumerate(PAIRS):
         pij = p[i] * p[j]
+        pc = (lambda d: p[d]) if plant == "cross_parity" else (lambda d: pij)
+        second = 0.0 if plant == "drop_cross" else (F(prof[j] * up[i], pc(i)) - FU[j] * Fu[i])
         tau[q] = ((F(prof[i] * prof[j], pij) - FU[i] * FU[j])
-                  + (F(prof[i] * up[j], pij) - FU[i] * Fu[j])
-                  + (F(prof[j] * up[i], pij) - FU[j] * Fu[i])
+                  + (F(prof[i] * up[j], pc(j)) - FU[i] * Fu[j])
+                  + second
                   + (F(up[i] * up[j], pij) - Fu[i] * Fu[j]))
     return ub, tau
 

@@ -17,6 +17,10 @@ Functions:
     ghosts of parity (+, -, +) at the walls (Eq. 8);
   * ``forward`` / ``backward`` -- the MLP and its exact gradients (written out
     layer by layer, no automatic differentiation);
+  * ``adam_init`` / ``adam_step`` -- one update of the Adam method (Kingma and
+    Ba, 2015: exponential moving averages of the gradient and of its square,
+    each divided by its bias factor 1 - beta^t, step lr m_hat / (sqrt(v_hat)
+    + eps)), the optimiser the library trains with;
   * ``gradient_model`` -- the second-moment (gradient) model
     T_ij ~ (Delta^2 / 12) d~bar(u_i)/dx_k d~bar(u_j)/dx_k, the baseline the
     learned closure is compared with.
@@ -78,6 +82,38 @@ def backward(params, cache, Y, T):
         if l > 0:
             d = (d @ W) * silu_prime(Z[l - 1])
     return grads
+
+
+def adam_init(params):
+    """Zero first and second moments and step count 0 for ``params``."""
+    return {"t": 0,
+            "m": [[np.zeros_like(W), np.zeros_like(b)] for W, b in params],
+            "v": [[np.zeros_like(W), np.zeros_like(b)] for W, b in params]}
+
+
+def bias_factors(t, beta1, beta2):
+    """Adam's bias factors 1 - beta1^t and 1 - beta2^t after t steps."""
+    return 1.0 - beta1 ** t, 1.0 - beta2 ** t
+
+
+def adam_step(params, grads, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update in FP64; returns the new parameters (``state`` is
+    updated in place).  With t the new step count:
+      m <- beta1 m + (1 - beta1) g,   v <- beta2 v + (1 - beta2) g^2,
+      w <- w - lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps)."""
+    state["t"] += 1
+    c1, c2 = bias_factors(state["t"], beta1, beta2)
+    out = []
+    for l, (wb, gb) in enumerate(zip(params, grads)):
+        new = []
+        for k in range(2):
+            w, g = wb[k], gb[k]
+            m = beta1 * state["m"][l][k] + (1.0 - beta1) * g
+            v = beta2 * state["v"][l][k] + (1.0 - beta2) * g * g
+            state["m"][l][k], state["v"][l][k] = m, v
+            new.append(w - lr * (m / c1) / (np.sqrt(v / c2) + eps))
+        out.append(tuple(new))
+    return out
 
 
 def les_gradients(ub, les, parity=(1, -1, 1)):

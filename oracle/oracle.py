@@ -153,7 +153,11 @@ def direct3d_points(dns, les, delta: float, u, pts, ext: int = EXT_EVEN_ODD):
     return ub, tau
 
 
-def subfilter_stress_decomposed(dns, les, delta: float, u, U, ext: int = EXT_EVEN_ODD, form: str = "bracket"):
+PLANTS = ("cross_parity", "drop_cross", "swap_cross", "drop_wall_term", "ubar_parity")
+
+
+def subfilter_stress_decomposed(dns, les, delta: float, u, U, ext: int = EXT_EVEN_ODD, form: str = "bracket",
+                                plant: str | None = None):
     """ubar and T of Eq. 6 written about a profile U[3][ny] (any profile).
 
     With u_a = U_a(y) + u'_a, h_f = A_z A_x f for f = u'_a and u'_a u'_b, and
@@ -167,7 +171,17 @@ def subfilter_stress_decomposed(dns, les, delta: float, u, U, ext: int = EXT_EVE
     cross brackets as
       C_ab - AU_a q_b = sum_j A^{p_ab}[J][j] (U_a(j) - AU_a(J)) h_b(j)
                         + [p_a odd] AU_a(J) ((A^{-p_b} - A^{p_b}) h_b)(J).
+
+    ``plant`` (tests only) names one deliberate mistake, to show that the
+    comparison with the plain evaluation catches it: "cross_parity" (cross
+    terms filtered with the fluctuation's parity p_b instead of p_a p_b),
+    "drop_cross" (the [C_ba - AU_b q_a] bracket left out), "swap_cross" (the
+    [C_ab - AU_a q_b] bracket counted twice instead of once per order),
+    "drop_wall_term" (deviation form without the [p_a odd] wall term),
+    "ubar_parity" (AU_a of the second component with the wrong parity).
     """
+    if plant is not None and plant not in PLANTS:
+        raise ValueError(f"plant is one of {PLANTS}")
     if form not in ("bracket", "deviation"):
         raise ValueError("form is 'bracket' or 'deviation'")
     if ext not in (EXT_EVEN_ODD, EXT_ODD_EVEN):
@@ -183,7 +197,7 @@ def subfilter_stress_decomposed(dns, les, delta: float, u, U, ext: int = EXT_EVE
     h = [apply_separable(up[a], Ax, eye, Az) for a in range(3)]                 # [ny][nlz][nlx]
     hh = [apply_separable(up[a] * up[b], Ax, eye, Az) for a, b in PAIRS]
     ycon = lambda A, f: np.einsum("Jj,jzx->Jzx", A, f)
-    AU = [Ay[par[a]] @ U[a] for a in range(3)]                                    # [nly]
+    AU = [Ay[-par[a] if (plant == "ubar_parity" and a == 1) else par[a]] @ U[a] for a in range(3)]   # [nly]
     q = [ycon(Ay[par[a]], h[a]) for a in range(3)]
     ubar = np.stack([AU[a][:, None, None] + q[a] for a in range(3)])
     tau = np.zeros((6, les.ny, les.nz, les.nx))
@@ -193,14 +207,16 @@ def subfilter_stress_decomposed(dns, les, delta: float, u, U, ext: int = EXT_EVE
         qab = ycon(A, hh[k])
 
         def cross(c, d):                                                          # C_cd - AU_c q_d
+            Ac = Ay[par[d]] if plant == "cross_parity" else A
             if form == "bracket":
-                return ycon(A, U[c][:, None, None] * h[d]) - AU[c][:, None, None] * q[d]
-            dev = np.einsum("Jj,jzx->Jzx", A * (U[c][None, :] - AU[c][:, None]), h[d])
-            if par[c] < 0:
+                return ycon(Ac, U[c][:, None, None] * h[d]) - AU[c][:, None, None] * q[d]
+            dev = np.einsum("Jj,jzx->Jzx", Ac * (U[c][None, :] - AU[c][:, None]), h[d])
+            if par[c] < 0 and plant != "drop_wall_term":
                 dev = dev + AU[c][:, None, None] * ycon(Ay[-par[d]] - Ay[par[d]], h[d])
             return dev
 
         prof = (A @ (U[a] * U[b]) - AU[a] * AU[b])[:, None, None]
-        tau[k] = prof + cross(a, b) + cross(b, a) + (qab - q[a] * q[b])
+        second = 0.0 if plant == "drop_cross" else cross(a, b) if plant == "swap_cross" else cross(b, a)
+        tau[k] = prof + cross(a, b) + second + (qab - q[a] * q[b])
     return ubar, tau
 

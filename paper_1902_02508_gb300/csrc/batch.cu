@@ -15,6 +15,8 @@ struct ef_batch {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<const void *> key;   // pointers the graph was captured with
+    std::vector<unsigned> gens;      // the plans' generations at capture
+    long captures = 0;
     int device = 0;
 };
 
@@ -27,6 +29,7 @@ void drop_graph(ef_batch *b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
     b->key.clear();
+    b->gens.clear();
 }
 
 int run_items(ef_batch *b, const void *const *u, void *const *ubar, void *const *tau, cudaStream_t s)
@@ -65,6 +68,8 @@ int ef_batch_create(ef_plan *const *plans, const int *nsnap, int n, ef_batch **o
     return EF_OK;
 }
 
+long ef_batch_captures(const ef_batch *b) { return b ? b->captures : -1; }
+
 void ef_batch_destroy(ef_batch *b)
 {
     if (!b) return;
@@ -83,9 +88,11 @@ int ef_batch_run(ef_batch *b, const void *const *u, void *const *ubar, void *con
         if (((uintptr_t)u[i]) % 16) { set_error("ef_batch_run: u of item %zu not 16-byte aligned", i); return EF_ERR_ARG; }
         key.push_back(u[i]); key.push_back(ubar[i]); key.push_back(tau[i]);
     }
+    std::vector<unsigned> gens;
+    for (ef_plan *p : b->plans) gens.push_back(p->gen);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
-    if (!b->exec || key != b->key) {
+    if (!b->exec || key != b->key || gens != b->gens) {
         drop_graph(b);
         // one eager pass (first-use kernel attributes are set outside capture)
         int rc = run_items(b, u, ubar, tau, b->cap);
@@ -102,6 +109,8 @@ int ef_batch_run(ef_batch *b, const void *const *u, void *const *ubar, void *con
         cudaGraphDestroy(g);
         if (e != cudaSuccess) { b->exec = nullptr; return cuda_fail(e, "graph instantiate"); }
         b->key = key;
+        b->gens = gens;
+        b->captures++;
     }
     if ((e = cudaGraphLaunch(b->exec, s)) != cudaSuccess) return cuda_fail(e, "graph launch");
     return EF_OK;
@@ -117,6 +126,7 @@ int ef_plan_autotune(ef_plan *p, const void *u, void *ubar, void *tau, int reps,
     if (!p || !u || !ubar || !tau) { set_error("ef_plan_autotune: NULL argument"); return EF_ERR_ARG; }
     if (p->diff) { set_error("ef_plan_autotune: the differential filter has one variant"); return EF_ERR_UNSUPPORTED; }
     if (reps < 1) reps = 3;
+    p->gen++;
     struct Cand { bool fused; int xv; int P; };
     std::vector<Cand> cands;
     const Cand orig = {p->fused, p->x_variant, p->P};
@@ -190,6 +200,13 @@ int ef_plan_set_variant(ef_plan *p, int choice)
 {
     if (!p) { set_error("ef_plan_set_variant: NULL plan"); return EF_ERR_ARG; }
     if (p->diff) { set_error("ef_plan_set_variant: the differential filter has one variant"); return EF_ERR_UNSUPPORTED; }
+    if ((choice & EF_VARIANT_CUDA_CORE_Y) && p->prec != EF_PREC_BF16X3) {
+        set_error("ef_plan_set_variant: only split-precision plans have a y choice");
+        return EF_ERR_ARG;
+    }
+    p->gen++;
+    p->ytc_ok = p->ytc_fit && !(choice & EF_VARIANT_CUDA_CORE_Y);
+    choice &= EF_VARIANT_CUDA_CORE_Y - 1;
     const int v = choice / 16, P = choice % 16;
     if (P < 1 || (P & (P - 1)) || P > 8) { set_error("ef_plan_set_variant: bad column count"); return EF_ERR_ARG; }
     if (v == 0) {

@@ -100,6 +100,7 @@ int plan_reserve(ef_plan *p, int nsnap)
         return EF_OK;
     }
     if (nsnap <= p->reserve) return EF_OK;
+    p->gen++;   // the scratch pointers change: graphs holding the old ones are stale
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "reserve");
     cudaFree(p->d_g); cudaFree(p->d_h); cudaFree(p->d_uref); cudaFree(p->d_urefT); cudaFree(p->d_rowsum);

@@ -168,6 +168,8 @@ struct ef_plan {
     float *d_yw32[2] = {nullptr, nullptr};
     int ytaps_max = 0;
     bool ytc_ok = false;          // tensor-core y passes (EF_PREC_BF16X3)
+    bool ytc_fit = false;         // the banded y tiling fits this geometry (ytc_ok unless switched off)
+    unsigned gen = 0;             // bumped whenever scratch or the kernel choice changes (batch graphs re-capture)
     eles::YTcGeom ytc;            // their banded tiling
     uint4 *d_yfrag = nullptr;     // their A fragments, [S][kYOps][kstot][2][32]
     double *d_ygrid = nullptr;    // DNS y nodes on the device

@@ -27,6 +27,7 @@ KERNEL_GAUSSIAN_HAT = 1      # y integral exact against the piecewise-linear int
 KERNEL_DIFFERENTIAL = 2      # (1 - a^2 lap) ubar = u, a^2 = delta^2 / 40 (FP64)
 EXT_EVEN_ODD, EXT_ODD_EVEN, EXT_NONE = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_TF32X2, PREC_BF16X3 = 0, 1, 2, 3
+VARIANT_CUDA_CORE_Y = 256    # or-ed into a variant choice: y contraction on CUDA cores
 
 # every symbol include/eles.h declares
 EXPORTED = ("ef_filter_setup", "ef_plan_destroy", "ef_filter_fields", "ef_subfilter_stress",
@@ -36,7 +37,7 @@ EXPORTED = ("ef_filter_setup", "ef_plan_destroy", "ef_filter_fields", "ef_subfil
             "ef_closure_features", "ef_closure_fit_norm", "ef_closure_train", "ef_closure_infer",
             "ef_closure_gradients", "ef_closure_param_count", "ef_closure_get_params", "ef_closure_set_params",
             "ef_closure_save", "ef_closure_load", "ef_batch_create", "ef_batch_run", "ef_batch_destroy",
-            "ef_plan_autotune", "ef_plan_set_variant", "ef_closure_features_static", "ef_io_create",
+            "ef_batch_captures", "ef_plan_autotune", "ef_plan_set_variant", "ef_closure_features_static", "ef_io_create",
             "ef_closure_check_device_error", "ef_differential_unfilter", "ef_selftest_wait",
             "ef_io_destroy", "ef_subfilter_stress_host", "ef_stats_create", "ef_stats_destroy", "ef_plane_stats",
             "ef_error_field", "ef_error_profile")
@@ -134,6 +135,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             lib.ef_batch_run.restype = i
             lib.ef_batch_destroy.argtypes = [vp]
             lib.ef_batch_destroy.restype = None
+            lib.ef_batch_captures.argtypes = [vp]
+            lib.ef_batch_captures.restype = L
             lib.ef_plan_autotune.argtypes = [vp, vp, vp, vp, i, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float)]
             lib.ef_plan_autotune.restype = i
             lib.ef_plan_set_variant.argtypes = [vp, i]
@@ -485,6 +488,11 @@ def batch_run(batch: Batch, us, ubars, taus, stream=None) -> None:
     pb = (ctypes.c_void_p * n)(*[t.data_ptr() for t in ubars])
     pt = (ctypes.c_void_p * n)(*[t.data_ptr() for t in taus])
     _check(load().ef_batch_run(batch.handle, pu, pb, pt, _stream(stream)))
+
+
+def batch_captures(batch: Batch) -> int:
+    """How many times the batch has captured its CUDA graph."""
+    return int(load().ef_batch_captures(batch.handle))
 
 
 def plan_autotune(plan: Plan, u, ubar, tau, reps: int = 3):

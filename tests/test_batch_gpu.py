@@ -85,3 +85,36 @@ def test_autotune_choices_all_meet_tolerance(tmp_path):
         eles.subfilter_stress(plan, ud, ub, tau)
         torch.cuda.synchronize()
         assert np.abs(tau.double().cpu().numpy() - tau_ref).max() <= 1e-4, choice
+
+
+def test_batch_recaptures_after_scratch_or_variant_change():
+    """A batch graph holds each plan's scratch pointers and kernel choice: after
+    ef_plan_reserve grows a plan's scratch (freeing the old buffers) or
+    ef_plan_set_variant changes its kernel, the next run captures again and
+    the results still match the oracle."""
+    dev = torch.device("cuda")
+    plans, us, ubs, taus, cases = [], [], [], [], []
+    for k, item in enumerate(ITEMS[:2]):
+        dns, les, delta, plan = make(item, eles.PREC_BF16X3)
+        u = I.channel_velocity(dns, 300 + k)[None]
+        plans.append(plan)
+        cases.append((dns, les, delta, u))
+        us.append(torch.from_numpy(u).to(dev, torch.float32))
+        ubs.append(torch.empty((1, 3, les.ny, les.nz, les.nx), device=dev))
+        taus.append(torch.empty((1, 6, les.ny, les.nz, les.nx), device=dev))
+    batch = eles.batch_create(plans, [1, 1])
+    eles.batch_run(batch, us, ubs, taus)
+    eles.batch_run(batch, us, ubs, taus)
+    assert eles.batch_captures(batch) == 1
+    eles.plan_reserve(plans[0], 4)                 # frees and reallocates plan 0's scratch
+    for t in taus:
+        t.fill_(float("nan"))
+    eles.batch_run(batch, us, ubs, taus)
+    assert eles.batch_captures(batch) == 2
+    eles.plan_set_variant(plans[1], 1 * 16 + 4)    # CUDA-core fused kernel
+    eles.batch_run(batch, us, ubs, taus)
+    assert eles.batch_captures(batch) == 3
+    torch.cuda.synchronize()
+    for k, (dns, les, delta, u) in enumerate(cases):
+        _, tau_ref = O.subfilter_stress(dns, les, delta, u[0])
+        assert np.abs(taus[k][0].double().cpu().numpy() - tau_ref).max() <= 1e-4

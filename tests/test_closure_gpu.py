@@ -151,3 +151,40 @@ def test_checkpoint_resume_is_bitwise():
         open(path, "wb").write(bytes(raw))
         with pytest.raises(eles.EFError):
             eles.closure_load(b, path)
+
+
+def test_adam_steps_match_reference():
+    """Two ef_closure_train steps on one mini-batch against the FP64 Adam of the
+    reference (oracle/mlp.adam_step) fed with the library's own gradients at the
+    same weights (ef_closure_gradients, checked against the reference gradients
+    above): every parameter whose gradient is not lost in FP32 rounding within
+    1e-3 of the step size lr; the rest (|g| below 1e-5 of its layer's largest,
+    where Adam's sign-like first step is undetermined) within one step."""
+    dns, les, delta, ubs, taus, feats = dataset()
+    n = 256
+    lr = 1e-3
+    cl = eles.closure_create(batch=n, lr=lr, seed=5)
+    f, t = feats[1][:n].contiguous(), taus[1][:, :n].contiguous()
+    eles.closure_fit_norm(cl, f, t)
+    p0, _ = eles.closure_get_params(cl)
+    ref = [(W.astype(np.float64), b.astype(np.float64)) for W, b in eles.closure_unpack(p0)]
+    state = M.adam_init(ref)
+    small_total = 0
+    for step in range(2):
+        g, _ = eles.closure_gradients(cl, f, t)     # at the current weights
+        grads = [(gW.astype(np.float64), gb.astype(np.float64)) for gW, gb in eles.closure_unpack(g)]
+        eles.closure_train(cl, f, t, epochs=1)      # n == batch: one Adam step per epoch
+        ref = M.adam_step(ref, grads, state, lr)
+        got = eles.closure_unpack(eles.closure_get_params(cl)[0])
+        for l, (gl, rl, gr) in enumerate(zip(got, ref, grads)):
+            gmax = max(np.abs(gr[0]).max(), np.abs(gr[1]).max())
+            for k in range(2):
+                d = np.abs(gl[k] - rl[k])
+                small = np.abs(gr[k]) < 1e-5 * gmax
+                small_total += int(small.sum())
+                assert d[~small].max(initial=0.0) <= 1e-3 * lr, f"step {step + 1} layer {l} part {k}"
+                assert d[small].max(initial=0.0) <= 2.1 * lr, f"step {step + 1} layer {l} part {k}"
+    assert small_total < 0.01 * p0.size
+    # the steps moved the weights by about lr each (the comparison is not vacuous)
+    moved = np.abs(eles.closure_get_params(cl)[0] - p0)
+    assert np.median(moved) > 0.5 * lr

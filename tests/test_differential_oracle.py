@@ -204,3 +204,19 @@ def test_filter_parameter_matches_tophat_second_moment():
     m_y = float((w.sum(axis=(1, 2)) * ys**2).sum())
     for mom in (m_x, m_z, m_y):
         assert abs(mom / m_tophat - 1.0) < 1e-3
+
+
+@pytest.mark.parametrize("plant", D.PLANTS)
+def test_planted_fluctuation_form_mistakes_fail(plant):
+    """Each mistake planted in the fluctuation form (a cross term filtered with
+    the fluctuation's parity, a dropped cross bracket, the wrong parity of the
+    u2 profile) breaks the 1e-12 agreement for at least one profile."""
+    dns = I.dns_grid(16, 17, 12, 2 * math.pi, math.pi)
+    les = I.les_grid(dns, 8, 9, 6)
+    u = I.channel_velocity(dns, 13)
+    ub0, t0 = D.subfilter_stress(dns, les, 0.5, u)
+    worst = 0.0
+    for U in (u.mean(axis=(2, 3)), np.stack([2 + 4 * dns.y ** 2, 0.5 * dns.y + 0.1, 1 - dns.y ** 4])):
+        ub, t = D.subfilter_stress_decomposed(dns, les, 0.5, u, U, plant=plant)
+        worst = max(worst, np.abs(t - t0).max() / np.abs(t0).max(), np.abs(ub - ub0).max() / np.abs(ub0).max())
+    assert worst > 1e-6

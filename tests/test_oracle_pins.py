@@ -438,3 +438,23 @@ def test_decomposition_about_any_profile_matches_eq6(ext, form):
         ub, t = O.subfilter_stress_decomposed(dns, les, delta, u, U, ext=ext, form=form)
         assert np.abs(ub - ub0).max() <= 1e-12 * np.abs(ub0).max()
         assert np.abs(t - t0).max() <= 1e-12 * np.abs(t0).max()
+
+
+@pytest.mark.parametrize("plant", O.PLANTS)
+def test_planted_decomposition_mistakes_fail(plant):
+    """Each mistake planted in the decomposed evaluation (a wrong cross-term or
+    ubar parity, a dropped or doubled cross bracket, the deviation form without
+    its wall term) breaks the 1e-12 agreement with the plain evaluation for at
+    least one of the profiles of the test above."""
+    dns = I.dns_grid(32, 33, 32, 2 * math.pi, math.pi)
+    les = I.les_grid(dns, 8, 9, 8)
+    u = I.channel_velocity(dns, 11)
+    delta = 2 * math.pi / 16
+    ub0, t0 = O.subfilter_stress(dns, les, delta, u)
+    profiles = [u.mean(axis=(2, 3)), np.stack([3 + 5 * dns.y ** 2, 0.3 * dns.y + 0.2, 1 - dns.y ** 4])]
+    form = "deviation" if plant == "drop_wall_term" else "bracket"
+    worst = 0.0
+    for U in profiles:
+        ub, t = O.subfilter_stress_decomposed(dns, les, delta, u, U, form=form, plant=plant)
+        worst = max(worst, np.abs(t - t0).max() / np.abs(t0).max(), np.abs(ub - ub0).max() / np.abs(ub0).max())
+    assert worst > 1e-6

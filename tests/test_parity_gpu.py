@@ -311,3 +311,41 @@ def test_hat_quadrature_matches_oracle(name, prec):
     assert_close(tau.double().cpu().numpy(), tau_ref, tol, "tau")
     # the trapezoid operator differs (the quadrature really changed)
     assert np.abs(eles.plan_weights(plan, 2) - O.op_wall(dns.y, les.y, delta, +1)).max() > 1e-8
+
+
+@pytest.mark.parametrize("name", ["tc", "tc2"])
+def test_cuda_core_y_after_tensor_core_xz(name):
+    """A split-precision plan whose y tiling does not fit runs the CUDA-core y
+    pass after the tensor-core x-z kernel; the same combination, selected with
+    EF_VARIANT_CUDA_CORE_Y on grids where it would fit, meets the FP32 bar."""
+    dns, les, delta, u = case(name, seed=21)
+    ub_ref, tau_ref = O.subfilter_stress(dns, les, delta, u)
+    plan = eles.filter_setup(dns, les, delta, precision=eles.PREC_BF16X3)
+    xv = eles.plan_info(plan, 10)
+    assert xv in (2, 3)
+    eles.plan_set_variant(plan, xv * 16 + 2 | eles.VARIANT_CUDA_CORE_Y)
+    assert eles.plan_info(plan, 13) == 0 and eles.plan_info(plan, 10) == xv
+    dev = torch.device("cuda")
+    ud = torch.from_numpy(u).to(dev, torch.float32)
+    ub = torch.full((3, les.ny, les.nz, les.nx), float("nan"), device=dev)
+    tau = torch.full((6, les.ny, les.nz, les.nx), float("nan"), device=dev)
+    eles.subfilter_stress(plan, ud, ub, tau)
+    torch.cuda.synchronize()
+    assert eles.check_device_error(plan) == 0
+    assert_close(ub.double().cpu().numpy(), ub_ref, TOL32, "ubar")
+    assert_close(tau.double().cpu().numpy(), tau_ref, TOL32, "tau")
+    eles.plan_set_variant(plan, xv * 16 + 2)      # back on the tensor-core y pass
+    assert eles.plan_info(plan, 13) == 1
+
+
+def test_full_size_whole_grid_bf16x3():
+    """512 x 257 x 384 -> 64 x 65 x 48, Delta = Lx / 64, split BF16 on the
+    tensor cores: every LES point of ubar and T against the oracle's separable
+    FP64 evaluation (the bench's workload and launch configuration)."""
+    dns, les, u = big_field()
+    delta = dns.Lx / 64
+    plan, (ub, tau) = run_gpu(dns, les, delta, u, eles.PREC_BF16X3)
+    assert eles.plan_info(plan, 10) == 3 and eles.plan_info(plan, 13) == 1
+    ub_ref, tau_ref = O.subfilter_stress(dns, les, delta, u)
+    assert_close(ub, ub_ref, TOL32, "ubar")
+    assert_close(tau, tau_ref, TOL32, "tau")
