@@ -55,7 +55,7 @@ WORKLOADS = {
     "re550_d64": (512, 257, 384, 2 * math.pi, math.pi, 64, 65, 48, 1 / 64, 4),
     "re550_d32": (512, 257, 384, 2 * math.pi, math.pi, 64, 65, 48, 1 / 32, 4),
 }
-PREC = {"fp32": 1, "fp64": 0, "bf16x3": 3}
+PREC = {"fp32": 1, "fp64": 0, "bf16x3": 3, "tf32x2": 2}
 L2_BYTES = 129e6
 
 
@@ -561,7 +561,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": {"fp32": "f32", "fp64": "f64", "bf16x3": "bf16x3"}[args.precision],
+                "dtype": {"fp32": "f32", "fp64": "f64", "bf16x3": "bf16x3", "tf32x2": "tf32x2"}[args.precision],
                 "data": "synthetic (seeded solenoidal channel fields, Reichardt mean profile)",
                 "config": workload_config(args.workload, args.precision),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64,

@@ -94,12 +94,32 @@ enum {
     EF_EXT_NONE = 2          /* no extension: support cut at the walls (does not commute, Sec. 2.2) */
 };
 
-/* Arithmetic of the filter contractions. */
+/* Arithmetic of the filter contractions.
+ * The split-precision forms (float in/out) contract the fluctuations about a
+ * reference profile U(y) (the mean of each plane's z-row 0; exact algebra of
+ * Eq. 6) on the tensor cores with FP32 accumulation, and form ~bar(u) and T
+ * from FP64 profile terms:
+ *   EF_PREC_BF16X3  x: every field and weight split into two BF16 parts,
+ *                   three products (A_hi B_hi + A_lo B_hi + A_hi B_lo);
+ *   EF_PREC_TF32X2  x: the velocity fluctuations and the weights split into
+ *                   two TF32 parts (three products); the six product fields
+ *                   u'_a u'_b rounded once to TF32 against the split weights
+ *                   (two products);
+ * in both, z and y contract in split BF16 (three products).  A plan of either
+ * form runs the x-z contraction on the tensor cores or is refused with
+ * EF_ERR_UNSUPPORTED: the warp-specialised kernel needs LES x and z nodes at
+ * every r-th DNS node (x stride 4, 8 or 16), nz in {64, 128, 192, 256, 384},
+ * nlz a multiple of 16, nlx a multiple of 16 / (x stride), and a filter that
+ * fits its window (2.5 Delta at most about 13 x strides; wider x filters are
+ * split into 2 or 4 output phases, each a CTA that re-reads the plane);
+ * BF16X3 plans outside it may still run the earlier tensor-core kernel
+ * (x stride 8 with at most 7 outputs per input).  ef_plan_info index 10
+ * tells which kernel runs. */
 enum {
     EF_PREC_FP64 = 0,        /* double in, double out, FP64 throughout */
     EF_PREC_FP32 = 1,        /* float in/out, FP32 contractions on CUDA cores, FP64 recovery */
-    EF_PREC_TF32X2 = 2,      /* reserved */
-    EF_PREC_BF16X3 = 3       /* float in/out, x-contraction on tensor cores with split BF16 operands */
+    EF_PREC_TF32X2 = 2,      /* float in/out, split TF32 x-contraction on tensor cores (above) */
+    EF_PREC_BF16X3 = 3       /* float in/out, split BF16 x-contraction on tensor cores (above) */
 };
 
 /*
@@ -210,8 +230,9 @@ int ef_selftest_wait(ef_plan *plan, long long limit_cycles, int complete, void *
  * row, 10 x-contraction variant (0 generic, 1 banded ring on CUDA cores,
  * 2 tensor cores, 3 tensor cores with warp-specialised producer, x and z
  * roles), 11 x and z fused in one kernel (0/1), 12 reserved snapshots,
- * 13 y-contraction variant (0 CUDA cores, 1 tensor cores, EF_PREC_BF16X3),
- * 14 differential-filter plan (0/1).
+ * 13 y-contraction variant (0 CUDA cores, 1 tensor cores; split-precision
+ * plans), 14 differential-filter plan (0/1), 15 output phases of the
+ * warp-specialised x-z kernel (CTAs per y-plane; 0 when it does not run).
  * Returns EF_ERR_ARG for an unknown index. */
 int ef_plan_info(const ef_plan *plan, int what, long *value);
 
@@ -345,14 +366,15 @@ long ef_batch_captures(const ef_batch *batch);
 /*
  * ef_plan_autotune -- time the x-z kernel variants the plan supports (the
  * unfused kernels; the fused kernel on CUDA cores or, for EF_PREC_BF16X3, on
- * the tensor cores; 2, 4 or 8 columns per z phase) on one sample snapshot u
- * (device, plan precision; ubar, tau are scratch outputs of one snapshot),
- * keep the fastest, and report it as *choice = variant * 16 + columns
- * (variant 0 unfused, 1 fused CUDA cores, 2 fused tensor cores, 3 fused
- * tensor cores warp-specialised, which always parks two columns and ignores
- * the column count) and its time.  Synchronises the device.
+ * the tensor cores; 2, 4 or 8 columns per z phase; for the split precisions
+ * the warp-specialised tensor-core kernel) on one sample snapshot u (device,
+ * plan precision; ubar, tau are scratch outputs of one snapshot), keep the
+ * fastest, and report it as *choice = variant * 16 + columns (variant 0
+ * unfused, 1 fused CUDA cores, 2 fused tensor cores, 3 fused tensor cores
+ * warp-specialised, which ignores the column count) and its time.
+ * Synchronises the device.
  * ef_plan_set_variant applies a stored choice (EF_ERR_UNSUPPORTED if the
- * plan cannot run that variant).  For EF_PREC_BF16X3 plans the flag
+ * plan cannot run that variant).  For split-precision plans the flag
  * EF_VARIANT_CUDA_CORE_Y may be or-ed into the choice: the y contraction then
  * runs on the CUDA cores (the pass such a plan takes when the banded
  * tensor-core tiling does not fit its geometry) after the tensor-core x-z

@@ -132,10 +132,10 @@ int ef_plan_autotune(ef_plan *p, const void *u, void *ubar, void *tau, int reps,
     const Cand orig = {p->fused, p->x_variant, p->P};
     cands.push_back({false, p->rx.ok ? 1 : 0, p->P});
     if (orig.fused) {
-        if (p->tcws_ok) cands.push_back({true, 3, p->P});
+        if (p->ws.ok) cands.push_back({true, 3, p->P});
         for (int xv = 1; xv <= 2; xv++) {
             if (xv == 2 && !p->tc_ok) continue;
-            if (xv == 1 && !fused_supported(p->rx.r, p->rx.D, p->rz.r, p->rz.D)) continue;
+            if (xv == 1 && (!fused_supported(p->rx.r, p->rx.D, p->rz.r, p->rz.D) || !p->nblk_x)) continue;
             for (int P = 2; P <= 8; P *= 2) {
                 const size_t need = xv == 2 ? tc_smem_bytes(P, p->nz, p->tc.KS) : fused_smem_bytes(p->rx.r, P, p->nz);
                 if (need <= 222 * 1024) cands.push_back({true, xv, P});
@@ -196,17 +196,8 @@ int ef_plan_autotune(ef_plan *p, const void *u, void *ubar, void *tau, int reps,
 }
 
 // Apply a choice made earlier (for example one read from a tuning cache).
-int ef_plan_set_variant(ef_plan *p, int choice)
+static int set_x_variant(ef_plan *p, int choice)
 {
-    if (!p) { set_error("ef_plan_set_variant: NULL plan"); return EF_ERR_ARG; }
-    if (p->diff) { set_error("ef_plan_set_variant: the differential filter has one variant"); return EF_ERR_UNSUPPORTED; }
-    if ((choice & EF_VARIANT_CUDA_CORE_Y) && p->prec != EF_PREC_BF16X3) {
-        set_error("ef_plan_set_variant: only split-precision plans have a y choice");
-        return EF_ERR_ARG;
-    }
-    p->gen++;
-    p->ytc_ok = p->ytc_fit && !(choice & EF_VARIANT_CUDA_CORE_Y);
-    choice &= EF_VARIANT_CUDA_CORE_Y - 1;
     const int v = choice / 16, P = choice % 16;
     if (P < 1 || (P & (P - 1)) || P > 8) { set_error("ef_plan_set_variant: bad column count"); return EF_ERR_ARG; }
     if (v == 0) {
@@ -220,7 +211,7 @@ int ef_plan_set_variant(ef_plan *p, int choice)
         return EF_OK;
     }
     if (v == 3) {
-        if (!p->tcws_ok) { set_error("ef_plan_set_variant: warp-specialised kernel unavailable"); return EF_ERR_UNSUPPORTED; }
+        if (!p->ws.ok) { set_error("ef_plan_set_variant: warp-specialised kernel unavailable"); return EF_ERR_UNSUPPORTED; }
         p->fused = true;
         p->x_variant = 3;
         return EF_OK;
@@ -238,6 +229,22 @@ int ef_plan_set_variant(ef_plan *p, int choice)
         if (p->nlz % q == 0) { NQ = q; break; }
     p->NQ = NQ;
     p->ZQs = p->nlz / NQ;
+    return EF_OK;
+}
+
+int ef_plan_set_variant(ef_plan *p, int choice)
+{
+    if (!p) { set_error("ef_plan_set_variant: NULL plan"); return EF_ERR_ARG; }
+    if (p->diff) { set_error("ef_plan_set_variant: the differential filter has one variant"); return EF_ERR_UNSUPPORTED; }
+    const bool split = p->prec == EF_PREC_BF16X3 || p->prec == EF_PREC_TF32X2;
+    if ((choice & EF_VARIANT_CUDA_CORE_Y) && !split) {
+        set_error("ef_plan_set_variant: only split-precision plans have a y choice");
+        return EF_ERR_ARG;
+    }
+    const int rc = set_x_variant(p, choice & (EF_VARIANT_CUDA_CORE_Y - 1));
+    if (rc) return rc;
+    p->ytc_ok = p->ytc_fit && !(choice & EF_VARIANT_CUDA_CORE_Y);
+    p->gen++;
     return EF_OK;
 }
 

@@ -169,6 +169,7 @@ void ef_plan_destroy(ef_plan *p)
     cudaFree(p->d_ytmp);
     cudaFree(p->d_yfrag);
     cudaFree(p->d_zfrag);
+    ws_free(p->ws);
     cudaFree(p->d_err);
     diff_destroy(p->diff);
     for (int t = 0; t < ef_plan::kProfSlots; t++)
@@ -192,8 +193,14 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
     }
     const bool differential = kernel == EF_KERNEL_DIFFERENTIAL;
     if (extension < EF_EXT_EVEN_ODD || extension > EF_EXT_NONE) { set_error("unknown extension %d", extension); return EF_ERR_ARG; }
-    if (precision != EF_PREC_FP64 && precision != EF_PREC_FP32 && precision != EF_PREC_BF16X3) {
-        set_error("precision %d not implemented", precision);
+    if (precision != EF_PREC_FP64 && precision != EF_PREC_FP32 && precision != EF_PREC_BF16X3 &&
+        precision != EF_PREC_TF32X2) {
+        set_error("unknown precision %d", precision);
+        return EF_ERR_UNSUPPORTED;
+    }
+    const bool split = precision == EF_PREC_BF16X3 || precision == EF_PREC_TF32X2;
+    if (split && kernel == EF_KERNEL_DIFFERENTIAL) {
+        set_error("the differential filter runs in FP64 or FP32 (EF_PREC_FP64, EF_PREC_FP32)");
         return EF_ERR_UNSUPPORTED;
     }
     if (les->Lx != dns->Lx || les->Lz != dns->Lz) { set_error("LES and DNS boxes differ"); return EF_ERR_SHAPE; }
@@ -229,6 +236,7 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
         if ((rc = build_ring(p->bz, &p->rz))) goto fail;
         p->x_variant = p->rx.ok ? 1 : 0;
         // FP32 plans use the fused x-z kernel when its ring sizes are instantiated
+        // (CUDA cores); BF16X3 may also run the tensor-core fused kernel (variant 2)
         const bool tc = precision == EF_PREC_BF16X3 && p->rx.ok && p->rz.ok &&
                         tc_supported(p->rx.r, p->rx.D, p->rz.r, p->rz.D, p->nlz);
         if (precision != EF_PREC_FP64 && p->rx.ok && p->rz.ok && p->nz <= kFusedMaxRows && p->nz % 32 == 0 &&
@@ -237,7 +245,7 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
             const int SB = fused_stage_blocks(p->rx.r);
             std::vector<unsigned> zf;
             int zoff = 0;
-            const int KS = tc ? tc_zfrags(p->rz, p->nlz, zf, &zoff, false) : 0;
+            const int KS = tc ? tc_zfrags(p->rz, p->nlz, zf, &zoff) : 0;
             auto smem = [&](int P) {
                 return tc ? tc_smem_bytes(P, p->nz, KS) : fused_smem_bytes(p->rx.r, P, p->nz);
             };
@@ -261,28 +269,26 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
                     p->tc.KS = KS;
                     p->tc.zoff = zoff;
                     if (KS > 0) {
-                        // z-phase A fragments, the rotated x B fragments, the z-phase A
-                        // fragments in pair order
-                        std::vector<unsigned> bv, zfp;
-                        tc_bvar(p->rx, bv);
-                        int zoff2 = 0;
-                        tc_zfrags(p->rz, p->nlz, zfp, &zoff2, true);
-                        const size_t nz4 = zf.size() / 4;
-                        zf.insert(zf.end(), bv.begin(), bv.end());
-                        zf.insert(zf.end(), zfp.begin(), zfp.end());
                         CK(cudaMalloc(&p->d_zfrag, sizeof(unsigned) * zf.size()), "cudaMalloc z fragments");
                         CK(cudaMemcpy(p->d_zfrag, zf.data(), sizeof(unsigned) * zf.size(), cudaMemcpyHostToDevice),
                            "copy z fragments");
                         p->tc.afrag = p->d_zfrag;
-                        p->tc.bvar = p->d_zfrag + nz4;
-                        p->tc.afrag_ws = p->d_zfrag + nz4 + bv.size() / 4;
-                        if (tcws_supported(p->rx.r, p->rx.D, p->rz.r, p->nlz, p->nz) && 2 * zoff <= p->nz &&
-                            tcws_smem_bytes(p->nz, KS) <= 227 * 1024 - 1024) {
-                            p->tcws_ok = true;
-                            p->x_variant = 3;
-                        }
                     }
                 }
+            }
+        }
+        if (split) {
+            // the warp-specialised tensor-core kernel; a split-precision plan never
+            // falls back to CUDA-core contractions by itself
+            const char *why = nullptr;
+            if ((rc = ws_setup(p, &why))) goto fail;
+            if (p->ws.ok) {
+                p->fused = true;
+                p->x_variant = 3;
+            } else if (!p->tc_ok) {
+                set_error("ef_filter_setup: no tensor-core x-z kernel for this plan (%s)", why ? why : "unsupported");
+                rc = EF_ERR_UNSUPPORTED;
+                goto fail;
             }
         }
         p->nzw = (p->nz + 31) / 32;
@@ -432,6 +438,7 @@ int ef_plan_info(const ef_plan *p, int what, long *value)
     case 11: *value = p->fused ? 1 : 0; break;
     case 12: *value = p->reserve; break;
     case 13: *value = p->ytc_ok ? 1 : 0; break;
+    case 15: *value = p->x_variant == 3 ? p->ws.OP : 0; break;
     case 14: *value = p->diff ? 1 : 0; break;
     default: set_error("ef_plan_info: unknown index %d", what); return EF_ERR_ARG;
     }

@@ -63,21 +63,29 @@ struct FusedTCArgs {
     unsigned Bl[64];
     int KS = 0, zoff = 0;          // tensor-core z phase: k-steps per Z tile, window offset (KS 0: CUDA cores)
     const uint4 *afrag = nullptr;  // its A fragments [KS][32][hi, lo] (device)
-    const uint4 *bvar = nullptr;   // rotated x-operator B fragments [4][32] (device; x_variant 3)
-    const uint4 *afrag_ws = nullptr;   // z A fragments in the pre-split pair order (device; x_variant 3)
 };
 bool tc_supported(int rx, int dx, int rz, int dz, int nlz);
 void tc_weights(const Ring &rx, FusedTCArgs *ta);
 size_t tc_smem_bytes(int P, int nz, int KS);
 // Encode the TMA view of a batch of snapshots u [S][3][ny][nz][nx] (host).
 int encode_u_map(const float *u, int nx, int ny, int nz, int nsnap, int box_w, int box_rows, CUtensorMap *map);
-constexpr int kTcwsStageWidth = 16;   // floats per row of a warp-specialised kernel stage
 cudaError_t launch_fused_tc(int rz, int dz, const FusedTCArgs &ta, int nsnap, cudaStream_t st);
-int tc_zfrags(const Ring &rz, int nlz, std::vector<unsigned> &out, int *zoff_out, bool pairperm);
-bool tcws_supported(int rx, int dx, int rz, int nlz, int nz);
-size_t tcws_smem_bytes(int nz, int KS);
-void tc_bvar(const Ring &rx, std::vector<unsigned> &out);
-cudaError_t launch_tcws(const FusedTCArgs &ta, int nsnap, cudaStream_t st);
+int tc_zfrags(const Ring &rz, int nlz, std::vector<unsigned> &out, int *zoff_out);
+
+// Warp-specialised tensor-core x-z kernel (xz_ws.cuh, x_variant 3) for the
+// split-precision plans: the grid heights it is instantiated for, and its
+// per-plan tables.
+#define ELES_WS_NZ_LIST(X) X(64) X(128) X(192) X(256) X(384)
+struct WsHost {
+    bool ok = false;
+    int mode = 0;                 // ws::MODE_BF16X3 or ws::MODE_TF32X2
+    int OP = 1, OPC = 2, CB = 2;  // output phases, outputs per chunk and phase, x blocks per chunk
+    int bshift = 0, nchunk = 0;   // x stream
+    int xc0[4] = {0, 0, 0, 0};    // first output completed by chunk 0, per phase
+    int KS = 0, zoff = 0;         // tensor-core z phase
+    unsigned *d_afrag = nullptr;  // z A fragments (device)
+    unsigned *d_bvar = nullptr;   // rotated x B fragments (device)
+};
 
 bool fused_supported(int rx, int dx, int rz, int dz);
 int fused_stage_blocks(int rx);
@@ -178,8 +186,8 @@ struct ef_plan {
     int bshift = 0, nblk_x = 0;   // its x stream
     eles::FusedTCArgs tc;         // tensor-core B fragments (x_variant 2)
     bool tc_ok = false;           // the tensor-core x-z kernel supports this plan
-    bool tcws_ok = false;         // so does its warp-specialised form
-    uint4 *d_zfrag = nullptr;     // tensor-core z-phase A fragments
+    eles::WsHost ws;              // the warp-specialised tensor-core kernel (x_variant 3), if ok
+    uint4 *d_zfrag = nullptr;     // tensor-core z-phase A fragments (x_variant 2)
     // scratch owned by the plan, sized for `reserve` snapshots per launch
     int reserve = 0;
     void *d_g = nullptr;          // x-contracted fields of one snapshot [9][ny][nz][nlx] (unfused path)
@@ -225,6 +233,12 @@ inline void prof_mark(const PhaseEvents *pe, int k, cudaStream_t s)
 int run_filter(ef_plan *p, int nsnap, const void *u, void *ubar, void *tau, double *plane_mean,
                bool stress, cudaStream_t s, const PhaseEvents *pe);
 int plan_reserve(ef_plan *p, int nsnap);
+
+// xz_ws.cu
+int ws_setup(ef_plan *p, const char **why);
+void ws_free(WsHost &w);
+int ws_run(const ef_plan *p, int nsnap, const float *u, float *h, double *uref, double *plane_mean, int nf,
+           cudaStream_t st);
 
 // closure_tc.cu: tensor-core inference of the closure MLP.  `image` is a
 // device buffer of closure_tc_image_bytes() that the call repacks from the

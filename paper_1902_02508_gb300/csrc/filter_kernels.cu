@@ -453,15 +453,17 @@ int run_group(ef_plan *p, int ns, const T *u, T *ubar, T *tau, double *plane_mea
             while ((1 << a.lP) < a.P) a.lP++;
             for (int i = 0; i < p->rx.r * p->rx.D; i++) a.WX[i] = p->rx.W32[i];
             for (int i = 0; i < p->rz.r * p->rz.D; i++) a.WZ[i] = p->rz.W32[i];
-            if (p->x_variant >= 2) {
+            if (p->x_variant == 3) {
+                int rc = ws_run(p, ns, u, h, p->d_uref, plane_mean, nf, s);
+                if (rc) return rc;
+            } else if (p->x_variant == 2) {
                 FusedTCArgs ta = p->tc;
                 a.box_rows = p->nz > 256 ? p->nz / 2 : p->nz;
                 a.use_tma = 1;
-                int rc = encode_u_map(u, p->nx, p->ny, p->nz, ns, p->x_variant == 3 ? kTcwsStageWidth : 8,
-                                      a.box_rows, &a.tmap);
+                int rc = encode_u_map(u, p->nx, p->ny, p->nz, ns, 8, a.box_rows, &a.tmap);
                 if (rc) return rc;
                 ta.f = a;     // KS, zoff, afrag and the B fragments come from the plan
-                e = p->x_variant == 3 ? launch_tcws(ta, ns, s) : launch_fused_tc(p->rz.r, p->rz.D, ta, ns, s);
+                e = launch_fused_tc(p->rz.r, p->rz.D, ta, ns, s);
             } else {
                 e = launch_fused(p->rx.r, p->rx.D, p->rz.r, p->rz.D, a, ns, s);
             }
@@ -480,7 +482,7 @@ int run_group(ef_plan *p, int ns, const T *u, T *ubar, T *tau, double *plane_mea
                            p->ext == EF_EXT_ODD_EVEN, ns, p->d_AU, p->d_AUU, wy, p->d_Kab, s);
     if (e != cudaSuccess) return cuda_fail(e, "yprofile launch");
     if constexpr (sizeof(T) == 4) {
-        if (p->ytc_ok) {   // tensor-core y passes (EF_PREC_BF16X3)
+        if (p->ytc_ok) {   // tensor-core y passes (split-precision plans)
             YTcArgs yt;
             memset(&yt, 0, sizeof yt);
             yt.geo = p->ytc;

@@ -267,7 +267,7 @@ int build_wall_rows(ef_plan *p, const double *h_les_y)
     std::vector<int> sta(p->nly);
     e = cudaMemcpy(sta.data(), p->d_ystart, sizeof(int) * p->nly, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "read y starts");
-    p->ytc_fit = p->prec == EF_PREC_BF16X3 && ytc_geometry(sta, cnt, p->ny, p->nlz * p->nlx, &p->ytc);
+    p->ytc_fit = (p->prec == EF_PREC_BF16X3 || p->prec == EF_PREC_TF32X2) && ytc_geometry(sta, cnt, p->ny, p->nlz * p->nlx, &p->ytc);
     p->ytc_ok = p->ytc_fit;
     return EF_OK;
 }

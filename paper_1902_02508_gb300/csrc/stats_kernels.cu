@@ -138,7 +138,8 @@ int ef_stats_create(const ef_grid *g, int precision, ef_stats **out)
         set_error("ef_stats_create: bad grid");
         return EF_ERR_ARG;
     }
-    if (precision != EF_PREC_FP64 && precision != EF_PREC_FP32 && precision != EF_PREC_BF16X3) {
+    if (precision != EF_PREC_FP64 && precision != EF_PREC_FP32 && precision != EF_PREC_BF16X3 &&
+        precision != EF_PREC_TF32X2) {
         set_error("ef_stats_create: unknown precision %d", precision);
         return EF_ERR_ARG;
     }

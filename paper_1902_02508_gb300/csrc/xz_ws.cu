@@ -1,0 +1,301 @@
+// Host side of the warp-specialised tensor-core x-z kernel (xz_ws.cuh): the
+// choice of output phases, the rotated x-operator B fragments of both split
+// forms, the z-operator A fragments, and the launch.  This file instantiates
+// the BF16X3 kernels; xz_ws_tf32.cu the TF32X2 ones.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "eles_internal.h"
+#include "xz_ws.cuh"
+
+namespace eles {
+
+namespace {
+
+unsigned short bf16_bits(double w)
+{
+    const float x = (float)w;
+    unsigned u;
+    memcpy(&u, &x, 4);
+    return (unsigned short)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
+}
+double bf16_value(unsigned short b)
+{
+    const unsigned u = (unsigned)b << 16;
+    float x;
+    memcpy(&x, &u, 4);
+    return x;
+}
+// TF32 (10 explicit mantissa bits) nearest to w, ties away from zero, as
+// FP32 bits with the 13 low bits clear.
+unsigned tf32_bits(double w)
+{
+    const float x = (float)w;
+    unsigned u;
+    memcpy(&u, &x, 4);
+    return (u + 0x1000u) & 0xffffe000u;
+}
+double tf32_value(unsigned b)
+{
+    float x;
+    memcpy(&x, &b, 4);
+    return x;
+}
+// IEEE binary16 nearest to w (ties to even), for |w| < 65504.
+unsigned short f16_bits(double w)
+{
+    if (w == 0.0) return 0;
+    const unsigned short sign = w < 0 ? 0x8000u : 0u;
+    const double a = fabs(w);
+    int e = 0;
+    const double m = frexp(a, &e);                 // a = m 2^e, m in [0.5, 1)
+    const int E = e - 1 + 15;                      // biased exponent of a = 2m 2^(e-1)
+    if (E <= 0) {                                  // subnormal: multiples of 2^-24
+        const double r = nearbyint(ldexp(a, 24));  // 1024 rounds up to the smallest normal
+        return (unsigned short)(sign | (unsigned)r);
+    }
+    double f = nearbyint((2.0 * m - 1.0) * 1024.0);
+    unsigned bits = (unsigned)E << 10;
+    if (f >= 1024.0) { bits = (unsigned)(E + 1) << 10; f = 0.0; }
+    return (unsigned short)(sign | bits | (unsigned)f);
+}
+double f16_value(unsigned short b)
+{
+    const int E = (b >> 10) & 31, f = b & 1023;
+    const double v = E ? ldexp(1.0 + f / 1024.0, E - 15) : ldexp((double)f, -24);
+    return (b & 0x8000u) ? -v : v;
+}
+
+// Weight of chunk input xi (0..15) to phase output n (0..6) of a stream
+// whose chunk 0 completes output xc0 first; n = 7 is the row-sum column.
+double bweight(const Ring &r, int xi, int n, int xc0, int OP, int bshift)
+{
+    if (n == 7) return 1.0;
+    const int dd = xc0 + OP * n + bshift - xi / r.r - r.dmin;
+    return (dd >= 0 && dd < r.D) ? r.W64[(xi % r.r) * r.D + dd] : 0.0;
+}
+
+}  // namespace
+
+// z-operator A fragments for the tensor-core z phase: k-step kk, lane
+// (g, t) holds A[g][2t..2t+1], A[g+8][2t..2t+1], A[g][2t+8..2t+9],
+// A[g+8][2t+8..2t+9] with A[m][k] = w[16 kk + r(k) - RZ m - zoff], split into
+// hi and lo bf16 pairs; r(2i + e) = i + 8e is the row order of the pre-split
+// parked pairs.  Returns KS (0 if the z operator does not qualify).
+int ws_zfrags(const Ring &rz, int nlz, std::vector<unsigned> &out, int *zoff_out)
+{
+    if (!rz.ok || nlz % 16 != 0) return 0;
+    const int R = rz.R, RZ = rz.r;
+    const int zoff = (R + 15) / 16 * 16;   // window starts on 16-row boundaries
+    const int KS = (zoff + 15 * RZ + R + 1 + 15) / 16;
+    auto w = [&](int o) -> double {        // weight at offset o = z - RZ Z
+        if (o < -R || o > R) return 0.0;
+        const int e = ((o % RZ) + RZ) % RZ;
+        const int dd = (e - o) / RZ - rz.dmin;
+        return (dd >= 0 && dd < rz.D) ? rz.W64[e * rz.D + dd] : 0.0;
+    };
+    out.assign((size_t)KS * 32 * 8, 0u);
+    for (int kk = 0; kk < KS; kk++)
+        for (int lane = 0; lane < 32; lane++) {
+            const int g = lane / 4, t = lane % 4;
+            const int rows[4] = {g, g + 8, g, g + 8}, kofs[4] = {0, 0, 8, 8};
+            for (int r = 0; r < 4; r++) {
+                unsigned hi = 0, lo = 0;
+                for (int e = 0; e < 2; e++) {
+                    const int k = 2 * t + kofs[r] + e;
+                    const int row = (k >> 1) + 8 * (k & 1);
+                    const double v = w(16 * kk + row - RZ * rows[r] - zoff);
+                    const unsigned short h = bf16_bits(v);
+                    const unsigned short l = bf16_bits(v - bf16_value(h));
+                    hi |= (unsigned)h << (16 * e);
+                    lo |= (unsigned)l << (16 * e);
+                }
+                out[((size_t)(2 * kk + 0) * 32 + lane) * 4 + r] = hi;
+                out[((size_t)(2 * kk + 1) * 32 + lane) * 4 + r] = lo;
+            }
+        }
+    *zoff_out = zoff;
+    return KS;
+}
+
+size_t ws_smem(int nz, int mode, int opc, int KS)
+{
+    using namespace ws;
+#define ELES_WS_SMEM(NZ)                                                                                  \
+    if (nz == NZ) {                                                                                       \
+        if (mode == MODE_BF16X3) return opc == 2 ? ws_smem_bytes<NZ, MODE_BF16X3, 2>(KS)                 \
+                                                 : ws_smem_bytes<NZ, MODE_BF16X3, 1>(KS);                 \
+        return opc == 2 ? ws_smem_bytes<NZ, MODE_TF32X2, 2>(KS) : ws_smem_bytes<NZ, MODE_TF32X2, 1>(KS);  \
+    }
+    ELES_WS_NZ_LIST(ELES_WS_SMEM)
+#undef ELES_WS_SMEM
+    return 0;
+}
+
+bool ws_nz_supported(int nz)
+{
+#define ELES_WS_HAS(NZ) if (nz == NZ) return true;
+    ELES_WS_NZ_LIST(ELES_WS_HAS)
+#undef ELES_WS_HAS
+    return false;
+}
+
+// Plan the kernel for a split-precision plan: output phases, B and z
+// fragments (uploaded to the device).  Leaves p->ws.ok false (and says why in
+// *why) when the grid or filter does not fit the kernel.
+int ws_setup(ef_plan *p, const char **why)
+{
+    WsHost &w = p->ws;
+    w = WsHost();
+    *why = nullptr;
+    const int mode = p->prec == EF_PREC_TF32X2 ? ws::MODE_TF32X2 : ws::MODE_BF16X3;
+    const Ring &rx = p->rx, &rz = p->rz;
+    if (!rx.ok || !rz.ok) { *why = "the LES x and z nodes must be every r-th DNS node"; return EF_OK; }
+    if (rx.r != 4 && rx.r != 8 && rx.r != 16) { *why = "the x stride must be 4, 8 or 16"; return EF_OK; }
+    if (!ws_nz_supported(p->nz)) { *why = "nz must be 64, 128, 192, 256 or 384"; return EF_OK; }
+    if (p->nlz % 16 != 0) { *why = "the LES nz must be a multiple of 16"; return EF_OK; }
+    const int CB = 16 / rx.r;
+    if (p->nlx % CB != 0) { *why = "the LES nx must be a multiple of 16 / (x stride)"; return EF_OK; }
+    const int bshift = (rx.dmax + CB - 1) / CB * CB;
+    // output phases: the fewest whose window (plus the idle row-sum column)
+    // fits 8 tile columns in every phase
+    int OP = 0;
+    int xc0[4] = {0, 0, 0, 0};
+    for (int op = 1; op <= 4 && !OP; op *= 2) {
+        if (CB % op != 0 || CB / op > 2) continue;
+        bool fits = true;
+        for (int ph = 0; ph < op; ph++) {
+            const int first = rx.dmin - bshift;               // outputs completed by chunk 0: [first, first + CB)
+            const int x0 = first + (((ph - first) % op) + op) % op;
+            xc0[ph] = x0;
+            const int delta = x0 + bshift - rx.dmin;          // in [0, op)
+            if (delta + 7 * op - (CB - 1) < rx.D) fits = false;
+        }
+        if (fits) OP = op;
+    }
+    if (!OP) { *why = "the x filter is too wide for the tensor-core window (ring depth)"; return EF_OK; }
+    const int OPC = CB / OP, NR = 8 / OPC;
+    std::vector<unsigned> zf;
+    int zoff = 0;
+    const int KS = ws_zfrags(rz, p->nlz, zf, &zoff);
+    if (KS <= 0 || 2 * zoff > p->nz) { *why = "the z filter is too wide for the tensor-core z phase"; return EF_OK; }
+    if (ws_smem(p->nz, mode, OPC, KS) > 227 * 1024 - 256) {   // static shared memory included
+        *why = "the kernel's shared memory exceeds 227 KB for this grid";
+        return EF_OK;
+    }
+    // rotated B fragments per phase: [OP][NR][32][BW] uint4
+    const int BW = mode == ws::MODE_TF32X2 ? 3 : 1;
+    std::vector<unsigned> bv((size_t)OP * NR * 32 * BW * 4, 0u);
+    for (int ph = 0; ph < OP; ph++)
+        for (int q = 0; q < NR; q++)
+            for (int lane = 0; lane < 32; lane++) {
+                const int g = lane / 4, t = lane % 4;
+                const int n = (g - OPC * q) & 7;             // phase output held by tile column g
+                unsigned *o = &bv[((((size_t)ph * NR + q) * 32 + lane) * BW) * 4];
+                if (mode == ws::MODE_BF16X3) {
+                    // k slot 2t + 8 kq + e <-> chunk input 4t + 2 kq + e
+                    for (int kq = 0; kq < 2; kq++) {
+                        unsigned hi = 0, lo = 0;
+                        for (int e = 0; e < 2; e++) {
+                            const double v = bweight(rx, 4 * t + 2 * kq + e, n, xc0[ph], OP, bshift);
+                            const unsigned short h = bf16_bits(v);
+                            const unsigned short l = bf16_bits(v - bf16_value(h));
+                            hi |= (unsigned)h << (16 * e);
+                            lo |= (unsigned)l << (16 * e);
+                        }
+                        o[kq] = hi;
+                        o[2 + kq] = lo;
+                    }
+                } else {
+                    // velocities, TF32 MMA k2: slot t <-> input 4t + 2 k2, slot t + 4 <-> 4t + 2 k2 + 1
+                    for (int k2 = 0; k2 < 2; k2++)
+                        for (int e = 0; e < 2; e++) {
+                            const double v = bweight(rx, 4 * t + 2 * k2 + e, n, xc0[ph], OP, bshift);
+                            const unsigned h = tf32_bits(v);
+                            o[4 * k2 + e] = h;
+                            o[4 * k2 + 2 + e] = tf32_bits(v - tf32_value(h));
+                        }
+                    // products, FP16 MMA: k slots as the BF16X3 words
+                    for (int kq = 0; kq < 2; kq++) {
+                        unsigned hi = 0, lo = 0;
+                        for (int e = 0; e < 2; e++) {
+                            const double v = bweight(rx, 4 * t + 2 * kq + e, n, xc0[ph], OP, bshift);
+                            const unsigned short h = f16_bits(v);
+                            const unsigned short l = f16_bits(v - f16_value(h));
+                            hi |= (unsigned)h << (16 * e);
+                            lo |= (unsigned)l << (16 * e);
+                        }
+                        o[8 + kq] = hi;
+                        o[8 + 2 + kq] = lo;
+                    }
+                }
+            }
+    cudaError_t e;
+    if ((e = cudaMalloc(&w.d_afrag, sizeof(unsigned) * zf.size())) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc z fragments");
+    if ((e = cudaMemcpy(w.d_afrag, zf.data(), sizeof(unsigned) * zf.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "copy z fragments");
+    if ((e = cudaMalloc(&w.d_bvar, sizeof(unsigned) * bv.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc x fragments");
+    if ((e = cudaMemcpy(w.d_bvar, bv.data(), sizeof(unsigned) * bv.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "copy x fragments");
+    w.mode = mode;
+    w.OP = OP;
+    w.OPC = OPC;
+    w.CB = CB;
+    w.bshift = bshift;
+    w.nchunk = (p->nlx - rx.dmin + bshift + CB - 1) / CB;
+    for (int ph = 0; ph < 4; ph++) w.xc0[ph] = xc0[ph];
+    w.KS = KS;
+    w.zoff = zoff;
+    w.ok = true;
+    return EF_OK;
+}
+
+void ws_free(WsHost &w)
+{
+    cudaFree(w.d_afrag);
+    cudaFree(w.d_bvar);
+    w.d_afrag = nullptr;
+    w.d_bvar = nullptr;
+    w.ok = false;
+}
+
+cudaError_t ws_launch_bf16(const ws::WsArgs &a, int nz, int opc, int nsnap, cudaStream_t st);
+cudaError_t ws_launch_tf32(const ws::WsArgs &a, int nz, int opc, int nsnap, cudaStream_t st);
+
+int ws_run(const ef_plan *p, int nsnap, const float *u, float *h, double *uref, double *plane_mean, int nf,
+           cudaStream_t st)
+{
+    const WsHost &w = p->ws;
+    ws::WsArgs a;
+    memset(&a, 0, sizeof a);
+    a.box_rows = p->nz > 256 ? p->nz / 2 : p->nz;
+    int rc = encode_u_map(u, p->nx, p->ny, p->nz, nsnap, ws::CW, a.box_rows, &a.tmap);
+    if (rc) return rc;
+    a.u = u; a.h = h; a.uref = uref; a.plane_mean = plane_mean; a.err = p->d_err;
+    a.nx = p->nx; a.ny = p->ny; a.nz = p->nz; a.nlx = p->nlx; a.nlz = p->nlz;
+    a.nchunk = w.nchunk; a.bshift = w.bshift; a.rx = p->rx.r; a.CB = w.CB; a.OP = w.OP;
+    for (int ph = 0; ph < 4; ph++) a.xc0[ph] = w.xc0[ph];
+    a.RZ = p->rz.r; a.KS = w.KS; a.zoff = w.zoff; a.nf = nf;
+    a.afrag = reinterpret_cast<const uint4 *>(w.d_afrag);
+    a.bvar = reinterpret_cast<const uint4 *>(w.d_bvar);
+    const cudaError_t e = w.mode == ws::MODE_TF32X2 ? ws_launch_tf32(a, p->nz, w.OPC, nsnap, st)
+                                                     : ws_launch_bf16(a, p->nz, w.OPC, nsnap, st);
+    if (e != cudaSuccess) return cuda_fail(e, "xz_ws launch");
+    return EF_OK;
+}
+
+cudaError_t ws_launch_bf16(const ws::WsArgs &a, int nz, int opc, int nsnap, cudaStream_t st)
+{
+    using namespace ws;
+#define ELES_WS_GO(NZ)                                                                                   \
+    if (nz == NZ) return opc == 2 ? ws_launch<NZ, MODE_BF16X3, 2>(a, nsnap, st)                          \
+                                  : ws_launch<NZ, MODE_BF16X3, 1>(a, nsnap, st);
+    ELES_WS_NZ_LIST(ELES_WS_GO)
+#undef ELES_WS_GO
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace eles

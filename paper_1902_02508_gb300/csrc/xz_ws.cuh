@@ -1,0 +1,574 @@
+// Warp-specialised x-z kernel on the tensor cores (x_variant 3), for the
+// split-precision plans: EF_PREC_BF16X3 and EF_PREC_TF32X2.
+//
+// One CTA per (snapshot, y-plane, output phase) with three roles that meet
+// only at mbarriers (every wait bounded):
+//   * NZ / 32 x warps (32 z-rows each) contract x with mma.sync on the tensor
+//     cores, FP32 accumulation;
+//   * one producer warp streams the plane through TMA stages of one chunk
+//     (16 x-inputs of every row, three components) with a full and an empty
+//     barrier per stage;
+//   * kZW z warps contract z (split BF16, tensor cores) for the outputs each
+//     chunk completes, from a double-buffered column buffer.  (An FP32 z
+//     phase on the CUDA cores was measured 2.4 times slower: the z warps are
+//     few, and a 63-tap FP32 dot product per output outweighs the banded MMAs.)
+//
+// The x contraction is a strided convolution: output X (at DNS column rx X)
+// takes inputs x with |x - rx X| <= R.  A chunk feeds the outputs in flight,
+// held as the 8 columns of the MMA accumulator tile (rows = z-rows).  When the
+// band is wide (ring depth D above what 7 columns hold), the outputs are split
+// into OP phases X = OP m + p, one CTA per phase, each re-reading the plane
+// (from L2: the phases of a plane run side by side).  Every chunk completes
+// OPC = 16 / (rx OP) outputs of a phase (1 or 2).  Phase output m lives in
+// tile column (m - m0) mod 8 for the whole stream, so the chunk's B operand
+// rotates (NR = 8 / OPC rotations, built on the host) and the outputs a
+// chunk completes always sit in columns OPC q .. OPC q + OPC - 1 (q = chunk
+// mod NR).  The column after the window (OPC q + 7) is idle: its B column is
+// all ones and collects the chunk's row sums of the fluctuation (plane means).
+//
+// Fields: u'_c = u_c - U_c(y) (U_c the mean of the plane's z-row 0) and the
+// six products u'_a u'_b, formed in registers.
+//   BF16X3: every field x = hi + lo (bf16 pair), weights likewise; the
+//           products Ahi Bhi + Alo Bhi + Ahi Blo (m16n8k16).
+//   TF32X2: the three velocities split as hi = x with its 13 low bits
+//           cleared (TF32), lo = x - hi (exact; no conversion instruction),
+//           against TF32 hi + lo weights: Ahi Bhi + Alo Bhi + Ahi Blo
+//           (m16n8k8).  The six product fields are rounded once to an 11-bit
+//           significand (the TF32 precision) and contracted against hi + lo
+//           weights of the same precision: A Bhi + A Blo.  They travel in the
+//           FP16 format (m16n8k16), whose significand is TF32's: one
+//           conversion per pair of values (a TF32 rounding costs several
+//           instructions per value), exact range for |u'_a u'_b| < 65504,
+//           and values below 2^-14 kept to 2^-25 absolute as subnormals.
+#pragma once
+
+#include "eles_internal.h"
+#include "fused_stage.cuh"
+
+namespace eles {
+namespace ws {
+
+using namespace fz;
+
+constexpr int kZW = 3;               // z warps
+constexpr int CW = 16;               // floats per row per TMA stage: one chunk
+constexpr int CSTG = 2;              // stages in flight
+constexpr int NCB = 2 * NF + 3;      // parked columns per buffer: two outputs x NF fields, 3 row sums
+enum { MODE_BF16X3 = 0, MODE_TF32X2 = 1 };
+
+// B words per lane and rotation: one uint4 (BF16X3), or three (TF32X2: two
+// TF32 k-halves for the velocities, one FP16 word set for the products).
+template <int MODE>
+struct Bw { static constexpr int n = MODE == MODE_TF32X2 ? 3 : 1; };
+
+struct WsArgs {
+    CUtensorMap tmap;     // TMA view of u: {nx, nz, 3 ny S} floats, box {16, box_rows, 1}
+    const float *u;       // [S][3][ny][nz][nx]
+    float *h;             // [S][9][ny][nlz][nlx]
+    double *uref;         // [S][3][ny]
+    double *plane_mean;   // [S][3][ny] or nullptr
+    int *err;             // device error word
+    int nx, ny, nz, nlx, nlz;
+    int box_rows;
+    int nchunk;           // chunks per row stream
+    int bshift;           // chunk k starts at x block CB k - bshift (mod nlx)
+    int rx, CB;           // DNS columns per LES column, x blocks per chunk (16 / rx)
+    int OP;               // output phases (CTAs per plane)
+    int xc0[4];           // per phase: first output completed by chunk 0 (may be < 0)
+    int RZ, KS, zoff;     // z phase: stride, k-steps per Z tile, window offset
+    int nf;               // fields contracted in z (9, or 3 for the velocities only)
+    const uint4 *afrag;   // z A fragments [KS][hi, lo][32 lanes] (pair order)
+    const uint4 *bvar;    // x B fragments [OP][NR][32 lanes][Bw]
+};
+
+__device__ __forceinline__ unsigned pack_f16(float lo_k, float hi_k)
+{
+    unsigned d;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi_k), "f"(lo_k));
+    return d;
+}
+
+__device__ __forceinline__ void mma_f16(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                        unsigned b0, unsigned b1)
+{
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ unsigned pack_bf16(float lo_k, float hi_k)
+{
+    unsigned d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi_k), "f"(lo_k));
+    return d;
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1)
+{
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1)
+{
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// x = hi + lo for a pair (k, k+1), bf16 words, with a packed FP32 subtraction.
+__device__ __forceinline__ void split2(float2 x, unsigned &hi, unsigned &lo)
+{
+    hi = pack_bf16(x.x, x.y);
+    const float2 h = make_float2(__uint_as_float(hi << 16), __uint_as_float(hi & 0xffff0000u));
+    const float2 l = __ffma2_rn(h, make_float2(-1.f, -1.f), x);
+    lo = pack_bf16(l.x, l.y);
+}
+
+__device__ __forceinline__ unsigned pack_f16_2(float2 x) { return pack_f16(x.x, x.y); }
+
+template <int F>
+__device__ __forceinline__ float2 field2(float2 v0, float2 v1, float2 v2)
+{
+    if constexpr (F == 0) return v0;
+    else if constexpr (F == 1) return v1;
+    else if constexpr (F == 2) return v2;
+    else if constexpr (F == 3) return __fmul2_rn(v0, v0);
+    else if constexpr (F == 4) return __fmul2_rn(v0, v1);
+    else if constexpr (F == 5) return __fmul2_rn(v0, v2);
+    else if constexpr (F == 6) return __fmul2_rn(v1, v1);
+    else if constexpr (F == 7) return __fmul2_rn(v1, v2);
+    else return __fmul2_rn(v2, v2);
+}
+
+// order 0 3 4 5 | 1 6 7 | 2 8: each component's registers die as early as possible
+template <int F>
+__host__ __device__ constexpr int next_field()
+{
+    return F == 0 ? 3 : F == 3 ? 4 : F == 4 ? 5 : F == 5 ? 1 : F == 1 ? 6 : F == 6 ? 7 : F == 7 ? 2 : F == 2 ? 8 : -1;
+}
+
+// One 16-row tile, all fields, one chunk.  v[c][h][k2] holds component c at
+// row g + 8h and chunk inputs 4t + 2k2 (.x) and 4t + 2k2 + 1 (.y).
+//   BF16X3 k slots: 2t + 8 k2 + e <-> input 4t + 2 k2 + e.
+//   TF32X2, MMA k2: slot t <-> input 4t + 2 k2, slot t + 4 <-> 4t + 2 k2 + 1.
+template <int MODE, int F>
+__device__ __forceinline__ void x_mma(float (&acc)[NF][4], const float2 (&v)[3][2][2], const uint4 (&B)[Bw<MODE>::n])
+{
+    if constexpr (MODE == MODE_BF16X3) {
+        unsigned ah[4], al[4];
+        split2(field2<F>(v[0][0][0], v[1][0][0], v[2][0][0]), ah[0], al[0]);   // row g,     k 2t, 2t+1
+        split2(field2<F>(v[0][1][0], v[1][1][0], v[2][1][0]), ah[1], al[1]);   // row g + 8, k 2t, 2t+1
+        split2(field2<F>(v[0][0][1], v[1][0][1], v[2][0][1]), ah[2], al[2]);   // row g,     k 2t+8, 2t+9
+        split2(field2<F>(v[0][1][1], v[1][1][1], v[2][1][1]), ah[3], al[3]);   // row g + 8, k 2t+8, 2t+9
+        mma_bf16(acc[F], ah[0], ah[1], ah[2], ah[3], B[0].x, B[0].y);
+        mma_bf16(acc[F], al[0], al[1], al[2], al[3], B[0].x, B[0].y);
+        mma_bf16(acc[F], ah[0], ah[1], ah[2], ah[3], B[0].z, B[0].w);
+    } else if constexpr (F < 3) {
+#pragma unroll
+        for (int k2 = 0; k2 < 2; k2++) {
+            const float2 x0 = v[F][0][k2], x1 = v[F][1][k2];     // rows g, g + 8
+            const uint4 b = B[k2];           // b0 hi, b1 hi, b0 lo, b1 lo
+            const unsigned h00 = __float_as_uint(x0.x) & 0xffffe000u, h01 = __float_as_uint(x0.y) & 0xffffe000u;
+            const unsigned h10 = __float_as_uint(x1.x) & 0xffffe000u, h11 = __float_as_uint(x1.y) & 0xffffe000u;
+            const float2 m1 = make_float2(-1.f, -1.f);
+            const float2 l0 = __ffma2_rn(make_float2(__uint_as_float(h00), __uint_as_float(h01)), m1, x0);
+            const float2 l1 = __ffma2_rn(make_float2(__uint_as_float(h10), __uint_as_float(h11)), m1, x1);
+            mma_tf32(acc[F], h00, h10, h01, h11, b.x, b.y);
+            mma_tf32(acc[F], __float_as_uint(l0.x), __float_as_uint(l1.x), __float_as_uint(l0.y),
+                     __float_as_uint(l1.y), b.x, b.y);
+            mma_tf32(acc[F], h00, h10, h01, h11, b.z, b.w);
+        }
+    } else {
+        // products: one rounding to an 11-bit significand (FP16 carrier); k slots as BF16X3
+        const unsigned a0 = pack_f16_2(field2<F>(v[0][0][0], v[1][0][0], v[2][0][0]));   // row g,     k 2t, 2t+1
+        const unsigned a1 = pack_f16_2(field2<F>(v[0][1][0], v[1][1][0], v[2][1][0]));   // row g + 8, k 2t, 2t+1
+        const unsigned a2 = pack_f16_2(field2<F>(v[0][0][1], v[1][0][1], v[2][0][1]));   // row g,     k 2t+8, 2t+9
+        const unsigned a3 = pack_f16_2(field2<F>(v[0][1][1], v[1][1][1], v[2][1][1]));   // row g + 8, k 2t+8, 2t+9
+        mma_f16(acc[F], a0, a1, a2, a3, B[2].x, B[2].y);
+        mma_f16(acc[F], a0, a1, a2, a3, B[2].z, B[2].w);
+    }
+    constexpr int nx = next_field<F>();
+    if constexpr (nx >= 0) x_mma<MODE, nx>(acc, v, B);
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait shared by the roles.  Once any wait of the CTA has run out
+// the others return at once and the roles stop: the producer issues no new
+// stage and the consumers stop touching the stage and column buffers (a bulk
+// copy issued before may still be landing; the producer waits for those
+// with its own bound before the CTA exits).  The error word tells the host.
+__device__ __forceinline__ bool wait_or_abort(unsigned long long *bar, unsigned parity, volatile int *abort_flag,
+                                              int *err)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (clock64() - t0 < kWaitCycles) {
+        if (*abort_flag) return false;
+        if (mbar_try_wait(bar, parity)) return true;
+    }
+    *abort_flag = 1;
+    if (err) atomicCAS(err, 0, (int)EF_ERR_TIMEOUT);
+    return false;
+}
+
+// z work: Z tile zt (16 outputs) x column tiles nt0 .. nt0 + NT - 1 (8 of
+// the OPC NF parked columns each, column c = j NF + f for output X0 + OP j),
+// KS k-steps over the tile's z window.  The parked columns hold, per 16-row
+// block and pair i < 8, the split (hi, lo) bf16 words of rows (i, i + 8);
+// the k index of a k-step runs over the block's rows in the order
+// k = 2i + e -> row i + 8e, which the A fragments follow.  One A fragment
+// load per k-step feeds all NT column tiles.  The window starts on a 16-row
+// boundary (zoff is a multiple of 16), so a k-step wraps periodically as a
+// whole or not at all.  Lanes whose column is idle use zeros.
+template <int OPC, int NT, int LD>
+__device__ __forceinline__ void z_tile(const WsArgs &a, const float *colb, const uint4 *afrag,
+                                       int s, int j, int X0, bool val0, bool val1, int zt, int nt0, int lane)
+{
+    const int g = lane >> 2, t = lane & 3;
+    const uint2 *cp[NT];
+    unsigned keep[NT];                            // all ones for a live column, zero for an idle one
+#pragma unroll
+    for (int i = 0; i < NT; i++) {
+        const int c = (nt0 + i) * 8 + g;          // this lane's B column
+        const bool bval = c < OPC * NF && (c < NF ? val0 : val1);
+        cp[i] = reinterpret_cast<const uint2 *>(colb + (size_t)(bval ? c : 0) * LD) + t;
+        keep[i] = bval ? 0xffffffffu : 0u;
+    }
+    float acc[NT][3][4];   // one accumulator per split product: independent chains
+#pragma unroll
+    for (int i = 0; i < NT; i++)
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int e = 0; e < 4; e++) acc[i][r][e] = 0.f;
+    int z0 = 16 * a.RZ * zt - a.zoff;
+#pragma unroll 2
+    for (int kk = 0; kk < a.KS; kk++, z0 += 16) {
+        const int zr = (z0 < 0 ? z0 + a.nz : (z0 >= a.nz ? z0 - a.nz : z0)) >> 1;   // in 8-byte words
+        const uint4 ah = afrag[(2 * kk) * 32 + lane], al = afrag[(2 * kk + 1) * 32 + lane];
+#pragma unroll
+        for (int i = 0; i < NT; i++) {
+            uint2 w0 = cp[i][zr], w1 = cp[i][zr + 4];           // pairs t and t + 4: (hi, lo)
+            w0.x &= keep[i]; w0.y &= keep[i]; w1.x &= keep[i]; w1.y &= keep[i];
+            mma_bf16(acc[i][0], ah.x, ah.y, ah.z, ah.w, w0.x, w1.x);
+            mma_bf16(acc[i][1], al.x, al.y, al.z, al.w, w0.x, w1.x);
+            mma_bf16(acc[i][2], ah.x, ah.y, ah.z, ah.w, w0.y, w1.y);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NT; i++)
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            const int cc = (nt0 + i) * 8 + 2 * t + e;
+            if (cc >= OPC * NF) continue;
+            const int n = cc >= NF ? 1 : 0, f = cc - n * NF;
+            if (f >= a.nf || !(n ? val1 : val0)) continue;
+            float *hout = a.h + ((((size_t)s * NF + f) * a.ny + j) * a.nlz + 16 * zt) * a.nlx + X0 + a.OP * n;
+            hout[(size_t)g * a.nlx] = (acc[i][0][e] + acc[i][1][e]) + acc[i][2][e];
+            hout[(size_t)(g + 8) * a.nlx] = (acc[i][0][2 + e] + acc[i][1][2 + e]) + acc[i][2][2 + e];
+        }
+}
+
+__device__ __forceinline__ void named_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Column stride of the parked columns (floats): +8 makes the 8-byte B loads
+// of the z warps conflict-free.
+template <int NZ>
+struct Geo {
+    static constexpr int LD = NZ + 8;
+    static constexpr int NXW = NZ / 32;                    // x warps
+    static constexpr int THREADS = NZ + 32 * (1 + kZW);
+    static constexpr int STGF = 3 * NZ * CW;               // floats per stage
+};
+
+template <int NZ, int MODE, int OPC>
+__global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_constant__ WsArgs a)
+{
+    using G = Geo<NZ>;
+    constexpr int LD = G::LD, NXW = G::NXW, STGF = G::STGF;
+    constexpr int NR = 8 / OPC;                  // B rotations
+    constexpr int BW = Bw<MODE>::n;
+    constexpr int NCOL = OPC * NF;               // output columns parked per chunk
+    constexpr int NCBO = NCOL + 3;               // with the three row sums
+    extern __shared__ float4 smem_dyn[];
+    const int KS = a.KS;
+    uint4 *afrag = reinterpret_cast<uint4 *>(smem_dyn);        // [KS][hi, lo][32 lanes]
+    uint4 *bvar = afrag + KS * 64;                              // [NR][32 lanes][BW]
+    float *colbuf = reinterpret_cast<float *>(bvar + NR * 32 * BW);   // [2 buffers][NCBO][LD]
+    float *stg;                                                 // [CSTG][3][NZ][CW], 128-B aligned
+    {
+        char *end = reinterpret_cast<char *>(colbuf + (size_t)2 * NCBO * LD);
+        const unsigned sa = smem_u32(end);
+        stg = reinterpret_cast<float *>(end + (((sa + 127u) & ~127u) - sa));
+    }
+    __shared__ alignas(8) unsigned long long full[CSTG], empty[CSTG], cfull[2], cempty[2];
+    __shared__ float Us[3];
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int p = blockIdx.x % a.OP, j = blockIdx.x / a.OP, s = blockIdx.y;
+    const size_t np = (size_t)a.nx * a.ny * NZ;
+    const int nchunk = a.nchunk;
+    const bool pm = a.plane_mean != nullptr && p == 0;
+    volatile int *abort_v = &abort_flag;
+
+    if (tid == 0) {
+        for (int i = 0; i < CSTG; i++) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 32 * NXW);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&cfull[b], 32 * NXW);
+            mbar_init(&cempty[b], 32 * kZW);
+        }
+        abort_flag = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    if (warp == NXW) {   // producer: stage k = chunk k = x blocks CB k - bshift .. + CB - 1
+        if (lane == 0) {
+            const int pc0 = s * 3 * a.ny + j;  // TMA plane coordinate of component 0
+            int issued = 0;
+            for (int k = 0; k < nchunk; k++) {
+                const int st = k % CSTG;
+                if (k >= CSTG && !wait_or_abort(&empty[st], ((k / CSTG) - 1) & 1, abort_v, a.err)) break;
+                if (*abort_v) break;
+                int b = (a.CB * k - a.bshift) % a.nlx;   // a multiple of CB: the chunk never wraps
+                if (b < 0) b += a.nlx;
+                proxy_fence();
+                float *buf = stg + st * STGF;
+                mbar_expect_tx(&full[st], 3u * NZ * CW * 4u);
+                for (int c = 0; c < 3; c++)
+                    for (int r0 = 0; r0 < NZ; r0 += a.box_rows)
+                        tma_load3(buf + ((size_t)c * NZ + r0) * CW, &a.tmap, &full[st], b * a.rx, r0, pc0 + c * a.ny);
+                issued = k + 1;
+            }
+            // no copy may be in flight when the CTA exits
+            for (int k = issued > CSTG ? issued - CSTG : 0; k < issued; k++)
+                mbar_wait(&full[k % CSTG], (k / CSTG) & 1, a.err);
+        }
+        return;
+    }
+
+    // x and z warps: z fragments, this phase's rotated x fragments, reference profile
+    constexpr int nwork = G::THREADS - 32;
+    const int wtid = tid < 32 * NXW ? tid : tid - 32;
+    for (int i = wtid; i < KS * 64; i += nwork) afrag[i] = a.afrag[i];
+    for (int i = wtid; i < NR * 32 * BW; i += nwork) bvar[i] = a.bvar[(size_t)p * NR * 32 * BW + i];
+    const float *plane = a.u + (size_t)s * 3 * np + (size_t)j * NZ * a.nx;
+    const int wk = warp < NXW ? warp : warp - 1;  // index among the x and z warps
+    if (wk < 3) {
+        const float *r0 = plane + (size_t)wk * np;
+        double acc = 0.0;
+        for (int i = lane; i < a.nx; i += 32) acc += (double)r0[i];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            const float Uc = (float)(acc / a.nx);
+            Us[wk] = Uc;
+            if (p == 0) a.uref[((size_t)s * 3 + wk) * a.ny + j] = (double)Uc;
+        }
+    }
+    named_sync(1, nwork);
+
+    const int xc0 = a.xc0[p];
+    if (warp < NXW) {   // ---------------- x warps
+        volatile float *Uv = Us;    // re-read per tile: keeps three register pairs free
+        float acc[2][NF][4];
+#pragma unroll
+        for (int m = 0; m < 2; m++)
+#pragma unroll
+            for (int f = 0; f < NF; f++)
+#pragma unroll
+                for (int i = 0; i < 4; i++) acc[m][f][i] = 0.f;
+        const float *xrow = stg + (size_t)(warp * 32 + g) * CW + 4 * t;   // this lane's row g, inputs 4t..
+        float *colw0 = colbuf + warp * 32 + 2 * g;
+        for (int sidx = 0; sidx < nchunk; sidx++) {
+            const int st = sidx % CSTG;
+            if (!wait_or_abort(&full[st], (sidx / CSTG) & 1, abort_v, a.err)) break;
+            const int q = sidx % NR;
+            uint4 B[BW];
+#pragma unroll
+            for (int w = 0; w < BW; w++) B[w] = bvar[(q * 32 + lane) * BW + w];
+            const float *buf = xrow + st * STGF;
+#pragma unroll
+            for (int m = 0; m < 2; m++) {
+                float2 v[3][2][2];
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const float nu = -Uv[c];
+                    const float2 nU = make_float2(nu, nu);
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const float4 x = *reinterpret_cast<const float4 *>(buf + (c * NZ + 16 * m + 8 * h) * CW);
+                        v[c][h][0] = __fadd2_rn(make_float2(x.x, x.y), nU);
+                        v[c][h][1] = __fadd2_rn(make_float2(x.z, x.w), nU);
+                    }
+                }
+                x_mma<MODE, 0>(acc[m], v, B);
+            }
+            mbar_arrive(&empty[st]);
+            // the chunk completes phase outputs X0 + OP i, i < OPC (tile columns OPC q + i)
+            const int cb = sidx & 1;
+            if (sidx >= 2 && !wait_or_abort(&cempty[cb], ((sidx >> 1) - 1) & 1, abort_v, a.err)) break;
+            const int X0 = xc0 + a.OP * OPC * sidx;
+            const int b0 = a.CB * sidx - a.bshift;     // first x block of the chunk
+            float *colw = colw0 + (size_t)cb * NCBO * LD;
+            const int csum = (OPC * q + 7) & 7;        // the idle column: row sums
+            // rows (g, g + 8) of each 16-row block as one pair
+            auto park = [&](float *dst, float r0, float r8) { *reinterpret_cast<float2 *>(dst) = make_float2(r0, r8); };
+            if constexpr (OPC == 2) {
+                // columns 2q, 2q + 1 (lanes t == q, elements 0 and 1)
+                if (t == q) {
+#pragma unroll
+                    for (int n = 0; n < 2; n++)
+                        if (X0 + a.OP * n >= 0 && X0 + a.OP * n < a.nlx) {
+#pragma unroll
+                            for (int m = 0; m < 2; m++)
+#pragma unroll
+                                for (int f = 0; f < NF; f++)
+                                    park(colw + (n * NF + f) * LD + 16 * m, acc[m][f][n], acc[m][f][2 + n]);
+                        }
+                }
+            } else {
+                // column q (lanes t == q / 2, element q % 2)
+                if (t == (q >> 1) && X0 >= 0 && X0 < a.nlx) {
+                    if (q & 1) {
+#pragma unroll
+                        for (int m = 0; m < 2; m++)
+#pragma unroll
+                            for (int f = 0; f < NF; f++) park(colw + f * LD + 16 * m, acc[m][f][1], acc[m][f][3]);
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < 2; m++)
+#pragma unroll
+                            for (int f = 0; f < NF; f++) park(colw + f * LD + 16 * m, acc[m][f][0], acc[m][f][2]);
+                    }
+                }
+            }
+            // row sums of fields 0-2 (the idle column) go to parked columns NCOL + c
+            // when the chunk's blocks are owned (each input counted once)
+            if (pm && t == (csum >> 1) && b0 >= 0 && b0 < a.nlx) {
+                const int es = csum & 1;
+#pragma unroll
+                for (int m = 0; m < 2; m++)
+#pragma unroll
+                    for (int c = 0; c < 3; c++)
+                        *reinterpret_cast<float2 *>(colw + (NCOL + c) * LD + 16 * m) =
+                            es ? make_float2(acc[m][c][1], acc[m][c][3]) : make_float2(acc[m][c][0], acc[m][c][2]);
+            }
+            // clear the completed columns and the sum column without a branch; a
+            // non-finite value stays in its column, and the y pass flags it
+            {
+                const unsigned clr = (((OPC == 2 ? 3u : 1u) << (OPC * q)) | (1u << csum)) >> (2 * t);
+                const float2 keep = make_float2(clr & 1u ? 0.f : 1.f, clr & 2u ? 0.f : 1.f);
+#pragma unroll
+                for (int m = 0; m < 2; m++)
+#pragma unroll
+                    for (int f = 0; f < NF; f++) {
+                        const float2 lo = __fmul2_rn(make_float2(acc[m][f][0], acc[m][f][1]), keep);
+                        const float2 hi = __fmul2_rn(make_float2(acc[m][f][2], acc[m][f][3]), keep);
+                        acc[m][f][0] = lo.x; acc[m][f][1] = lo.y; acc[m][f][2] = hi.x; acc[m][f][3] = hi.y;
+                    }
+            }
+            // split the warp's parked pairs into (hi, lo) bf16 words in place, all
+            // lanes sharing the work: NCOL columns x 2 blocks x 8 pairs
+            {
+                __syncwarp();
+                float *cw = colbuf + (size_t)cb * NCBO * LD + warp * 32;
+#pragma unroll
+                for (int r = 0; r < (NCOL * 16 + 31) / 32; r++) {
+                    const int pidx = lane + 32 * r, col = pidx >> 4, off = pidx & 15;
+                    if (NCOL * 16 % 32 == 0 || pidx < NCOL * 16) {
+                        float2 *pp = reinterpret_cast<float2 *>(cw + (size_t)col * LD) + off;
+                        unsigned hi, lo;
+                        split2(*pp, hi, lo);
+                        *reinterpret_cast<uint2 *>(pp) = make_uint2(hi, lo);
+                    }
+                }
+            }
+            mbar_arrive(&cfull[cb]);
+        }
+        return;
+    }
+
+    // ---------------- z warps: with as many Z tiles as z warps, z warp zw takes
+    // tile zw and every column tile; otherwise the (Z tile, column tile) pairs
+    // round robin.  z warp c < 3 also sums the parked row sums of component c.
+    constexpr int NCT = (NCOL + 7) / 8;          // column tiles
+    const int zw = warp - NXW - 1;
+    const int nzt = a.nlz / 16;
+    double pmean = 0.0;
+    for (int sidx = 0; sidx < nchunk; sidx++) {
+        const int cb = sidx & 1;
+        if (!wait_or_abort(&cfull[cb], (sidx >> 1) & 1, abort_v, a.err)) break;
+        const int X0 = xc0 + a.OP * OPC * sidx;
+        const bool val0 = X0 >= 0 && X0 < a.nlx;
+        const bool val1 = OPC == 2 && X0 + a.OP >= 0 && X0 + a.OP < a.nlx;
+        const float *colb = colbuf + (size_t)cb * NCBO * LD;
+        if (pm && zw < 3) {
+            const int b0 = a.CB * sidx - a.bshift;
+            if (b0 >= 0 && b0 < a.nlx) {
+                float ssum = 0.f;
+                for (int z = lane; z < NZ; z += 32) ssum += colb[(NCOL + zw) * LD + z];
+                pmean += (double)ssum;
+            }
+        }
+        if (val0 || val1) {
+            if (nzt == kZW) {
+                z_tile<OPC, NCT, LD>(a, colb, afrag, s, j, X0, val0, val1, zw, 0, lane);
+            } else {
+                for (int it = zw; it < NCT * nzt; it += kZW)
+                    z_tile<OPC, 1, LD>(a, colb, afrag, s, j, X0, val0, val1, it / NCT, it % NCT, lane);
+            }
+        }
+        mbar_arrive(&cempty[cb]);
+    }
+    if (pm && zw < 3 && !*abort_v) {
+        for (int o = 16; o > 0; o >>= 1) pmean += __shfl_xor_sync(0xffffffffu, pmean, o);
+        if (lane == 0)
+            a.plane_mean[((size_t)s * 3 + zw) * a.ny + j] = (double)Us[zw] + pmean / ((double)a.nx * NZ);
+    }
+}
+
+// Dynamic shared memory: z fragments, x B fragments, the parked columns,
+// 128-byte alignment, the TMA stages.
+template <int NZ, int MODE, int OPC>
+size_t ws_smem_bytes(int KS)
+{
+    using G = Geo<NZ>;
+    constexpr int NCBO = OPC * NF + 3;
+    return sizeof(uint4) * (64 * (size_t)KS + (8 / OPC) * 32 * Bw<MODE>::n) + 128 +
+           sizeof(float) * ((size_t)2 * NCBO * G::LD + (size_t)CSTG * G::STGF);
+}
+
+template <int NZ, int MODE, int OPC>
+cudaError_t ws_launch(const WsArgs &a, int nsnap, cudaStream_t st)
+{
+    const size_t smem = ws_smem_bytes<NZ, MODE, OPC>(a.KS);
+    static size_t attr = 0;
+    if (smem > attr) {
+        cudaError_t e = cudaFuncSetAttribute(xz_ws<NZ, MODE, OPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    xz_ws<NZ, MODE, OPC><<<dim3(a.ny * a.OP, nsnap), Geo<NZ>::THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace ws
+}  // namespace eles

@@ -60,7 +60,6 @@ def test_setup_rejects_bad_arguments_on_host(lib):
     assert _setup_rc(lib, d, l, delta=2.0)[0] == 1            # support wider than half the box
     assert _setup_rc(lib, d, l, kernel=5)[0] == 7
     assert _setup_rc(lib, d, l, ext=9)[0] == 1
-    assert _setup_rc(lib, d, l, prec=2)[0] == 7               # TF32x2 reserved
     assert _setup_rc(lib, d, l, prec=9)[0] == 7
     bad = I.Grid(32, 33, 32, 2 * math.pi, math.pi, d.y[::-1].copy())
     rc, msg = _setup_rc(lib, bad, l)

@@ -25,7 +25,7 @@ def built():
 
 
 # (nx, ny, nz, nlx, nly, nlz, delta fraction of Lx) in the 4 pi x 2 x 2 pi box
-ITEMS = [(64, 49, 64, 16, 13, 16, 1 / 16), (96, 49, 96, 24, 13, 24, 1 / 32), (128, 65, 128, 32, 17, 32, 1 / 48)]
+ITEMS = [(64, 49, 64, 16, 13, 16, 1 / 16), (192, 49, 128, 48, 13, 32, 1 / 32), (128, 65, 128, 32, 17, 32, 1 / 48)]
 
 
 def make(item, prec):
@@ -35,7 +35,7 @@ def make(item, prec):
     return dns, les, f * dns.Lx, eles.filter_setup(dns, les, f * dns.Lx, precision=prec)
 
 
-@pytest.mark.parametrize("prec", [eles.PREC_FP32, eles.PREC_BF16X3])
+@pytest.mark.parametrize("prec", [eles.PREC_FP32, eles.PREC_BF16X3, eles.PREC_TF32X2])
 def test_batch_graph_equals_single_calls(prec):
     dev = torch.device("cuda")
     nsnap = [2, 1, 3]
@@ -111,7 +111,7 @@ def test_batch_recaptures_after_scratch_or_variant_change():
         t.fill_(float("nan"))
     eles.batch_run(batch, us, ubs, taus)
     assert eles.batch_captures(batch) == 2
-    eles.plan_set_variant(plans[1], 1 * 16 + 4)    # CUDA-core fused kernel
+    eles.plan_set_variant(plans[1], 0 * 16 + 8)    # unfused CUDA-core kernels
     eles.batch_run(batch, us, ubs, taus)
     assert eles.batch_captures(batch) == 3
     torch.cuda.synchronize()

@@ -54,9 +54,11 @@ def grids(nx, ny, nz, Lx, Lz, nlx, nly, nlz):
     return dns, I.les_grid(dns, nlx, nly, nlz)
 
 
-@pytest.mark.parametrize("prec", [eles.PREC_FP64, eles.PREC_FP32, eles.PREC_BF16X3])
+@pytest.mark.parametrize("prec", [eles.PREC_FP64, eles.PREC_FP32, eles.PREC_BF16X3, eles.PREC_TF32X2])
 @pytest.mark.parametrize("geom", ["tiny", "tc2"])
 def test_stress_outputs(prec, geom):
+    if geom == "tiny" and prec in (eles.PREC_BF16X3, eles.PREC_TF32X2):
+        pytest.skip("split precision needs a tensor-core geometry")
     if geom == "tiny":
         dns, les = grids(32, 33, 32, 2 * math.pi, math.pi, 8, 9, 8)
         delta = 2 * math.pi / 16

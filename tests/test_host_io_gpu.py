@@ -28,7 +28,7 @@ def built():
     entry.build()
 
 
-@pytest.mark.parametrize("prec", [eles.PREC_FP32, eles.PREC_BF16X3])
+@pytest.mark.parametrize("prec", [eles.PREC_FP32, eles.PREC_BF16X3, eles.PREC_TF32X2])
 @pytest.mark.parametrize("chunk", [1, 2])
 def test_host_pipeline_equals_device_call(prec, chunk):
     dns = I.dns_grid(128, 65, 128, 2 * math.pi, math.pi)

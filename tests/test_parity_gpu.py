@@ -4,8 +4,9 @@ Tolerances:
   * FP64 path: per component, max |GPU - oracle| <= 1e-12 max(|oracle|, 1)
     (the plain formula cancels bar(u1 u1) ~ 400 to T11 ~ 1..20, so the
     oracle itself carries ~1e-14 relative roundoff);
-  * FP32 path: max |GPU - oracle| <= 1e-4 u_tau^2 for every T_ij component
-    (velocities in units of u_tau) and <= 1e-4 for ~bar(u_i).
+  * FP32 and split-precision paths (BF16X3, TF32X2): max |GPU - oracle|
+    <= 1e-4 u_tau^2 for every T_ij component (velocities in units of u_tau)
+    and <= 1e-4 for ~bar(u_i).
 Operator weights are compared entry by entry with the oracle's FP64 operators.
 """
 import math
@@ -70,7 +71,15 @@ CASES = {
     # stride 8, 8 x warps, odd first output of the x stream, 24 outputs per row
     # (not a multiple of the four B rotations): warp-specialised tensor-core kernel
     "tc2": (192, 33, 256, 2 * math.pi, math.pi, 24, 17, 32, 10 * math.pi / 192),
+    # stride 8 with a wide x filter (2.5 Delta = 30 x cells): two output phases
+    "wide": (128, 65, 128, 2 * math.pi, math.pi, 16, 17, 16, 24 * math.pi / 128),
+    # stride 4 in x and z (the batched configuration's LES = DNS / 4)
+    "s4": (128, 65, 128, 4 * math.pi, 2 * math.pi, 32, 17, 32, 4 * math.pi / 20),
+    # stride 4 with a wide filter (2.5 Delta = 35 x cells): four output phases
+    "s4w": (256, 49, 128, 4 * math.pi, 2 * math.pi, 64, 13, 32, 0.7),
 }
+SPLIT = (eles.PREC_BF16X3, eles.PREC_TF32X2)
+TC_CASES = ("tc", "tc2", "wide", "s4", "s4w")
 
 
 def case(name, seed=1000):
@@ -92,8 +101,10 @@ def test_weights_match_oracle(name):
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
-@pytest.mark.parametrize("prec", [eles.PREC_FP64, eles.PREC_FP32, eles.PREC_BF16X3])
+@pytest.mark.parametrize("prec", [eles.PREC_FP64, eles.PREC_FP32, eles.PREC_BF16X3, eles.PREC_TF32X2])
 def test_subfilter_stress_matches_oracle(name, prec):
+    if prec in SPLIT and name not in TC_CASES:
+        pytest.skip("split precision runs on tensor-core geometries only (refusal tested below)")
     dns, les, delta, u = case(name)
     ub_ref, tau_ref = O.subfilter_stress(dns, les, delta, u)
     plan, (ub, tau) = run_gpu(dns, les, delta, u, prec)
@@ -136,15 +147,17 @@ def big_field():
     return _BIG["v"]
 
 
-@pytest.mark.parametrize("dfrac,prec", [(64, eles.PREC_FP32), (32, eles.PREC_FP32), (64, eles.PREC_BF16X3)])
+@pytest.mark.parametrize("dfrac,prec", [(64, eles.PREC_FP32), (32, eles.PREC_FP32), (64, eles.PREC_BF16X3),
+                                        (32, eles.PREC_BF16X3), (64, eles.PREC_TF32X2), (32, eles.PREC_TF32X2)])
 def test_full_size_sampled_points(dfrac, prec):
     """512 x 257 x 384 -> 64 x 65 x 48 at full size, checked at seeded LES
     points (wall rows included) by the oracle's direct 3-D summation."""
     dns, les, u = big_field()
     delta = dns.Lx / dfrac
     plan, (ub, tau) = run_gpu(dns, les, delta, u, prec)
-    if prec == eles.PREC_BF16X3:
+    if prec in SPLIT:
         assert eles.plan_info(plan, 10) == 3          # warp-specialised tensor-core x-z kernel
+        assert eles.plan_info(plan, 15) == (1 if dfrac == 64 else 2)   # output phases
     rng = np.random.default_rng(3)
     pts = np.stack([rng.integers(0, les.nx, 12), rng.integers(0, les.ny, 12),
                     rng.integers(0, les.nz, 12)], axis=1)
@@ -245,17 +258,19 @@ def test_tensor_core_variant_selected():
         eles.plan_set_variant(plan32, 3 * 16 + 2)     # no tensor cores for an FP32 plan
 
 
-@pytest.mark.parametrize("name", ["tc", "tc2"])
-@pytest.mark.parametrize("variant", [2, 3])
-def test_tensor_core_variants_match_oracle(name, variant):
-    """Both tensor-core x-z kernels (slide and warp-specialised), with and
-    without plane means, against the oracle; the plane means against the
-    FP64 mean of the field."""
+@pytest.mark.parametrize("name,variant,prec", [("tc", 2, eles.PREC_BF16X3), ("tc2", 2, eles.PREC_BF16X3)] +
+                         [(n, 3, pr) for n in TC_CASES for pr in SPLIT])
+def test_tensor_core_variants_match_oracle(name, variant, prec):
+    """Both tensor-core x-z kernels (slide and warp-specialised; one, two or
+    four output phases; x stride 8 and 4), with and without plane means,
+    against the oracle; the plane means against the FP64 mean of the field."""
     dns, les, delta, u = case(name, seed=31)
     ub_ref, tau_ref = O.subfilter_stress(dns, les, delta, u)
-    plan = eles.filter_setup(dns, les, delta, precision=eles.PREC_BF16X3)
+    plan = eles.filter_setup(dns, les, delta, precision=prec)
     eles.plan_set_variant(plan, variant * 16 + 2)
     assert eles.plan_info(plan, 10) == variant
+    if variant == 3:
+        assert eles.plan_info(plan, 15) == {"wide": 2, "s4": 2, "s4w": 4}.get(name, 1)
     dev = torch.device("cuda")
     ud = torch.from_numpy(u).to(dev, torch.float32)
     for with_mean in (False, True):
@@ -287,8 +302,8 @@ def test_repeat_calls_are_bitwise_stable():
     assert torch.equal(outs[0], outs[1])
 
 
-@pytest.mark.parametrize("name", ["tiny", "tc"])
-@pytest.mark.parametrize("prec", [eles.PREC_FP64, eles.PREC_FP32, eles.PREC_BF16X3])
+@pytest.mark.parametrize("name,prec", [("tiny", eles.PREC_FP64), ("tiny", eles.PREC_FP32), ("tc", eles.PREC_FP64),
+                                       ("tc", eles.PREC_FP32), ("tc", eles.PREC_BF16X3), ("tc", eles.PREC_TF32X2)])
 def test_hat_quadrature_matches_oracle(name, prec):
     """EF_KERNEL_GAUSSIAN_HAT: the y operators built on the device equal the
     oracle's hat-quadrature operators, and the whole path matches the
@@ -311,6 +326,17 @@ def test_hat_quadrature_matches_oracle(name, prec):
     assert_close(tau.double().cpu().numpy(), tau_ref, tol, "tau")
     # the trapezoid operator differs (the quadrature really changed)
     assert np.abs(eles.plan_weights(plan, 2) - O.op_wall(dns.y, les.y, delta, +1)).max() > 1e-8
+
+
+@pytest.mark.parametrize("name", ["tiny", "tiles", "stride6", "interp"])
+@pytest.mark.parametrize("prec", [eles.PREC_BF16X3, eles.PREC_TF32X2])
+def test_split_precision_refused_off_tensor_cores(name, prec):
+    """A split-precision plan on a geometry the tensor-core x-z kernels do not
+    cover is refused (EF_ERR_UNSUPPORTED) rather than run on CUDA cores."""
+    dns, les, delta, _ = case(name)
+    with pytest.raises(eles.EFError) as e:
+        eles.filter_setup(dns, les, delta, precision=prec)
+    assert e.value.code == 7
 
 
 @pytest.mark.parametrize("name", ["tc", "tc2"])
@@ -338,13 +364,16 @@ def test_cuda_core_y_after_tensor_core_xz(name):
     assert eles.plan_info(plan, 13) == 1
 
 
-def test_full_size_whole_grid_bf16x3():
-    """512 x 257 x 384 -> 64 x 65 x 48, Delta = Lx / 64, split BF16 on the
-    tensor cores: every LES point of ubar and T against the oracle's separable
-    FP64 evaluation (the bench's workload and launch configuration)."""
+@pytest.mark.parametrize("dfrac", [64, 32])
+@pytest.mark.parametrize("prec", [eles.PREC_BF16X3, eles.PREC_TF32X2])
+def test_full_size_whole_grid_split_precision(prec, dfrac):
+    """512 x 257 x 384 -> 64 x 65 x 48, Delta = Lx / 64 and Lx / 32, split
+    precision on the tensor cores: every LES point of ubar and T against the
+    oracle's separable FP64 evaluation (the bench's workloads and launch
+    configuration)."""
     dns, les, u = big_field()
-    delta = dns.Lx / 64
-    plan, (ub, tau) = run_gpu(dns, les, delta, u, eles.PREC_BF16X3)
+    delta = dns.Lx / dfrac
+    plan, (ub, tau) = run_gpu(dns, les, delta, u, prec)
     assert eles.plan_info(plan, 10) == 3 and eles.plan_info(plan, 13) == 1
     ub_ref, tau_ref = O.subfilter_stress(dns, les, delta, u)
     assert_close(ub, ub_ref, TOL32, "ubar")
