@@ -104,6 +104,7 @@ struct YArgs {
     T *tmp;                // [S][12][nly][nlz][nlx]: q_a and C_ab between the two passes
     int ny, nly, nlz, nlx;
     int stress, flip;      // flip: Eq. 9 parities
+    int ptrans;            // h planes in (X, Z) order; outputs are written in (Z, X) order
     int *err;
 };
 
@@ -130,6 +131,7 @@ struct YTcArgs {
     float *ubar, *tau;             // [S][3][nly][nplane], [S][6][nly][nplane]
     float *tmp;                    // [S][kYTmp][nly][nplane]
     int ny, nly, nplane, stress, flip;
+    int nlz, nlx, ptrans;          // ptrans: h planes in (X, Z) order; outputs are written in (Z, X) order
     int *err;
 };
 bool ytc_geometry(const std::vector<int> &ystart, const std::vector<int> &ycount, int ny, int nplane, YTcGeom *g);

@@ -494,6 +494,7 @@ int run_group(ef_plan *p, int ns, const T *u, T *ubar, T *tau, double *plane_mea
             yt.frag = p->d_yfrag; yt.AU = p->d_AU; yt.Kab = p->d_Kab;
             yt.ubar = ubar; yt.tau = tau; yt.tmp = static_cast<float *>(p->d_ytmp);
             yt.ny = p->ny; yt.nly = p->nly; yt.nplane = nplane;
+            yt.nlz = p->nlz; yt.nlx = p->nlx; yt.ptrans = p->fused && p->x_variant == 3;
             yt.stress = stress ? 1 : 0; yt.flip = p->ext == EF_EXT_ODD_EVEN; yt.err = p->d_err;
             e = launch_ytc(yt, ns, s);
             if (e != cudaSuccess) return cuda_fail(e, "ytc launch");
@@ -508,6 +509,7 @@ int run_group(ef_plan *p, int ns, const T *u, T *ubar, T *tau, double *plane_mea
     y.h = h; y.wy = wy; y.AU = p->d_AU; y.AUU = p->d_AUU; y.ystart = p->d_ystart; y.ycount = p->d_ycount;
     y.ubar = ubar; y.tau = tau; y.tmp = static_cast<T *>(p->d_ytmp); y.ny = p->ny; y.nly = p->nly; y.nlz = p->nlz; y.nlx = p->nlx;
     y.stress = stress ? 1 : 0; y.flip = p->ext == EF_EXT_ODD_EVEN; y.err = p->d_err;
+    y.ptrans = p->fused && p->x_variant == 3;
     e = launch_ypass<T>(y, ns, s);
     if (e != cudaSuccess) return cuda_fail(e, "ypass launch");
     prof_mark(pe, 3, s);

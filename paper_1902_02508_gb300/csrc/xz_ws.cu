@@ -77,6 +77,18 @@ double bweight(const Ring &r, int xi, int n, int xc0, int OP, int bshift)
     return (dd >= 0 && dd < r.D) ? r.W64[(xi % r.r) * r.D + dd] : 0.0;
 }
 
+// Reference profile U_c(y_j): the mean of z-row 0 of each plane, one warp
+// per (component, plane, snapshot), FP64 sum.
+__global__ void __launch_bounds__(96) ws_uref(const float *__restrict__ u, int nx, int ny, int nz, double *uref)
+{
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31, j = blockIdx.x, s = blockIdx.y;
+    const float *r0 = u + (((size_t)s * 3 + c) * ny + j) * (size_t)nz * nx;
+    double acc = 0.0;
+    for (int i = lane; i < nx; i += 32) acc += (double)r0[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) uref[((size_t)s * 3 + c) * ny + j] = (double)(float)(acc / nx);
+}
+
 }  // namespace
 
 // z-operator A fragments for the tensor-core z phase: k-step kk, lane
@@ -274,6 +286,8 @@ int ws_run(const ef_plan *p, int nsnap, const float *u, float *h, double *uref, 
     a.box_rows = p->nz > 256 ? p->nz / 2 : p->nz;
     int rc = encode_u_map(u, p->nx, p->ny, p->nz, nsnap, ws::CW, a.box_rows, &a.tmap);
     if (rc) return rc;
+    // the reference profile first (1/nz of a plane read), then the persistent kernel
+    ws_uref<<<dim3(p->ny, nsnap), 96, 0, st>>>(u, p->nx, p->ny, p->nz, uref);
     a.u = u; a.h = h; a.uref = uref; a.plane_mean = plane_mean; a.err = p->d_err;
     a.nx = p->nx; a.ny = p->ny; a.nz = p->nz; a.nlx = p->nlx; a.nlz = p->nlz;
     a.nchunk = w.nchunk; a.bshift = w.bshift; a.rx = p->rx.r; a.CB = w.CB; a.OP = w.OP;

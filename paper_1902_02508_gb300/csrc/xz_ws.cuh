@@ -1,8 +1,10 @@
 // Warp-specialised x-z kernel on the tensor cores (x_variant 3), for the
 // split-precision plans: EF_PREC_BF16X3 and EF_PREC_TF32X2.
 //
-// One CTA per (snapshot, y-plane, output phase) with three roles that meet
-// only at mbarriers (every wait bounded):
+// A persistent grid (as many CTAs as fit at once) walks the items (snapshot,
+// y-plane, output phase); in each CTA three roles meet only at mbarriers
+// (every wait bounded), and the producer streams the next item while the
+// other roles finish the current one:
 //   * NZ / 32 x warps (32 z-rows each) contract x with mma.sync on the tensor
 //     cores, FP32 accumulation;
 //   * one producer warp streams the plane through TMA stages of one chunk
@@ -64,8 +66,8 @@ struct Bw { static constexpr int n = MODE == MODE_TF32X2 ? 3 : 1; };
 struct WsArgs {
     CUtensorMap tmap;     // TMA view of u: {nx, nz, 3 ny S} floats, box {16, box_rows, 1}
     const float *u;       // [S][3][ny][nz][nx]
-    float *h;             // [S][9][ny][nlz][nlx]
-    double *uref;         // [S][3][ny]
+    float *h;             // [S][9][ny][nlx][nlz]: the plane in (X, Z) order, Z fastest
+    const double *uref;   // [S][3][ny]: the reference profile (written by ws_uref before the launch)
     double *plane_mean;   // [S][3][ny] or nullptr
     int *err;             // device error word
     int nx, ny, nz, nlx, nlz;
@@ -77,6 +79,7 @@ struct WsArgs {
     int xc0[4];           // per phase: first output completed by chunk 0 (may be < 0)
     int RZ, KS, zoff;     // z phase: stride, k-steps per Z tile, window offset
     int nf;               // fields contracted in z (9, or 3 for the velocities only)
+    int nsnap;            // snapshots (items are (snapshot, y-plane, phase))
     const uint4 *afrag;   // z A fragments [KS][hi, lo][32 lanes] (pair order)
     const uint4 *bvar;    // x B fragments [OP][NR][32 lanes][Bw]
 };
@@ -230,7 +233,10 @@ __device__ __forceinline__ bool wait_or_abort(unsigned long long *bar, unsigned 
 // k = 2i + e -> row i + 8e, which the A fragments follow.  One A fragment
 // load per k-step feeds all NT column tiles.  The window starts on a 16-row
 // boundary (zoff is a multiple of 16), so a k-step wraps periodically as a
-// whole or not at all.  Lanes whose column is idle use zeros.
+// whole or not at all.  Lanes whose column is idle use zeros.  Outputs go to
+// h in (X, Z) plane order (Z fastest), so that each store instruction writes
+// 4 runs of 8 consecutive floats instead of 32 scattered ones (a chunk
+// completes whole Z columns of one or two X); the y passes transpose back.
 template <int OPC, int NT, int LD>
 __device__ __forceinline__ void z_tile(const WsArgs &a, const float *colb, const uint4 *afrag,
                                        int s, int j, int X0, bool val0, bool val1, int zt, int nt0, int lane)
@@ -274,9 +280,11 @@ __device__ __forceinline__ void z_tile(const WsArgs &a, const float *colb, const
             if (cc >= OPC * NF) continue;
             const int n = cc >= NF ? 1 : 0, f = cc - n * NF;
             if (f >= a.nf || !(n ? val1 : val0)) continue;
-            float *hout = a.h + ((((size_t)s * NF + f) * a.ny + j) * a.nlz + 16 * zt) * a.nlx + X0 + a.OP * n;
-            hout[(size_t)g * a.nlx] = (acc[i][0][e] + acc[i][1][e]) + acc[i][2][e];
-            hout[(size_t)(g + 8) * a.nlx] = (acc[i][0][2 + e] + acc[i][1][2 + e]) + acc[i][2][2 + e];
+            // h plane in (X, Z) order, Z fastest: the 8 rows g of a store are contiguous
+            float *hout = a.h + (((size_t)s * NF + f) * a.ny + j) * ((size_t)a.nlz * a.nlx) +
+                          (size_t)(X0 + a.OP * n) * a.nlz + 16 * zt;
+            hout[g] = (acc[i][0][e] + acc[i][1][e]) + acc[i][2][e];
+            hout[g + 8] = (acc[i][0][2 + e] + acc[i][1][2 + e]) + acc[i][2][2 + e];
         }
 }
 
@@ -316,11 +324,13 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
         stg = reinterpret_cast<float *>(end + (((sa + 127u) & ~127u) - sa));
     }
     __shared__ alignas(8) unsigned long long full[CSTG], empty[CSTG], cfull[2], cempty[2];
-    __shared__ float Us[3];
     __shared__ int abort_flag;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t = lane & 3;
-    const int p = blockIdx.x % a.OP, j = blockIdx.x / a.OP, s = blockIdx.y;
+    // persistent: items (snapshot, plane, phase) = it, it + gridDim.x, ...;
+    // gridDim.x is a multiple of OP, so the phase of a CTA is fixed
+    const int p = blockIdx.x % a.OP;
+    const int nitems = a.ny * a.OP * a.nsnap;
     const size_t np = (size_t)a.nx * a.ny * NZ;
     const int nchunk = a.nchunk;
     const bool pm = a.plane_mean != nullptr && p == 0;
@@ -340,168 +350,175 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
     }
     __syncthreads();
 
-    if (warp == NXW) {   // producer: stage k = chunk k = x blocks CB k - bshift .. + CB - 1
+    // warp 0: producer; warps 1 .. kZW: z warps; the rest: x warps.  The
+    // producer and z warps take the lowest warp ids (the schedulers prefer
+    // older warps).
+    if (warp == 0) {   // producer: stage k = chunk k = x blocks CB k - bshift .. + CB - 1, item by item
         if (lane == 0) {
-            const int pc0 = s * 3 * a.ny + j;  // TMA plane coordinate of component 0
-            int issued = 0;
-            for (int k = 0; k < nchunk; k++) {
-                const int st = k % CSTG;
-                if (k >= CSTG && !wait_or_abort(&empty[st], ((k / CSTG) - 1) & 1, abort_v, a.err)) break;
-                if (*abort_v) break;
-                int b = (a.CB * k - a.bshift) % a.nlx;   // a multiple of CB: the chunk never wraps
-                if (b < 0) b += a.nlx;
-                proxy_fence();
-                float *buf = stg + st * STGF;
-                mbar_expect_tx(&full[st], 3u * NZ * CW * 4u);
-                for (int c = 0; c < 3; c++)
-                    for (int r0 = 0; r0 < NZ; r0 += a.box_rows)
-                        tma_load3(buf + ((size_t)c * NZ + r0) * CW, &a.tmap, &full[st], b * a.rx, r0, pc0 + c * a.ny);
-                issued = k + 1;
+            int gk = 0;
+            for (int it = blockIdx.x; it < nitems && !*abort_v; it += gridDim.x) {
+                const int j = (it / a.OP) % a.ny, s = it / (a.OP * a.ny);
+                const int pc0 = s * 3 * a.ny + j;   // TMA plane coordinate of component 0
+                for (int k = 0; k < nchunk; k++, gk++) {
+                    const int st = gk % CSTG;
+                    if (gk >= CSTG && !wait_or_abort(&empty[st], ((gk / CSTG) - 1) & 1, abort_v, a.err)) break;
+                    if (*abort_v) break;
+                    int b = (a.CB * k - a.bshift) % a.nlx;   // a multiple of CB: the chunk never wraps
+                    if (b < 0) b += a.nlx;
+                    proxy_fence();
+                    float *buf = stg + st * STGF;
+                    mbar_expect_tx(&full[st], 3u * NZ * CW * 4u);
+                    for (int c = 0; c < 3; c++)
+                        for (int r0 = 0; r0 < NZ; r0 += a.box_rows)
+                            tma_load3(buf + ((size_t)c * NZ + r0) * CW, &a.tmap, &full[st], b * a.rx, r0,
+                                      pc0 + c * a.ny);
+                }
             }
             // no copy may be in flight when the CTA exits
-            for (int k = issued > CSTG ? issued - CSTG : 0; k < issued; k++)
-                mbar_wait(&full[k % CSTG], (k / CSTG) & 1, a.err);
+            for (int k = gk > CSTG ? gk - CSTG : 0; k < gk; k++) mbar_wait(&full[k % CSTG], (k / CSTG) & 1, a.err);
         }
         return;
     }
 
-    // x and z warps: z fragments, this phase's rotated x fragments, reference profile
+    // x and z warps: z fragments, this phase's rotated x fragments
     constexpr int nwork = G::THREADS - 32;
-    const int wtid = tid < 32 * NXW ? tid : tid - 32;
+    const int wtid = tid - 32;
     for (int i = wtid; i < KS * 64; i += nwork) afrag[i] = a.afrag[i];
     for (int i = wtid; i < NR * 32 * BW; i += nwork) bvar[i] = a.bvar[(size_t)p * NR * 32 * BW + i];
-    const float *plane = a.u + (size_t)s * 3 * np + (size_t)j * NZ * a.nx;
-    const int wk = warp < NXW ? warp : warp - 1;  // index among the x and z warps
-    if (wk < 3) {
-        const float *r0 = plane + (size_t)wk * np;
-        double acc = 0.0;
-        for (int i = lane; i < a.nx; i += 32) acc += (double)r0[i];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) {
-            const float Uc = (float)(acc / a.nx);
-            Us[wk] = Uc;
-            if (p == 0) a.uref[((size_t)s * 3 + wk) * a.ny + j] = (double)Uc;
-        }
-    }
     named_sync(1, nwork);
 
     const int xc0 = a.xc0[p];
-    if (warp < NXW) {   // ---------------- x warps
-        volatile float *Uv = Us;    // re-read per tile: keeps three register pairs free
-        float acc[2][NF][4];
+    const int xw = warp - 1 - kZW;                // x warp index (rows 32 xw ..)
+    if (xw >= 0) {   // ---------------- x warps
+        const float *xrow = stg + (size_t)(xw * 32 + g) * CW + 4 * t;   // this lane's row g, inputs 4t..
+        float *colw0 = colbuf + xw * 32 + 2 * g;
+        // the reference profile U_c(y_j) of each item (uref, written by the
+        // launch before), the next item's read one item ahead
+        auto uref_of = [&](int it, float (&U)[3]) {
+            const int j = (it / a.OP) % a.ny, s = it / (a.OP * a.ny);
 #pragma unroll
-        for (int m = 0; m < 2; m++)
+            for (int c = 0; c < 3; c++) U[c] = it < nitems ? (float)a.uref[((size_t)s * 3 + c) * a.ny + j] : 0.f;
+        };
+        float Un[3];
+        uref_of(blockIdx.x, Un);
+        int gc = 0;                               // chunks of this CTA so far
+        for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+            const float U[3] = {Un[0], Un[1], Un[2]};
+            uref_of(it + gridDim.x, Un);
+            float acc[2][NF][4];
 #pragma unroll
-            for (int f = 0; f < NF; f++)
+            for (int m = 0; m < 2; m++)
 #pragma unroll
-                for (int i = 0; i < 4; i++) acc[m][f][i] = 0.f;
-        const float *xrow = stg + (size_t)(warp * 32 + g) * CW + 4 * t;   // this lane's row g, inputs 4t..
-        float *colw0 = colbuf + warp * 32 + 2 * g;
-        for (int sidx = 0; sidx < nchunk; sidx++) {
-            const int st = sidx % CSTG;
-            if (!wait_or_abort(&full[st], (sidx / CSTG) & 1, abort_v, a.err)) break;
-            const int q = sidx % NR;
-            uint4 B[BW];
+                for (int f = 0; f < NF; f++)
 #pragma unroll
-            for (int w = 0; w < BW; w++) B[w] = bvar[(q * 32 + lane) * BW + w];
-            const float *buf = xrow + st * STGF;
+                    for (int i = 0; i < 4; i++) acc[m][f][i] = 0.f;
+            bool stop = false;
+            for (int sidx = 0; sidx < nchunk; sidx++, gc++) {
+                const int st = gc % CSTG;
+                if (!wait_or_abort(&full[st], (gc / CSTG) & 1, abort_v, a.err)) { stop = true; break; }
+                const int q = sidx % NR;
+                uint4 B[BW];
 #pragma unroll
-            for (int m = 0; m < 2; m++) {
-                float2 v[3][2][2];
+                for (int w = 0; w < BW; w++) B[w] = bvar[(q * 32 + lane) * BW + w];
+                const float *buf = xrow + st * STGF;
 #pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    const float nu = -Uv[c];
-                    const float2 nU = make_float2(nu, nu);
+                for (int m = 0; m < 2; m++) {
+                    float2 v[3][2][2];
 #pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        const float4 x = *reinterpret_cast<const float4 *>(buf + (c * NZ + 16 * m + 8 * h) * CW);
-                        v[c][h][0] = __fadd2_rn(make_float2(x.x, x.y), nU);
-                        v[c][h][1] = __fadd2_rn(make_float2(x.z, x.w), nU);
+                    for (int c = 0; c < 3; c++) {
+                        const float2 nU = make_float2(-U[c], -U[c]);
+#pragma unroll
+                        for (int h = 0; h < 2; h++) {
+                            const float4 x = *reinterpret_cast<const float4 *>(buf + (c * NZ + 16 * m + 8 * h) * CW);
+                            v[c][h][0] = __fadd2_rn(make_float2(x.x, x.y), nU);
+                            v[c][h][1] = __fadd2_rn(make_float2(x.z, x.w), nU);
+                        }
                     }
+                    x_mma<MODE, 0>(acc[m], v, B);
                 }
-                x_mma<MODE, 0>(acc[m], v, B);
-            }
-            mbar_arrive(&empty[st]);
-            // the chunk completes phase outputs X0 + OP i, i < OPC (tile columns OPC q + i)
-            const int cb = sidx & 1;
-            if (sidx >= 2 && !wait_or_abort(&cempty[cb], ((sidx >> 1) - 1) & 1, abort_v, a.err)) break;
-            const int X0 = xc0 + a.OP * OPC * sidx;
-            const int b0 = a.CB * sidx - a.bshift;     // first x block of the chunk
-            float *colw = colw0 + (size_t)cb * NCBO * LD;
-            const int csum = (OPC * q + 7) & 7;        // the idle column: row sums
-            // rows (g, g + 8) of each 16-row block as one pair
-            auto park = [&](float *dst, float r0, float r8) { *reinterpret_cast<float2 *>(dst) = make_float2(r0, r8); };
-            if constexpr (OPC == 2) {
-                // columns 2q, 2q + 1 (lanes t == q, elements 0 and 1)
-                if (t == q) {
+                mbar_arrive(&empty[st]);
+                // the chunk completes phase outputs X0 + OP i, i < OPC (tile columns OPC q + i)
+                const int cb = gc & 1;
+                if (gc >= 2 && !wait_or_abort(&cempty[cb], ((gc >> 1) - 1) & 1, abort_v, a.err)) { stop = true; break; }
+                const int X0 = xc0 + a.OP * OPC * sidx;
+                const int b0 = a.CB * sidx - a.bshift;     // first x block of the chunk
+                float *colw = colw0 + (size_t)cb * NCBO * LD;
+                const int csum = (OPC * q + 7) & 7;        // the idle column: row sums
+                // rows (g, g + 8) of each 16-row block as one pair
+                auto park = [&](float *dst, float r0, float r8) { *reinterpret_cast<float2 *>(dst) = make_float2(r0, r8); };
+                if constexpr (OPC == 2) {
+                    // columns 2q, 2q + 1 (lanes t == q, elements 0 and 1)
+                    if (t == q) {
 #pragma unroll
-                    for (int n = 0; n < 2; n++)
-                        if (X0 + a.OP * n >= 0 && X0 + a.OP * n < a.nlx) {
+                        for (int n = 0; n < 2; n++)
+                            if (X0 + a.OP * n >= 0 && X0 + a.OP * n < a.nlx) {
+#pragma unroll
+                                for (int m = 0; m < 2; m++)
+#pragma unroll
+                                    for (int f = 0; f < NF; f++)
+                                        park(colw + (n * NF + f) * LD + 16 * m, acc[m][f][n], acc[m][f][2 + n]);
+                            }
+                    }
+                } else {
+                    // column q (lanes t == q / 2, element q % 2)
+                    if (t == (q >> 1) && X0 >= 0 && X0 < a.nlx) {
+                        if (q & 1) {
 #pragma unroll
                             for (int m = 0; m < 2; m++)
 #pragma unroll
-                                for (int f = 0; f < NF; f++)
-                                    park(colw + (n * NF + f) * LD + 16 * m, acc[m][f][n], acc[m][f][2 + n]);
+                                for (int f = 0; f < NF; f++) park(colw + f * LD + 16 * m, acc[m][f][1], acc[m][f][3]);
+                        } else {
+#pragma unroll
+                            for (int m = 0; m < 2; m++)
+#pragma unroll
+                                for (int f = 0; f < NF; f++) park(colw + f * LD + 16 * m, acc[m][f][0], acc[m][f][2]);
+                        }
+                    }
+                }
+                // row sums of fields 0-2 (the idle column) go to parked columns NCOL + c
+                // when the chunk's blocks are owned (each input counted once)
+                if (pm && t == (csum >> 1) && b0 >= 0 && b0 < a.nlx) {
+                    const int es = csum & 1;
+#pragma unroll
+                    for (int m = 0; m < 2; m++)
+#pragma unroll
+                        for (int c = 0; c < 3; c++)
+                            *reinterpret_cast<float2 *>(colw + (NCOL + c) * LD + 16 * m) =
+                                es ? make_float2(acc[m][c][1], acc[m][c][3]) : make_float2(acc[m][c][0], acc[m][c][2]);
+                }
+                // clear the completed columns and the sum column without a branch; a
+                // non-finite value stays in its column, and the y pass flags it
+                {
+                    const unsigned clr = (((OPC == 2 ? 3u : 1u) << (OPC * q)) | (1u << csum)) >> (2 * t);
+                    const float2 keep = make_float2(clr & 1u ? 0.f : 1.f, clr & 2u ? 0.f : 1.f);
+#pragma unroll
+                    for (int m = 0; m < 2; m++)
+#pragma unroll
+                        for (int f = 0; f < NF; f++) {
+                            const float2 lo = __fmul2_rn(make_float2(acc[m][f][0], acc[m][f][1]), keep);
+                            const float2 hi = __fmul2_rn(make_float2(acc[m][f][2], acc[m][f][3]), keep);
+                            acc[m][f][0] = lo.x; acc[m][f][1] = lo.y; acc[m][f][2] = hi.x; acc[m][f][3] = hi.y;
                         }
                 }
-            } else {
-                // column q (lanes t == q / 2, element q % 2)
-                if (t == (q >> 1) && X0 >= 0 && X0 < a.nlx) {
-                    if (q & 1) {
-#pragma unroll
-                        for (int m = 0; m < 2; m++)
-#pragma unroll
-                            for (int f = 0; f < NF; f++) park(colw + f * LD + 16 * m, acc[m][f][1], acc[m][f][3]);
-                    } else {
-#pragma unroll
-                        for (int m = 0; m < 2; m++)
-#pragma unroll
-                            for (int f = 0; f < NF; f++) park(colw + f * LD + 16 * m, acc[m][f][0], acc[m][f][2]);
-                    }
-                }
-            }
-            // row sums of fields 0-2 (the idle column) go to parked columns NCOL + c
-            // when the chunk's blocks are owned (each input counted once)
-            if (pm && t == (csum >> 1) && b0 >= 0 && b0 < a.nlx) {
-                const int es = csum & 1;
-#pragma unroll
-                for (int m = 0; m < 2; m++)
-#pragma unroll
-                    for (int c = 0; c < 3; c++)
-                        *reinterpret_cast<float2 *>(colw + (NCOL + c) * LD + 16 * m) =
-                            es ? make_float2(acc[m][c][1], acc[m][c][3]) : make_float2(acc[m][c][0], acc[m][c][2]);
-            }
-            // clear the completed columns and the sum column without a branch; a
-            // non-finite value stays in its column, and the y pass flags it
-            {
-                const unsigned clr = (((OPC == 2 ? 3u : 1u) << (OPC * q)) | (1u << csum)) >> (2 * t);
-                const float2 keep = make_float2(clr & 1u ? 0.f : 1.f, clr & 2u ? 0.f : 1.f);
-#pragma unroll
-                for (int m = 0; m < 2; m++)
-#pragma unroll
-                    for (int f = 0; f < NF; f++) {
-                        const float2 lo = __fmul2_rn(make_float2(acc[m][f][0], acc[m][f][1]), keep);
-                        const float2 hi = __fmul2_rn(make_float2(acc[m][f][2], acc[m][f][3]), keep);
-                        acc[m][f][0] = lo.x; acc[m][f][1] = lo.y; acc[m][f][2] = hi.x; acc[m][f][3] = hi.y;
-                    }
-            }
-            // split the warp's parked pairs into (hi, lo) bf16 words in place, all
-            // lanes sharing the work: NCOL columns x 2 blocks x 8 pairs
-            {
+                // split the warp's parked pairs into (hi, lo) bf16 words in place, all
+                // lanes sharing the work: NCOL columns x 2 blocks x 8 pairs
                 __syncwarp();
-                float *cw = colbuf + (size_t)cb * NCBO * LD + warp * 32;
+                {
+                    float *cw = colbuf + (size_t)cb * NCBO * LD + xw * 32;
 #pragma unroll
-                for (int r = 0; r < (NCOL * 16 + 31) / 32; r++) {
-                    const int pidx = lane + 32 * r, col = pidx >> 4, off = pidx & 15;
-                    if (NCOL * 16 % 32 == 0 || pidx < NCOL * 16) {
-                        float2 *pp = reinterpret_cast<float2 *>(cw + (size_t)col * LD) + off;
-                        unsigned hi, lo;
-                        split2(*pp, hi, lo);
-                        *reinterpret_cast<uint2 *>(pp) = make_uint2(hi, lo);
+                    for (int r = 0; r < (NCOL * 16 + 31) / 32; r++) {
+                        const int pidx = lane + 32 * r, col = pidx >> 4, off = pidx & 15;
+                        if (NCOL * 16 % 32 == 0 || pidx < NCOL * 16) {
+                            float2 *pp = reinterpret_cast<float2 *>(cw + (size_t)col * LD) + off;
+                            unsigned hi, lo;
+                            split2(*pp, hi, lo);
+                            *reinterpret_cast<uint2 *>(pp) = make_uint2(hi, lo);
+                        }
                     }
                 }
+                mbar_arrive(&cfull[cb]);
             }
-            mbar_arrive(&cfull[cb]);
+            if (stop) break;
         }
         return;
     }
@@ -510,38 +527,46 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
     // tile zw and every column tile; otherwise the (Z tile, column tile) pairs
     // round robin.  z warp c < 3 also sums the parked row sums of component c.
     constexpr int NCT = (NCOL + 7) / 8;          // column tiles
-    const int zw = warp - NXW - 1;
+    const int zw = warp - 1;
     const int nzt = a.nlz / 16;
-    double pmean = 0.0;
-    for (int sidx = 0; sidx < nchunk; sidx++) {
-        const int cb = sidx & 1;
-        if (!wait_or_abort(&cfull[cb], (sidx >> 1) & 1, abort_v, a.err)) break;
-        const int X0 = xc0 + a.OP * OPC * sidx;
-        const bool val0 = X0 >= 0 && X0 < a.nlx;
-        const bool val1 = OPC == 2 && X0 + a.OP >= 0 && X0 + a.OP < a.nlx;
-        const float *colb = colbuf + (size_t)cb * NCBO * LD;
+    int gc = 0;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int j = (it / a.OP) % a.ny, s = it / (a.OP * a.ny);
+        double pmean = 0.0;
+        bool stop = false;
+        for (int sidx = 0; sidx < nchunk; sidx++, gc++) {
+            const int cb = gc & 1;
+            if (!wait_or_abort(&cfull[cb], (gc >> 1) & 1, abort_v, a.err)) { stop = true; break; }
+            const int X0 = xc0 + a.OP * OPC * sidx;
+            const bool val0 = X0 >= 0 && X0 < a.nlx;
+            const bool val1 = OPC == 2 && X0 + a.OP >= 0 && X0 + a.OP < a.nlx;
+            const float *colb = colbuf + (size_t)cb * NCBO * LD;
+            if (pm && zw < 3) {
+                const int b0 = a.CB * sidx - a.bshift;
+                if (b0 >= 0 && b0 < a.nlx) {
+                    float ssum = 0.f;
+                    for (int z = lane; z < NZ; z += 32) ssum += colb[(NCOL + zw) * LD + z];
+                    pmean += (double)ssum;
+                }
+            }
+            if (val0 || val1) {
+                if (nzt == kZW) {
+                    z_tile<OPC, NCT, LD>(a, colb, afrag, s, j, X0, val0, val1, zw, 0, lane);
+                } else {
+                    for (int w = zw; w < NCT * nzt; w += kZW)
+                        z_tile<OPC, 1, LD>(a, colb, afrag, s, j, X0, val0, val1, w / NCT, w % NCT, lane);
+                }
+            }
+            mbar_arrive(&cempty[cb]);
+        }
+        if (stop) break;
         if (pm && zw < 3) {
-            const int b0 = a.CB * sidx - a.bshift;
-            if (b0 >= 0 && b0 < a.nlx) {
-                float ssum = 0.f;
-                for (int z = lane; z < NZ; z += 32) ssum += colb[(NCOL + zw) * LD + z];
-                pmean += (double)ssum;
+            for (int o = 16; o > 0; o >>= 1) pmean += __shfl_xor_sync(0xffffffffu, pmean, o);
+            if (lane == 0) {
+                const size_t k = ((size_t)s * 3 + zw) * a.ny + j;
+                a.plane_mean[k] = (double)(float)a.uref[k] + pmean / ((double)a.nx * NZ);
             }
         }
-        if (val0 || val1) {
-            if (nzt == kZW) {
-                z_tile<OPC, NCT, LD>(a, colb, afrag, s, j, X0, val0, val1, zw, 0, lane);
-            } else {
-                for (int it = zw; it < NCT * nzt; it += kZW)
-                    z_tile<OPC, 1, LD>(a, colb, afrag, s, j, X0, val0, val1, it / NCT, it % NCT, lane);
-            }
-        }
-        mbar_arrive(&cempty[cb]);
-    }
-    if (pm && zw < 3 && !*abort_v) {
-        for (int o = 16; o > 0; o >>= 1) pmean += __shfl_xor_sync(0xffffffffu, pmean, o);
-        if (lane == 0)
-            a.plane_mean[((size_t)s * 3 + zw) * a.ny + j] = (double)Us[zw] + pmean / ((double)a.nx * NZ);
     }
 }
 
@@ -566,7 +591,24 @@ cudaError_t ws_launch(const WsArgs &a, int nsnap, cudaStream_t st)
         if (e != cudaSuccess) return e;
         attr = smem;
     }
-    xz_ws<NZ, MODE, OPC><<<dim3(a.ny * a.OP, nsnap), Geo<NZ>::THREADS, smem, st>>>(a);
+    // persistent grid: as many CTAs as fit at once, a multiple of OP (each CTA
+    // keeps one output phase), at most one per item
+    static int per_sm = 0, nsm = 0;
+    if (!per_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xz_ws<NZ, MODE, OPC>, Geo<NZ>::THREADS, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int nitems = a.ny * a.OP * nsnap;
+    int grid = nsm * per_sm / a.OP * a.OP;
+    if (grid < a.OP) grid = a.OP;
+    if (grid > nitems) grid = nitems;
+    WsArgs b = a;
+    b.nsnap = nsnap;
+    xz_ws<NZ, MODE, OPC><<<grid, Geo<NZ>::THREADS, smem, st>>>(b);
     return cudaGetLastError();
 }
 

@@ -178,13 +178,15 @@ __global__ void __launch_bounds__(YT) ypass_kernel(const __grid_constant__ YArgs
         const int J = J0 + b;
         if (J >= a.nly) break;
         const size_t o0 = (size_t)J * nplane + p0;
+        // outputs in (Z, X) order; h planes, and the scratch, in h's order
+        const size_t oo = (size_t)J * nplane + (a.ptrans ? (size_t)(p0 % a.nlz) * a.nlx + p0 / a.nlz : (size_t)p0);
         T *tmp = a.tmp + (size_t)s * 12 * nl + o0;
         if constexpr (PASS == 0) {
 #pragma unroll
             for (int c = 0; c < 3; c++) {
                 const double v = AU[c * a.nly + J] + (double)q[b][c];
                 bad |= !isfinite(v);
-                a.ubar[((size_t)s * 3 + c) * nl + o0] = (T)v;
+                a.ubar[((size_t)s * 3 + c) * nl + oo] = (T)v;
             }
             if (cross) {
 #pragma unroll
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(YT) ypass_kernel(const __grid_constant__ YArgs
                 const double v = (AUU[k * a.nly + J] - Ai * Am) + (Cim - Ai * qv[m])
                                + (Cmi - Am * qv[i]) + ((double)q[b][k] - qv[i] * qv[m]);
                 bad |= !isfinite(v);
-                a.tau[((size_t)s * 6 + k) * nl + o0] = (T)v;
+                a.tau[((size_t)s * 6 + k) * nl + oo] = (T)v;
             }
         }
     }

@@ -216,7 +216,8 @@ __global__ void __launch_bounds__(YTW * 32, 5) ytc_kernel(const __grid_constant_
                         if (o == 0) {
                             const float ub = (float)a.AU[((size_t)s * 3 + F) * a.nly + J] + v;
                             bad |= !isfinite(ub);
-                            a.ubar[((size_t)s * 3 + F) * nl + o0 + p] = ub;
+                            const int po = a.ptrans ? (p % a.nlz) * a.nlx + p / a.nlz : p;
+                            a.ubar[((size_t)s * 3 + F) * nl + o0 + po] = ub;
                         }
                         if (a.stress) {
                             const int slot = o == 0 ? F : o == 1 ? 12 + F : 3 + 3 * (o - 2) + F;
@@ -236,15 +237,11 @@ __global__ void __launch_bounds__(YTW * 32, 5) ytc_kernel(const __grid_constant_
 // C_ab - A_y U_a q_b = C'_ab + [p_a odd] A_y U_a d_b.  The first bracket,
 // the only one that cancels large terms, comes formed in FP64 per row (Kab);
 // the rest are O(1) and are summed in FP32.
-__global__ void yrecover_kernel(const __grid_constant__ YTcArgs a, int nsnap)
+// The six T_ab of snapshot s, LES row J, plane point r (in h's plane order).
+__device__ __forceinline__ bool recover_point(const YTcArgs &a, int s, int J, size_t r, float (&out)[6])
 {
     const size_t nl = (size_t)a.nly * a.nplane;
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nl * nsnap) return;
-    const int s = (int)(i / nl);
-    const size_t r = i - (size_t)s * nl;
-    const int J = (int)(r / a.nplane);
-    const float *tmp = a.tmp + (size_t)s * kYTmp * nl + r;
+    const float *tmp = a.tmp + (size_t)s * kYTmp * nl + (size_t)J * a.nplane + r;
     const double *AU = a.AU + (size_t)s * 3 * a.nly;
     const float *K = a.Kab + (size_t)s * 6 * a.nly;
     const int PI[6] = {0, 0, 0, 1, 1, 2}, PJ[6] = {0, 1, 2, 1, 2, 2};
@@ -268,9 +265,59 @@ __global__ void yrecover_kernel(const __grid_constant__ YTcArgs a, int nsnap)
         const int ia = PI[k], m = PJ[k];
         const float Bim = tmp[(size_t)(3 + 3 * ia + m) * nl] + dU[ia][m];
         const float Bmi = tmp[(size_t)(3 + 3 * m + ia) * nl] + dU[m][ia];
-        const float v = K[k * a.nly + J] + (Bim + Bmi) + fmaf(-qv[ia], qv[m], tmp[(size_t)(15 + k) * nl]);
-        bad |= !isfinite(v);
-        a.tau[((size_t)s * 6 + k) * nl + r] = v;
+        out[k] = K[k * a.nly + J] + (Bim + Bmi) + fmaf(-qv[ia], qv[m], tmp[(size_t)(15 + k) * nl]);
+        bad |= !isfinite(out[k]);
+    }
+    return bad;
+}
+
+// T_ab = [A_y(U_a U_b) - A_y U_a A_y U_b] + [C_ab - A_y U_a q_b]
+//      + [C_ba - A_y U_b q_a] + [q_ab - q_a q_b], with
+// C_ab - A_y U_a q_b = C'_ab + [p_a odd] A_y U_a d_b.  The first bracket,
+// the only one that cancels large terms, comes formed in FP64 per row (Kab);
+// the rest are O(1) and are summed in FP32.
+__global__ void yrecover_kernel(const __grid_constant__ YTcArgs a, int nsnap)
+{
+    const size_t nl = (size_t)a.nly * a.nplane;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nl * nsnap) return;
+    const int s = (int)(i / nl);
+    const size_t r = i - (size_t)s * nl;
+    const int J = (int)(r / a.nplane);
+    float out[6];
+    const bool bad = recover_point(a, s, J, r - (size_t)J * a.nplane, out);
+#pragma unroll
+    for (int k = 0; k < 6; k++) a.tau[((size_t)s * 6 + k) * nl + r] = out[k];
+    if (bad && a.err) atomicCAS(a.err, 0, (int)EF_ERR_NAN);
+}
+
+// The same for h planes in (X, Z) order: a 16 x 16 tile of (X, Z) points per
+// block, read along Z and written along X through shared memory.
+__global__ void __launch_bounds__(256) yrecover_t_kernel(const __grid_constant__ YTcArgs a)
+{
+    __shared__ float tile[6][16][17];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int X0 = 16 * blockIdx.x, Z0 = 16 * blockIdx.y;
+    const int J = blockIdx.z % a.nly, s = blockIdx.z / a.nly;
+    const size_t nl = (size_t)a.nly * a.nplane;
+    bool bad = false;
+    {   // read: thread (ty, tx) takes X = X0 + ty, Z = Z0 + tx
+        const int X = X0 + ty, Z = Z0 + tx;
+        if (X < a.nlx && Z < a.nlz) {
+            float out[6];
+            bad = recover_point(a, s, J, (size_t)X * a.nlz + Z, out);
+#pragma unroll
+            for (int k = 0; k < 6; k++) tile[k][tx][ty] = out[k];
+        }
+    }
+    __syncthreads();
+    {   // write: thread (ty, tx) takes Z = Z0 + ty, X = X0 + tx
+        const int Z = Z0 + ty, X = X0 + tx;
+        if (X < a.nlx && Z < a.nlz) {
+#pragma unroll
+            for (int k = 0; k < 6; k++)
+                a.tau[((size_t)s * 6 + k) * nl + (size_t)J * a.nplane + (size_t)Z * a.nlx + X] = tile[k][ty][tx];
+        }
     }
     if (bad && a.err) atomicCAS(a.err, 0, (int)EF_ERR_NAN);
 }
@@ -368,8 +415,12 @@ cudaError_t launch_ytc(const YTcArgs &a, int nsnap, cudaStream_t st)
     cudaError_t e = launch_part<5, 4>(a, nsnap, 3, st);
     if (e != cudaSuccess || !a.stress) return e;
     if ((e = launch_part<1, 2>(a, nsnap, 6, st)) != cudaSuccess) return e;
-    const size_t n = (size_t)a.nly * a.nplane * nsnap;
-    yrecover_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, nsnap);
+    if (a.ptrans) {
+        yrecover_t_kernel<<<dim3((a.nlx + 15) / 16, (a.nlz + 15) / 16, a.nly * nsnap), 256, 0, st>>>(a);
+    } else {
+        const size_t n = (size_t)a.nly * a.nplane * nsnap;
+        yrecover_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, nsnap);
+    }
     return cudaGetLastError();
 }
 
