@@ -4,10 +4,12 @@ Workload (default, the Re_tau ~ 550 precision form): DNS 512 x 257 x 384 in
 a 2 pi x 2 x pi box, tanh-stretched y, filtered with a Gaussian of constant
 width Delta = Lx / 64 (wall extension of Eq. 7) onto a 64 x 65 x 48 LES grid
 with split-BF16 tensor-core contractions; one step = ~bar(u_i), T_ij and the
-plane means of 4 seeded synthetic snapshots.  Inputs are 4 x 607 MB = 2.4 GB
+plane means of 8 seeded synthetic snapshots.  Inputs are 8 x 607 MB = 4.9 GB
 per step, far larger than the 129 MB L2, so no flush is needed between
-steps.  `--workload re180` selects the 192 x 129 x 192 -> 32 x 33 x 32,
-Delta = Lx / 32 channel (10 snapshots per step).
+steps.  `--workload re550_d32` is the same with Delta = Lx / 32;
+`--workload re180` selects the 192 x 129 x 192 -> 32 x 33 x 32,
+Delta = Lx / 32 channel (10 snapshots per step).  `--precision` picks the
+split form (bf16x3, the default, or tf32x2) or fp32 / fp64.
 
 Output: one JSON line (rank 0).  `value` is whole-job throughput in DNS
 points per second with inputs resident in HBM; `e2e` is the same metric
@@ -21,7 +23,10 @@ exact T_ij of snapshot 0, its error against the exact T_ij of snapshot 1 (a
 field of another seed), and tensor-core inference on 2^20 LES points with its
 roofline against the measured bf16 tensor peak.  `differential` times the
 paper's own filter (Sec. 3, a = 0.1) on one snapshot in FP64 against the FP64
-arithmetic bound.
+arithmetic bound.  `split_forms` runs the other split-precision form on the
+same snapshots, and both forms with the configuration's other filter width
+(Lx / 32 on the Lx / 64 workload), each with its x-z roofline and the T error
+of snapshot 0 against the oracle per component.
 
 Multi-GPU: one process per GPU; snapshots are independent, so every rank
 filters its own snapshots with no collective on the data path (weak
@@ -52,8 +57,8 @@ UNIT = "DNS points/s"
 WORKLOADS = {
     # name: (nx, ny, nz, Lx, Lz, nlx, nly, nlz, delta/Lx, snapshots per step)
     "re180": (192, 129, 192, 4 * math.pi, 2 * math.pi, 32, 33, 32, 1 / 32, 10),
-    "re550_d64": (512, 257, 384, 2 * math.pi, math.pi, 64, 65, 48, 1 / 64, 4),
-    "re550_d32": (512, 257, 384, 2 * math.pi, math.pi, 64, 65, 48, 1 / 32, 4),
+    "re550_d64": (512, 257, 384, 2 * math.pi, math.pi, 64, 65, 48, 1 / 64, 8),
+    "re550_d32": (512, 257, 384, 2 * math.pi, math.pi, 64, 65, 48, 1 / 32, 8),
 }
 PREC = {"fp32": 1, "fp64": 0, "bf16x3": 3, "tf32x2": 2}
 L2_BYTES = 129e6
@@ -62,7 +67,7 @@ L2_BYTES = 129e6
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="re550_d64", choices=sorted(WORKLOADS))
@@ -70,6 +75,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-closure", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--snapshots", type=int, default=0, help="snapshots per step (default: the workload's)")
     return ap.parse_args()
 
 
@@ -98,9 +105,10 @@ def whole_job_rate(world, units_per_rank_step, steps, ms):
     return world * units_per_rank_step * steps / (ms / 1e3)
 
 
-def make_workload(name, rank=0):
+def make_workload(name, rank=0, nsnap=0):
     from paper_1902_02508_gb300 import inputs as I
     nx, ny, nz, Lx, Lz, nlx, nly, nlz, dfrac, ns = WORKLOADS[name]
+    ns = nsnap or ns
     dns = I.dns_grid(nx, ny, nz, Lx, Lz)
     les = I.les_grid(dns, nlx, nly, nlz)
     delta = dfrac * Lx
@@ -110,8 +118,9 @@ def make_workload(name, rank=0):
     return dns, les, delta, snaps
 
 
-def workload_config(name, prec):
+def workload_config(name, prec, nsnap=0):
     nx, ny, nz, Lx, Lz, nlx, nly, nlz, dfrac, ns = WORKLOADS[name]
+    ns = nsnap or ns
     esz = 8 if prec == "fp64" else 4
     return {"workload": f"channel DNS {nx}x{ny}x{nz} -> LES {nlx}x{nly}x{nlz}, Delta=Lx/{round(1 / dfrac)}, "
                         f"Eq.7 wall extension, {ns} snapshots per step",
@@ -202,7 +211,7 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import oracle as O
-    dns, les, delta, snaps = make_workload(args.workload)
+    dns, les, delta, snaps = make_workload(args.workload, 0, args.snapshots)
     for s in range(args.warmup):
         O.subfilter_stress(dns, les, delta, snaps[s % len(snaps)])
     t0 = time.perf_counter()
@@ -213,7 +222,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args.workload, args.precision),
+            "data": "synthetic", "config": workload_config(args.workload, args.precision, args.snapshots),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
                              "sample": f"one whole snapshot per step ({dns.npts} DNS points)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -221,7 +230,7 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------- ours ----
-KERNEL_SOURCES = {"xz": ("fused_stage.cuh", "tc_kernels.cu", "eles_internal.h"),
+KERNEL_SOURCES = {"xz": ("fused_stage.cuh", "xz_ws.cuh", "xz_ws.cu", "eles_internal.h"),
                   "closure": ("closure_tc.cu", "fused_stage.cuh", "eles_internal.h")}
 
 
@@ -245,6 +254,46 @@ def traffic_from_profile(kernel_tag, points_per_launch, kind="xz"):
     except (OSError, ValueError, KeyError):
         pass
     return None
+
+
+def peak_of(peaks):
+    """Measured HBM copy bandwidth (GB/s) of the GB300s, else the fallback."""
+    if "hbm_gbs" in peaks:
+        return peaks["hbm_gbs"], "measured"
+    return 6800.0, "fallback"
+
+
+def form_measure(eles, torch, workload, pname, dns, les, snaps, u, ub, tau, pm, stream, timed, steps, peak, rank):
+    """One split-precision form on the workload's snapshots (same fields; the
+    filter width of `workload`): throughput, the x-z kernel against the HBM
+    roofline, and T of snapshot 0 against the oracle per component."""
+    nx, ny, nz, Lx, Lz, nlx, nly, nlz, dfrac, _ = WORKLOADS[workload]
+    delta = dfrac * Lx
+    plan = eles.filter_setup(dns, les, delta, precision=PREC[pname])
+    ns = u.shape[0]
+    eles.plan_reserve(plan, ns)
+    k = max(10, steps // 4)
+    ms = timed(lambda: eles.subfilter_stress_batch(plan, u, ub, tau, pm, stream=stream), k, 3)
+    eles.profile_enable(plan, True)
+    timed(lambda: eles.subfilter_stress_batch(plan, u, ub, tau, pm, stream=stream), max(5, k // 2), 1)
+    phase_ms, calls = eles.profile_read(plan)
+    eles.profile_enable(plan, False)
+    xz_ms = phase_ms[0] / max(calls, 1)
+    alg = 12 * dns.npts * ns
+    out = {"workload": workload_config(workload, pname)["workload"], "dtype": pname, "delta": delta,
+           "value": dns.npts * ns * k / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k,
+           "x_variant": eles.plan_info(plan, 10), "output_phases": eles.plan_info(plan, 15),
+           "roofline": {"bound": "hbm", "achieved": alg / (xz_ms / 1e3) / 1e9, "peak": peak[0], "unit": "GB/s",
+                        "frac": alg / (xz_ms / 1e3) / 1e9 / peak[0], "peak_source": peak[1],
+                        "phase_ms_per_step": {"xz": xz_ms, "y_recovery": phase_ms[2] / max(calls, 1)}}}
+    if rank == 0:
+        from oracle import oracle as O
+        _, tau_ref = O.subfilter_stress(dns, les, delta, snaps[0])
+        got = tau[0].double().cpu().numpy()
+        out["accuracy"] = {"tau_max_abs_err_utau2": [float(x) for x in np.abs(got - tau_ref).max(axis=(1, 2, 3))],
+                           "tau_order": ["11", "12", "13", "22", "23", "33"]}
+    plan.close()
+    return out
 
 
 def differential_measure(eles, torch, dns, les, u0, stream, timed, peaks):
@@ -408,13 +457,15 @@ def main():
     entry.build()
     from paper_1902_02508_gb300 import eles
 
-    dns, les, delta, snaps = make_workload(args.workload, rank)
+    dns, les, delta, snaps = make_workload(args.workload, rank, args.snapshots)
     ns = len(snaps)
     prec = PREC[args.precision]
     plan = eles.filter_setup(dns, les, delta, precision=prec)
     dt = plan.dtype
     stream = torch.cuda.Stream(dev)
-    u = torch.stack([torch.from_numpy(s) for s in snaps]).to(dev, dt)
+    u = torch.empty((ns, 3, dns.ny, dns.nz, dns.nx), device=dev, dtype=dt)
+    for k, sk in enumerate(snaps):
+        u[k] = torch.from_numpy(sk).to(dev, dt)
     ub = torch.empty((ns, 3, les.ny, les.nz, les.nx), device=dev, dtype=dt)
     tau = torch.empty((ns, 6, les.ny, les.nz, les.nx), device=dev, dtype=dt)
     pm = torch.empty((ns, 3, dns.ny), device=dev, dtype=torch.float64)
@@ -447,18 +498,21 @@ def main():
             step(plan, u, ub, tau, pm)
     torch.cuda.synchronize()
     assert eles.check_device_error(plan, stream) == 0
-    eles.profile_enable(plan, True)
+    # the headline pass (no phase events), then a pass with phase events for
+    # the per-kernel timing of the roofline
     with ClockSampler(local) as clk:
         ms = timed(lambda: step(plan, u, ub, tau, pm), args.steps, 0)
+    eles.profile_enable(plan, True)
+    timed(lambda: step(plan, u, ub, tau, pm), max(10, args.steps // 4), 1)
     phase_ms, calls = eles.profile_read(plan)
     eles.profile_enable(plan, False)
-    # a second pass without the phase events, for the headline number
-    ms = min(ms, timed(lambda: step(plan, u, ub, tau, pm), args.steps, 1))
     pts_step = ns * dns.npts
     value = whole_job_rate(world, pts_step, args.steps, ms)
 
     # --- end to end: pinned host in, results back to pinned host
-    hu = torch.stack([torch.from_numpy(s) for s in snaps]).to(dt).pin_memory()
+    hu = torch.empty(u.shape, dtype=dt).pin_memory()
+    for k, sk in enumerate(snaps):
+        hu[k] = torch.from_numpy(sk).to(dt)
     hb = torch.empty(ub.shape, dtype=dt).pin_memory()
     ht = torch.empty(tau.shape, dtype=dt).pin_memory()
 
@@ -537,9 +591,20 @@ def main():
             v, cores, sample = oracle_time(dns, les, delta, snaps)
             cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
+    # --- the other split-precision form on this workload, and both forms with
+    # the wider filter of the configuration (Delta = Lx/32 on the Lx/64 workload);
+    # after the accuracy check, since they reuse the output buffers
+    forms = None
+    if not args.no_forms and prec in (2, 3) and args.workload in ("re550_d64", "re550_d32"):
+        forms = {}
+        other = {"re550_d64": "re550_d32", "re550_d32": "re550_d64"}[args.workload]
+        cases = [(args.workload, "tf32x2" if prec == 3 else "bf16x3"), (other, "bf16x3"), (other, "tf32x2")]
+        for wl, pname in cases:
+            forms[f"{wl}_{pname}"] = form_measure(eles, torch, wl, pname, dns, les, snaps, u, ub, tau, pm,
+                                                  stream, timed, args.steps, peak_of(from_json), rank)
+
     # --- roofline of the dominant phase (x-contraction: it alone reads the input)
-    peak = from_json.get("hbm_gbs", 6800.0)
-    peak_src = "measured" if "hbm_gbs" in from_json else "fallback"
+    peak, peak_src = peak_of(from_json)
     xz_ms = phase_ms[0] / max(calls, 1)
     alg_bytes = (12 if prec != 0 else 24) * dns.npts * ns      # one launch covers the whole batch
     achieved = alg_bytes / (xz_ms / 1e3) / 1e9
@@ -549,23 +614,26 @@ def main():
             else "x and z contractions (unfused)",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_source": peak_src,
-            "traffic": traffic_from_profile(f"xz_fused_{args.workload}_{args.precision}", dns.npts * ns),
+            "traffic": traffic_from_profile(f"xz_ws_{args.workload}_{args.precision}", dns.npts * ns),
             "algorithmic_bytes_per_launch": alg_bytes,
             "phase_ms_per_step": {"xz": xz_ms, "y_recovery": phase_ms[2] / max(calls, 1)},
             "path_frac": (value / world) * (alg_bytes / (dns.npts * ns)) / 1e9 / peak}
-    # x-z: one fused launch (or 5 per snapshot + 2 unfused); y: profile, then
+    # x-z: the reference profile and the warp-specialised kernel (2 launches),
+    # one fused launch, or 5 per snapshot + 2 unfused; y: profile, then
     # fragments + velocities + products + recovery (tensor cores) or 2 passes
     ytc = eles.plan_info(plan, 13) == 1
-    per_call_launches = (1 if fused else 2 + 5 * ns) + 1 + (4 if ytc else 2)
+    xv = eles.plan_info(plan, 10)
+    per_call_launches = (2 if xv == 3 else 1 if fused else 2 + 5 * ns) + 1 + (4 if ytc else 2)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp32": "f32", "fp64": "f64", "bf16x3": "bf16x3", "tf32x2": "tf32x2"}[args.precision],
                 "data": "synthetic (seeded solenoidal channel fields, Reichardt mean profile)",
-                "config": workload_config(args.workload, args.precision),
+                "config": workload_config(args.workload, args.precision, args.snapshots),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64,
-                "accuracy": err, "closure": closure, "differential": differential, "clocks": clk.summary(),
+                "accuracy": err, "split_forms": forms, "closure": closure, "differential": differential,
+                "clocks": clk.summary(),
                 "gpu_launches": per_call_launches * args.steps,
                 "x_variant": eles.plan_info(plan, 10)}
         print(json.dumps(line), flush=True)
