@@ -468,6 +468,28 @@ int ef_closure_train(ef_closure *closure, const float *feats, const float *tau, 
 int ef_closure_infer(ef_closure *closure, const float *feats, float *tau_out, long n, const float *exact_tau,
                      long *n_fallback, void *stream);
 
+/*
+ * ef_closure_infer_exact -- inference with the exact filter as the fallback.
+ * As ef_closure_infer, but where a standardised input exceeds the guard the
+ * output is the exact subfilter stress of Eq. 6 at that point, evaluated from
+ * the DNS snapshot through the plan's operators (Eq. 2 with the wall
+ * extension of Eq. 7 or Eq. 9 folded in, linear interpolation to the LES
+ * node) by direct summation in FP64; the exact stress is computed only at
+ * the guarded points.
+ *  plan  a Gaussian-kernel plan (EF_KERNEL_GAUSSIAN or _HAT) of the LES grid
+ *        the features were taken on: n must be nly nlz nlx and point
+ *        p = (J nlz + Z) nlx + X (the order of ef_closure_features)
+ *  u     device [3][ny][nz][nx], the plan's element type (double for
+ *        EF_PREC_FP64 plans, float otherwise): the snapshot of the features
+ * *n_fallback (if not NULL) receives the number of guarded points
+ * (synchronises).  The plan is only read; calls on one closure must not
+ * overlap on the GPU.  Errors: EF_ERR_ARG, EF_ERR_SHAPE (n),
+ * EF_ERR_UNSUPPORTED (a differential-filter plan), EF_ERR_CUDA,
+ * EF_ERR_TIMEOUT (as ef_closure_infer).
+ */
+int ef_closure_infer_exact(ef_closure *closure, const float *feats, float *tau_out, long n, ef_plan *plan,
+                           const void *u, long *n_fallback, void *stream);
+
 /* Read (and clear) the closure's device error word; synchronises `stream`.
  * Returns EF_OK or the recorded ef_status (EF_ERR_TIMEOUT). */
 int ef_closure_check_device_error(ef_closure *closure, void *stream);

@@ -601,6 +601,49 @@ int ef_closure_infer(ef_closure *c, const float *feats, float *tau_out, long n, 
     return EF_OK;
 }
 
+int ef_closure_infer_exact(ef_closure *c, const float *feats, float *tau_out, long n, ef_plan *plan, const void *u,
+                           long *n_fallback, void *stream)
+{
+    int rc = check_closure(c, "ef_closure_infer_exact");
+    if (rc) return rc;
+    if (!plan || !u) { set_error("ef_closure_infer_exact: a plan and its DNS snapshot are required"); return EF_ERR_ARG; }
+    if (plan->diff) { set_error("ef_closure_infer_exact: the fallback needs a Gaussian-kernel plan"); return EF_ERR_UNSUPPORTED; }
+    if (n != (long)plan->nlx * plan->nly * plan->nlz) {
+        set_error("ef_closure_infer_exact: n (%ld) must be the plan's LES point count (%ld)", n,
+                  (long)plan->nlx * plan->nly * plan->nlz);
+        return EF_ERR_SHAPE;
+    }
+    if ((rc = ef_closure_infer(c, feats, tau_out, n, nullptr, nullptr, stream))) return rc;
+    ExactFallbackArgs a;
+    memset(&a, 0, sizeof a);
+    a.feats = feats; a.n = n; a.guard = c->cfg.guard_sigma;
+    a.image = static_cast<const unsigned char *>(c->image);
+    if (plan->prec == EF_PREC_FP64) a.u64 = static_cast<const double *>(u);
+    else a.u32 = static_cast<const float *>(u);
+    a.np = (size_t)plan->nx * plan->ny * plan->nz;
+    a.nx = plan->nx; a.ny = plan->ny; a.nz = plan->nz; a.nlx = plan->nlx; a.nly = plan->nly; a.nlz = plan->nlz;
+    a.xstart = plan->bx.d_start; a.xw = plan->bx.d_w64; a.Tx = plan->bx.T;
+    a.zstart = plan->bz.d_start; a.zw = plan->bz.d_w64; a.Tz = plan->bz.T;
+    a.ystart = plan->d_ystart; a.ycount = plan->d_ycount; a.yw[0] = plan->d_yw64[0]; a.yw[1] = plan->d_yw64[1];
+    for (int k = 0; k < 3; k++) a.par[k] = plan->par[k];
+    a.tau = tau_out;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((rc = closure_exact_fallback(a, s))) return rc;
+    if (n_fallback) {
+        int w[2] = {0, 0};
+        cudaError_t e = cudaMemcpyAsync(w, c->nfall, sizeof w, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "fallback count");
+        if (w[1]) {
+            cudaMemsetAsync(c->nfall + 1, 0, sizeof(int), s);
+            set_error("ef_closure_infer_exact: device error %d (a wait ran out)", w[1]);
+            return w[1];
+        }
+        *n_fallback = w[0];
+    }
+    return EF_OK;
+}
+
 int ef_closure_check_device_error(ef_closure *c, void *stream)
 {
     int rc = check_closure(c, "ef_closure_check_device_error");

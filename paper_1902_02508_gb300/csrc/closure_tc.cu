@@ -488,9 +488,108 @@ closure_mlp_tc_kernel(const uint4 *__restrict__ img, const float *__restrict__ f
     }
 }
 
+// Exact stress at the guarded points (the closure's fallback through a filter
+// plan).  Blocks stride over groups of 256 points; each thread repeats the
+// inference kernel's guard test (the same FP32 statistics of the packed image,
+// the same arithmetic), the block lists its group's guarded points and then
+// evaluates T at each of them by direct summation of the plan's banded
+// operators over the DNS snapshot in FP64 (Eq. 6):
+//   ubar_a = sum_{j,z,x} Ay^{p_a}[J][j] Az[Z][z] Ax[X][x] u_a(j, z, x),
+//   bar(u_a u_b) likewise with the parity p_a p_b,  T_ab = bar(u_a u_b) - ubar_a ubar_b,
+// at the LES node of point p = (J nlz + Z) nlx + X, overwriting tau there.
+__global__ void __launch_bounds__(256) exact_fallback_kernel(const __grid_constant__ ExactFallbackArgs a)
+{
+    __shared__ int list[256];
+    __shared__ int nlist;
+    __shared__ double red[8][9];
+    const float *st = reinterpret_cast<const float *>(a.image + kImgStats);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nrow_z = a.Tz;
+    for (long base = (long)blockIdx.x * 256; base < a.n; base += (long)gridDim.x * 256) {
+        if (tid == 0) nlist = 0;
+        __syncthreads();
+        const long p = base + tid;
+        if (p < a.n) {
+            bool out = false;
+#pragma unroll
+            for (int k = 0; k < kIn; k++) out |= fabsf((__ldg(a.feats + p * kIn + k) - st[k]) * st[16 + k]) > a.guard;
+            if (out) list[atomicAdd(&nlist, 1)] = tid;
+        }
+        __syncthreads();
+        const int nl = nlist;
+        for (int i = 0; i < nl; i++) {
+            const long q = base + list[i];
+            const int X = (int)(q % a.nlx), Z = (int)((q / a.nlx) % a.nlz), J = (int)(q / ((long)a.nlx * a.nlz));
+            const int j0 = a.ystart[J], nj = a.ycount[J];
+            double acc[9];
+#pragma unroll
+            for (int f = 0; f < 9; f++) acc[f] = 0.0;
+            for (int r = tid; r < nj * nrow_z; r += 256) {
+                const int j = j0 + r / nrow_z, kz = r % nrow_z;
+                int z = a.zstart[Z] + kz;
+                z = ((z % a.nz) + a.nz) % a.nz;
+                const double wz = a.zw[(size_t)Z * a.Tz + kz];
+                if (wz == 0.0) continue;
+                double s[9];
+#pragma unroll
+                for (int f = 0; f < 9; f++) s[f] = 0.0;
+                const size_t row = ((size_t)j * a.nz + z) * a.nx;
+                for (int kx = 0; kx < a.Tx; kx++) {
+                    int x = a.xstart[X] + kx;
+                    x = ((x % a.nx) + a.nx) % a.nx;
+                    const double wx = a.xw[(size_t)X * a.Tx + kx];
+                    double v[3];
+#pragma unroll
+                    for (int c = 0; c < 3; c++)
+                        v[c] = a.u64 ? a.u64[(size_t)c * a.np + row + x] : (double)a.u32[(size_t)c * a.np + row + x];
+                    s[0] += wx * v[0]; s[1] += wx * v[1]; s[2] += wx * v[2];
+                    s[3] += wx * v[0] * v[0]; s[4] += wx * v[0] * v[1]; s[5] += wx * v[0] * v[2];
+                    s[6] += wx * v[1] * v[1]; s[7] += wx * v[1] * v[2]; s[8] += wx * v[2] * v[2];
+                }
+                const double we = wz * a.yw[0][(size_t)J * a.ny + j], wo = wz * a.yw[1][(size_t)J * a.ny + j];
+                const int pa[9] = {a.par[0], a.par[1], a.par[2], 1, a.par[0] * a.par[1], a.par[0] * a.par[2], 1,
+                                   a.par[1] * a.par[2], 1};
+#pragma unroll
+                for (int f = 0; f < 9; f++) acc[f] += (pa[f] > 0 ? we : wo) * s[f];
+            }
+#pragma unroll
+            for (int f = 0; f < 9; f++) {
+                double v = acc[f];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) red[warp][f] = v;
+            }
+            __syncthreads();
+            if (tid < 6) {
+                const int PI[6] = {0, 0, 0, 1, 1, 2}, PJ[6] = {0, 1, 2, 1, 2, 2};
+                double ub[3] = {0.0, 0.0, 0.0}, uu = 0.0;
+                for (int w = 0; w < 8; w++) {
+                    for (int c = 0; c < 3; c++) ub[c] += red[w][c];
+                    uu += red[w][3 + tid];
+                }
+                a.tau[(size_t)tid * a.n + q] = (float)(uu - ub[PI[tid]] * ub[PJ[tid]]);
+            }
+            __syncthreads();
+        }
+        __syncthreads();   // every thread has read nlist before the next group resets it
+    }
+}
+
 }  // namespace
 
 size_t closure_tc_image_bytes() { return kImgBytes; }
+
+int closure_exact_fallback(const ExactFallbackArgs &a, cudaStream_t s)
+{
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "closure_exact_fallback");
+    const long groups = (a.n + 255) / 256;
+    const int grid = (int)(groups < 4L * nsm ? groups : 4L * nsm);
+    exact_fallback_kernel<<<grid, 256, 0, s>>>(a);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? EF_OK : cuda_fail(e, "exact_fallback_kernel");
+}
 
 int closure_infer_tc(const float *wq, const long *off_w, const long *off_b, const double *stats, void *image,
                      const float *feats, long n, float guard, const float *exact, float *tau, int *nfall, int *err,

@@ -253,6 +253,25 @@ int diff_run(ef_plan *p, int nsnap, const void *u, void *ubar, void *tau, double
              cudaStream_t s);
 
 size_t closure_tc_image_bytes();
+// The exact-stress fallback of the closure through a filter plan (closure_tc.cu).
+struct ExactFallbackArgs {
+    const float *feats;          // [n][10]
+    long n;
+    float guard;
+    const unsigned char *image;  // the packed inference image (its statistics)
+    const float *u32;            // DNS snapshot [3][ny][nz][nx] (FP32 plans) ...
+    const double *u64;           // ... or FP64 (FP64 plans); the other is NULL
+    size_t np;                   // nx ny nz
+    int nx, ny, nz, nlx, nly, nlz;
+    const int *xstart, *zstart;  // the banded x and z operators [nl][T]
+    const double *xw, *zw;
+    int Tx, Tz;
+    const int *ystart, *ycount;  // the y operators, dense [nly][ny] per parity (even, odd)
+    const double *yw[2];
+    int par[3];                  // wall parities of u1, u2, u3
+    float *tau;                  // [6][n]: overwritten at the guarded points
+};
+int closure_exact_fallback(const ExactFallbackArgs &a, cudaStream_t s);
 int closure_infer_tc(const float *wq, const long *off_w, const long *off_b, const double *stats, void *image,
                      const float *feats, long n, float guard, const float *exact, float *tau, int *nfall, int *err,
                      cudaStream_t s);

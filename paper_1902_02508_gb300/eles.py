@@ -35,6 +35,7 @@ EXPORTED = ("ef_filter_setup", "ef_plan_destroy", "ef_filter_fields", "ef_subfil
             "ef_check_device_error", "ef_plan_info", "ef_plan_weights", "ef_profile_enable",
             "ef_profile_read", "ef_last_error", "ef_version", "ef_closure_create", "ef_closure_destroy",
             "ef_closure_features", "ef_closure_fit_norm", "ef_closure_train", "ef_closure_infer",
+            "ef_closure_infer_exact",
             "ef_closure_gradients", "ef_closure_param_count", "ef_closure_get_params", "ef_closure_set_params",
             "ef_closure_save", "ef_closure_load", "ef_batch_create", "ef_batch_run", "ef_batch_destroy",
             "ef_batch_captures", "ef_plan_autotune", "ef_plan_set_variant", "ef_closure_features_static", "ef_io_create",
@@ -111,6 +112,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             lib.ef_closure_train.restype = i
             lib.ef_closure_infer.argtypes = [vp, vp, vp, L, vp, ctypes.POINTER(L), vp]
             lib.ef_closure_infer.restype = i
+            lib.ef_closure_infer_exact.argtypes = [vp, vp, vp, L, vp, vp, ctypes.POINTER(L), vp]
+            lib.ef_closure_infer_exact.restype = i
             lib.ef_selftest_wait.argtypes = [vp, ctypes.c_longlong, i, vp]
             lib.ef_selftest_wait.restype = i
             lib.ef_differential_unfilter.argtypes = [ctypes.POINTER(_Grid), d, i, vp, vp, vp]
@@ -375,6 +378,21 @@ def closure_infer(cl: Closure, feats, tau_out, exact_tau=None, stream=None, coun
                                    _field(tau_out, (6, n), torch.float32, "tau_out"), n,
                                    _field(exact_tau, (6, n), torch.float32, "exact_tau"),
                                    ctypes.byref(nf) if count else None, _stream(stream)))
+    return nf.value if count else None
+
+
+def closure_infer_exact(cl: Closure, feats, tau_out, plan: Plan, u, stream=None, count: bool = True):
+    """Tensor-core inference with the exact stress of `plan` on the DNS
+    snapshot u [3][ny][nz][nx] at the guarded points; returns their number
+    (count=True, synchronises) or None."""
+    import torch
+    n = _n_feats(feats)
+    d = plan.dns
+    nf = ctypes.c_long()
+    _check(load().ef_closure_infer_exact(cl.handle, _field(feats, (n, 10), torch.float32, "feats"),
+                                         _field(tau_out, (6, n), torch.float32, "tau_out"), n, plan.handle,
+                                         _field(u, (3, d.ny, d.nz, d.nx), plan.dtype, "u"),
+                                         ctypes.byref(nf) if count else None, _stream(stream)))
     return nf.value if count else None
 
 

@@ -188,3 +188,31 @@ def test_adam_steps_match_reference():
     # the steps moved the weights by about lr each (the comparison is not vacuous)
     moved = np.abs(eles.closure_get_params(cl)[0] - p0)
     assert np.median(moved) > 0.5 * lr
+
+
+def test_exact_fallback_through_a_plan():
+    """ef_closure_infer_exact: at the guarded points the output is the exact
+    stress, computed from the DNS snapshot through the plan, and equals the
+    oracle's direct 3-D summation at that LES point within 1e-4 u_tau^2; at
+    the other points it is the network's output, bit for bit."""
+    dns, les, delta, ubs, taus, feats = dataset()
+    ftr, ttr = _concat(feats[:2], 0), _concat(taus[:2], 1)
+    cl = eles.closure_create(batch=4096, lr=2e-3, seed=3, guard_sigma=3.0)
+    eles.closure_train(cl, ftr, ttr, epochs=3)
+    plan = eles.filter_setup(dns, les, delta, precision=eles.PREC_FP32)
+    u = torch.from_numpy(I.channel_velocity(dns, 2004)).to("cuda", torch.float32)   # snapshot 4 of the dataset
+    n = feats[4].shape[0]
+    plain = torch.empty((6, n), device="cuda")
+    nplain = eles.closure_infer(cl, feats[4], plain)
+    out = torch.full((6, n), float("nan"), device="cuda")
+    nfall = eles.closure_infer_exact(cl, feats[4], out, plan, u)
+    assert nfall == nplain and 0 < nfall < n // 2
+    differs = (out != plain).any(dim=0).cpu().numpy()
+    idx = np.nonzero(differs)[0]
+    assert len(idx) == nfall                       # exactly the guarded points changed
+    sample = idx[np.linspace(0, len(idx) - 1, min(24, len(idx))).astype(int)]
+    X, Z, J = sample % les.nx, (sample // les.nx) % les.nz, sample // (les.nx * les.nz)
+    pts = np.stack([X, J, Z], axis=1)
+    _, tau3 = O.direct3d_points(dns, les, delta, I.channel_velocity(dns, 2004), pts)
+    got = out[:, sample].double().cpu().numpy().T
+    assert np.abs(got - tau3).max() <= 1e-4
