@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="re550_d64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="re550_d64", choices=sorted(WORKLOADS) + ["batch64"])
     ap.add_argument("--precision", default="bf16x3", choices=sorted(PREC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -211,6 +211,33 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import oracle as O
+    if args.workload == "batch64":
+        # one step = one snapshot of each of the batch's plans in turn (a
+        # bounded sample of the 64-snapshot batch)
+        from paper_1902_02508_gb300 import inputs as I
+        combos, base = batch64_setup(0)
+        jobs = []
+        for shape, w, _ in combos:
+            dns, les = I.batch_grids(shape)
+            jobs.append((dns, les, dns.Lx / w, base[shape][0]))
+        for s in range(args.warmup):
+            O.subfilter_stress(*jobs[s % len(jobs)])
+        t0, npts = time.perf_counter(), 0
+        for s in range(args.steps):
+            O.subfilter_stress(*jobs[s % len(jobs)])
+            npts += jobs[s % len(jobs)][0].npts
+        dt = time.perf_counter() - t0
+        value = npts / dt
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": "batched (64 snapshots, 9 plans): one snapshot of "
+                                                            "each plan in turn per step"},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                                 "sample": f"{args.steps} whole snapshots, one per plan in turn"},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     dns, les, delta, snaps = make_workload(args.workload, 0, args.snapshots)
     for s in range(args.warmup):
         O.subfilter_stress(dns, les, delta, snaps[s % len(snaps)])
@@ -437,10 +464,164 @@ def closure_measure(eles, torch, les, ub, tau, stream, timed, exact_ms_per_les_p
             "gpu_launches_per_call": 2}
 
 
+def batch64_setup(rank=0):
+    """The batched configuration: 64 seeded draws of (grid, width); one plan
+    per drawn (grid, width), its snapshots the shifts of two seeded fields of
+    that grid.  Returns [(shape, width, count)] and the base fields."""
+    from collections import Counter
+    from paper_1902_02508_gb300 import inputs as I
+    combos = sorted(Counter(I.batch_draws(64, 7)).items())
+    base = {}
+    for (shape, w), count in combos:
+        if shape not in base:
+            dns, _ = I.batch_grids(shape)
+            base[shape] = [I.channel_velocity(dns, 1000 + 1000 * rank + 10 * shape[0] + k) for k in range(2)]
+    return [(shape, w, count) for (shape, w), count in combos], base
+
+
+def run_batch64(args):
+    """bench.py --workload batch64: the 64 snapshots (three grids, three
+    filter widths, nine plans) through one batch (one CUDA graph: a
+    persistent x-z launch per kernel class, then the plans' y stages)."""
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_1902_02508_gb300 import eles
+    from paper_1902_02508_gb300 import inputs as I
+    prec = PREC[args.precision]
+    combos, base = batch64_setup(rank)
+    stream = torch.cuda.Stream(dev)
+    plans, us, ubs, taus, info = [], [], [], [], []
+    pts = 0
+    for shape, w, count in combos:
+        dns, les = I.batch_grids(shape)
+        delta = dns.Lx / w
+        plan = eles.filter_setup(dns, les, delta, precision=prec)
+        b0 = [torch.from_numpy(f).to(dev, plan.dtype) for f in base[shape]]
+        u = torch.stack([torch.roll(b0[k % 2], shifts=(5 * k, 7 * k), dims=(2, 3)) for k in range(count)])
+        plans.append(plan)
+        us.append(u)
+        ubs.append(torch.empty((count, 3, les.ny, les.nz, les.nx), device=dev, dtype=plan.dtype))
+        taus.append(torch.empty((count, 6, les.ny, les.nz, les.nx), device=dev, dtype=plan.dtype))
+        info.append({"dns_grid": list(shape), "les_grid": [les.nx, les.ny, les.nz], "delta": f"Lx/{w}",
+                     "snapshots": count, "x_variant": eles.plan_info(plan, 10),
+                     "output_phases": eles.plan_info(plan, 15)})
+        pts += count * dns.npts
+    batch = eles.batch_create(plans, [c for _, _, c in combos])
+
+    def step():
+        eles.batch_run(batch, us, ubs, taus, stream=stream)
+
+    def timed(fn, steps, warmup):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                fn()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1), dev, world)
+
+    timed(step, 0, args.warmup)
+    for p in plans:
+        assert eles.check_device_error(p, stream) == 0
+    with ClockSampler(local) as clk:
+        ms = timed(step, args.steps, 0)
+    value = whole_job_rate(world, pts, args.steps, ms)
+    captures = eles.batch_captures(batch)
+    peak, peak_src = peak_of(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+                             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {})
+    ach = 12 * pts / (ms / args.steps / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": "the whole batch step (x-z launches per kernel class and every plan's y "
+                                      "stage, one CUDA graph): 12 B per DNS point read once",
+            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_source": peak_src,
+            "traffic": None, "algorithmic_bytes_per_launch": 12 * pts}
+
+    # end to end: every plan through the host-buffer entry point
+    hosts = []
+    for p, u, ub, tau in zip(plans, us, ubs, taus):
+        hosts.append((eles.io_create(p, 1), u.cpu().pin_memory(), torch.empty(ub.shape, dtype=ub.dtype).pin_memory(),
+                      torch.empty(tau.shape, dtype=tau.dtype).pin_memory()))
+
+    def e2e_step():
+        for io, hu, hb, ht in hosts:
+            eles.subfilter_stress_host(io, hu, hb, ht, stream=stream)
+
+    k_e2e = max(3, args.steps // 4)
+    ms_e2e = timed(e2e_step, k_e2e, 1)
+    e2e = {"value": world * pts * k_e2e / (ms_e2e / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": sum(h[1].numel() * h[1].element_size() for h in hosts),
+           "d2h_bytes_per_step": sum(h[2].numel() * h[2].element_size() + h[3].numel() * h[3].element_size()
+                                     for h in hosts),
+           "api": "ef_subfilter_stress_host per plan (pinned host buffers, 1-snapshot groups)"}
+    for h in hosts:
+        h[0].close()
+    del hosts
+
+    # accuracy: snapshot 0 of every plan against the oracle; the CPU baseline
+    err = cpu = None
+    step()
+    torch.cuda.synchronize()
+    if rank == 0:
+        from oracle import oracle as O
+        worst = np.zeros(6)
+        for (shape, w, count), tau in zip(combos, taus):
+            dns, les = I.batch_grids(shape)
+            _, tau_ref = O.subfilter_stress(dns, les, dns.Lx / w, base[shape][0])
+            worst = np.maximum(worst, np.abs(tau[0].double().cpu().numpy() - tau_ref).max(axis=(1, 2, 3)))
+        err = {"tau_max_abs_err_utau2": [float(x) for x in worst], "tau_order": ["11", "12", "13", "22", "23", "33"],
+               "over": "snapshot 0 of each of the nine plans"}
+        if not args.no_cpu_baseline and world == 1:
+            done, pdone, t0 = 0, 0, time.perf_counter()
+            while time.perf_counter() - t0 < 10.0:
+                shape, w, _ = combos[done % len(combos)]
+                dns, les = I.batch_grids(shape)
+                O.subfilter_stress(dns, les, dns.Lx / w, base[shape][0])
+                done += 1
+                pdone += dns.npts
+            dt = time.perf_counter() - t0
+            cpu = {"value": pdone / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                   "sample": f"{done} whole snapshots of the batch's plans in turn, {dt:.1f} s"}
+    launches = sum(6 for _ in plans) + len({(eles.plan_info(p, 2), eles.plan_info(p, 15)) for p in plans})
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+                "data": "synthetic (seeded solenoidal channel fields, Reichardt mean profile)",
+                "config": {"workload": "batched: 64 snapshots drawn (seed 7) over DNS grids 128x97x128, 192x129x192, "
+                                       "256x193x256 (4 pi x 2 x 2 pi, LES = DNS / 4) and widths Lx/16, Lx/32, Lx/48; "
+                                       "one batch (one CUDA graph) per step",
+                           "dns_points_per_step": pts, "plans": info, "graph_captures": captures,
+                           "l2": f"inputs {12 * pts / 1e6:.0f} MB per step > 129 MB L2, no flush"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "accuracy": err, "clocks": clk.summary(),
+                "gpu_launches": launches * args.steps}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batch64":
+        run_batch64(args)
         return
     import torch
     import torch.distributed as dist

@@ -225,6 +225,20 @@ int ef_check_device_error(ef_plan *plan, void *stream);
  */
 int ef_selftest_wait(ef_plan *plan, long long limit_cycles, int complete, void *stream);
 
+/*
+ * ef_plan_set_wait_limit -- bound, in SM clocks, of every wait inside the
+ * warp-specialised x-z kernel (its TMA stages and the hand-over between its
+ * roles); 0 restores the default (about 2 s at the SM clock).  A wait that
+ * runs out records EF_ERR_TIMEOUT in the plan's error word (read by
+ * ef_check_device_error) and the kernel's roles stop at once, after the
+ * bulk copies already issued have landed; the outputs of that call are then
+ * undefined, and the plan and the context stay usable.  For tests of the
+ * timeout path (a limit of 1 makes the first wait that is not already
+ * complete run out).  Batch graphs holding the plan re-capture.
+ * Errors: EF_ERR_ARG.
+ */
+int ef_plan_set_wait_limit(ef_plan *plan, long long cycles);
+
 /* Plan facts for callers and tests.  ints: 0 nx, 1 ny, 2 nz, 3 nlx, 4 nly,
  * 5 nlz, 6 precision, 7 x-taps per row, 8 z-taps per row, 9 max y-taps per
  * row, 10 x-contraction variant (0 generic, 1 banded ring on CUDA cores,

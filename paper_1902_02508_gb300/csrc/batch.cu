@@ -32,11 +32,33 @@ void drop_graph(ef_batch *b)
     b->gens.clear();
 }
 
+// The items' x-z stages: plans on the warp-specialised tensor-core kernel go
+// through one persistent launch per kernel class (all their snapshots, grids
+// and filter widths in one work list); the others run their own path.  Then
+// every such plan's y stage.
 int run_items(ef_batch *b, const void *const *u, void *const *ubar, void *const *tau, cudaStream_t s)
 {
+    std::vector<ef_plan *> wp;
+    std::vector<int> wn;
+    std::vector<const float *> wu;
+    std::vector<size_t> wi;
     for (size_t i = 0; i < b->plans.size(); i++) {
-        int rc = run_filter(b->plans[i], b->nsnap[i], u[i], ubar[i], tau[i], nullptr, true, s, nullptr);
+        ef_plan *p = b->plans[i];
+        if (p->fused && p->x_variant == 3 && p->ws.ok && b->nsnap[i] <= p->reserve) {
+            wp.push_back(p);
+            wn.push_back(b->nsnap[i]);
+            wu.push_back(static_cast<const float *>(u[i]));
+            wi.push_back(i);
+            continue;
+        }
+        int rc = run_filter(p, b->nsnap[i], u[i], ubar[i], tau[i], nullptr, true, s, nullptr);
         if (rc) return rc;
+    }
+    if (!wp.empty()) {
+        int rc = ws_run_batch(wp.data(), wn.data(), wu.data(), (int)wp.size(), 9, s);
+        if (rc) return rc;
+        for (size_t k = 0; k < wp.size(); k++)
+            if ((rc = run_y_stage(wp[k], wn[k], ubar[wi[k]], tau[wi[k]], true, s))) return rc;
     }
     return EF_OK;
 }

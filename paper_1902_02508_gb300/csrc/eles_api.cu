@@ -313,6 +313,14 @@ static int hot_args(ef_plan *p, const void *u, const void *ubar, const char *who
     return EF_OK;
 }
 
+int ef_plan_set_wait_limit(ef_plan *p, long long cycles)
+{
+    if (!p || cycles < 0) { set_error("ef_plan_set_wait_limit: NULL plan or negative limit"); return EF_ERR_ARG; }
+    p->wait_limit = cycles;
+    p->gen++;   // batch graphs hold the limit in their launch arguments
+    return EF_OK;
+}
+
 int ef_plan_reserve(ef_plan *p, int max_snapshots)
 {
     if (!p) { set_error("ef_plan_reserve: NULL plan"); return EF_ERR_ARG; }

@@ -12,7 +12,7 @@
 
 namespace eles {
 
-constexpr int kMaxRing = 24;      // largest ring (taps / stride + 1) of the banded ring kernels
+constexpr int kMaxRing = 64;      // largest ring (taps / stride + 1) of the strided-convolution tables
 constexpr int kMaxStride = 8;     // largest DNS/LES stride of the banded ring kernels
 
 // A banded operator A[nl][n]: row r has `T` entries starting at column
@@ -180,6 +180,7 @@ struct ef_plan {
     bool ytc_ok = false;          // tensor-core y passes (EF_PREC_BF16X3)
     bool ytc_fit = false;         // the banded y tiling fits this geometry (ytc_ok unless switched off)
     unsigned gen = 0;             // bumped whenever scratch or the kernel choice changes (batch graphs re-capture)
+    long long wait_limit = 0;     // bound of one device wait in SM clocks (0: the default, about 2 s)
     eles::YTcGeom ytc;            // their banded tiling
     uint4 *d_yfrag = nullptr;     // their A fragments, [S][kYOps][kstot][2][32]
     double *d_ygrid = nullptr;    // DNS y nodes on the device
@@ -241,6 +242,9 @@ int ws_setup(ef_plan *p, const char **why);
 void ws_free(WsHost &w);
 int ws_run(const ef_plan *p, int nsnap, const float *u, float *h, double *uref, double *plane_mean, int nf,
            cudaStream_t st);
+int ws_run_batch(ef_plan *const *plans, const int *nsnap, const float *const *u, int n, int nf, cudaStream_t st);
+// filter_kernels.cu: the y stage of a plan whose h (and profile) are in place
+int run_y_stage(ef_plan *p, int nsnap, void *ubar, void *tau, bool stress, cudaStream_t s);
 
 // closure_tc.cu: tensor-core inference of the closure MLP.  `image` is a
 // device buffer of closure_tc_image_bytes() that the call repacks from the

@@ -430,6 +430,55 @@ void xz_unfused(ef_plan *p, const T *u, T *h, double *uref, double *plane_mean, 
         plane_mean_direct<T><<<dim3(p->ny, 3), 256, 0, s>>>(u, uref, p->nx, p->ny, p->nz, plane_mean);
 }
 
+// The y contraction and the recovery of ~bar(u) and T (and the y-profile
+// terms) for ns snapshots whose h and reference profile are in place.
+template <typename T>
+int y_stage(ef_plan *p, int ns, T *ubar, T *tau, bool stress, cudaStream_t s, const PhaseEvents *pe)
+{
+    T *h = static_cast<T *>(p->d_h);
+    cudaError_t e = cudaSuccess;
+    T *wy = static_cast<T *>(p->d_wy);
+    e = launch_yprofile<T>(p->d_uref, p->d_ystart, p->d_ycount, p->d_yw64[0], p->d_yw64[1], p->ny, p->nly,
+                           p->ext == EF_EXT_ODD_EVEN, ns, p->d_AU, p->d_AUU, wy, p->d_Kab, s);
+    if (e != cudaSuccess) return cuda_fail(e, "yprofile launch");
+    if constexpr (sizeof(T) == 4) {
+        if (p->ytc_ok) {   // tensor-core y passes (split-precision plans)
+            YTcArgs yt;
+            memset(&yt, 0, sizeof yt);
+            yt.geo = p->ytc;
+            const int nplane = p->nlz * p->nlx;
+            int rc = encode_h_map(h, nplane, p->ny, ns, p->ytc.box_rows, &yt.hmap);
+            if (rc) return rc;
+            e = launch_yfrag(p->ytc, p->d_yw64[0], p->d_yw64[1], p->d_uref, p->d_AU, p->ny, p->nly, ns, p->d_yfrag, s);
+            if (e != cudaSuccess) return cuda_fail(e, "yfrag launch");
+            yt.frag = p->d_yfrag; yt.AU = p->d_AU; yt.Kab = p->d_Kab;
+            yt.ubar = ubar; yt.tau = tau; yt.tmp = static_cast<float *>(p->d_ytmp);
+            yt.ny = p->ny; yt.nly = p->nly; yt.nplane = nplane;
+            yt.nlz = p->nlz; yt.nlx = p->nlx; yt.ptrans = p->fused && p->x_variant == 3;
+            yt.stress = stress ? 1 : 0; yt.flip = p->ext == EF_EXT_ODD_EVEN; yt.err = p->d_err;
+            e = launch_ytc(yt, ns, s);
+            if (e != cudaSuccess) return cuda_fail(e, "ytc launch");
+            prof_mark(pe, 3, s);
+            prof_mark(pe, 4, s);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(e, "filter launch");
+            return EF_OK;
+        }
+    }
+    YArgs<T> y;
+    y.h = h; y.wy = wy; y.AU = p->d_AU; y.AUU = p->d_AUU; y.ystart = p->d_ystart; y.ycount = p->d_ycount;
+    y.ubar = ubar; y.tau = tau; y.tmp = static_cast<T *>(p->d_ytmp); y.ny = p->ny; y.nly = p->nly; y.nlz = p->nlz; y.nlx = p->nlx;
+    y.stress = stress ? 1 : 0; y.flip = p->ext == EF_EXT_ODD_EVEN; y.err = p->d_err;
+    y.ptrans = p->fused && p->x_variant == 3;
+    e = launch_ypass<T>(y, ns, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ypass launch");
+    prof_mark(pe, 3, s);
+    prof_mark(pe, 4, s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "filter launch");
+    return EF_OK;
+}
+
 template <typename T>
 int run_group(ef_plan *p, int ns, const T *u, T *ubar, T *tau, double *plane_mean, bool stress,
               cudaStream_t s, const PhaseEvents *pe)
@@ -477,46 +526,7 @@ int run_group(ef_plan *p, int ns, const T *u, T *ubar, T *tau, double *plane_mea
     }
     prof_mark(pe, 1, s);
     prof_mark(pe, 2, s);
-    T *wy = static_cast<T *>(p->d_wy);
-    e = launch_yprofile<T>(p->d_uref, p->d_ystart, p->d_ycount, p->d_yw64[0], p->d_yw64[1], p->ny, p->nly,
-                           p->ext == EF_EXT_ODD_EVEN, ns, p->d_AU, p->d_AUU, wy, p->d_Kab, s);
-    if (e != cudaSuccess) return cuda_fail(e, "yprofile launch");
-    if constexpr (sizeof(T) == 4) {
-        if (p->ytc_ok) {   // tensor-core y passes (split-precision plans)
-            YTcArgs yt;
-            memset(&yt, 0, sizeof yt);
-            yt.geo = p->ytc;
-            const int nplane = p->nlz * p->nlx;
-            int rc = encode_h_map(h, nplane, p->ny, ns, p->ytc.box_rows, &yt.hmap);
-            if (rc) return rc;
-            e = launch_yfrag(p->ytc, p->d_yw64[0], p->d_yw64[1], p->d_uref, p->d_AU, p->ny, p->nly, ns, p->d_yfrag, s);
-            if (e != cudaSuccess) return cuda_fail(e, "yfrag launch");
-            yt.frag = p->d_yfrag; yt.AU = p->d_AU; yt.Kab = p->d_Kab;
-            yt.ubar = ubar; yt.tau = tau; yt.tmp = static_cast<float *>(p->d_ytmp);
-            yt.ny = p->ny; yt.nly = p->nly; yt.nplane = nplane;
-            yt.nlz = p->nlz; yt.nlx = p->nlx; yt.ptrans = p->fused && p->x_variant == 3;
-            yt.stress = stress ? 1 : 0; yt.flip = p->ext == EF_EXT_ODD_EVEN; yt.err = p->d_err;
-            e = launch_ytc(yt, ns, s);
-            if (e != cudaSuccess) return cuda_fail(e, "ytc launch");
-            prof_mark(pe, 3, s);
-            prof_mark(pe, 4, s);
-            e = cudaGetLastError();
-            if (e != cudaSuccess) return cuda_fail(e, "filter launch");
-            return EF_OK;
-        }
-    }
-    YArgs<T> y;
-    y.h = h; y.wy = wy; y.AU = p->d_AU; y.AUU = p->d_AUU; y.ystart = p->d_ystart; y.ycount = p->d_ycount;
-    y.ubar = ubar; y.tau = tau; y.tmp = static_cast<T *>(p->d_ytmp); y.ny = p->ny; y.nly = p->nly; y.nlz = p->nlz; y.nlx = p->nlx;
-    y.stress = stress ? 1 : 0; y.flip = p->ext == EF_EXT_ODD_EVEN; y.err = p->d_err;
-    y.ptrans = p->fused && p->x_variant == 3;
-    e = launch_ypass<T>(y, ns, s);
-    if (e != cudaSuccess) return cuda_fail(e, "ypass launch");
-    prof_mark(pe, 3, s);
-    prof_mark(pe, 4, s);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "filter launch");
-    return EF_OK;
+    return y_stage<T>(p, ns, ubar, tau, stress, s, pe);
 }
 
 template <typename T>
@@ -537,6 +547,13 @@ int run_typed(ef_plan *p, int nsnap, const T *u, T *ubar, T *tau, double *plane_
 }
 
 }  // namespace
+
+int run_y_stage(ef_plan *p, int nsnap, void *ubar, void *tau, bool stress, cudaStream_t s)
+{
+    if (p->prec == EF_PREC_FP64)
+        return y_stage<double>(p, nsnap, static_cast<double *>(ubar), static_cast<double *>(tau), stress, s, nullptr);
+    return y_stage<float>(p, nsnap, static_cast<float *>(ubar), static_cast<float *>(tau), stress, s, nullptr);
+}
 
 int run_filter(ef_plan *p, int nsnap, const void *u, void *ubar, void *tau, double *plane_mean, bool stress,
                cudaStream_t s, const PhaseEvents *pe)

@@ -173,6 +173,16 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
                  : "memory");
     return ok != 0;
 }
+// Non-blocking test of a phase (no suspend).
+__device__ __forceinline__ bool mbar_test_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
 // Bounded wait of at most `limit` SM clocks; returns false (and flags the
 // plan) if the phase never completed.
 __device__ __forceinline__ bool mbar_wait_for(unsigned long long *bar, unsigned parity, int *err, long long limit)

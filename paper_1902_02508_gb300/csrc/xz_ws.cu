@@ -274,39 +274,80 @@ void ws_free(WsHost &w)
     w.ok = false;
 }
 
-cudaError_t ws_launch_bf16(const ws::WsArgs &a, int nz, int opc, int nsnap, cudaStream_t st);
-cudaError_t ws_launch_tf32(const ws::WsArgs &a, int nz, int opc, int nsnap, cudaStream_t st);
+cudaError_t ws_launch_bf16(const ws::WsMulti &m, int nz, int opc, cudaStream_t st);
+cudaError_t ws_launch_tf32(const ws::WsMulti &m, int nz, int opc, cudaStream_t st);
+
+// Kernel arguments of one plan for nsnap snapshots at u (the TMA view of u
+// included), after the reference-profile launch on stream st.
+static int ws_prepare(const ef_plan *p, int nsnap, const float *u, float *h, double *uref, double *plane_mean, int nf,
+                      cudaStream_t st, ws::WsArgs *a)
+{
+    const WsHost &w = p->ws;
+    memset(a, 0, sizeof *a);
+    a->box_rows = p->nz > 256 ? p->nz / 2 : p->nz;
+    int rc = encode_u_map(u, p->nx, p->ny, p->nz, nsnap, ws::CW, a->box_rows, &a->tmap);
+    if (rc) return rc;
+    // the reference profile first (1/nz of a plane read), then the persistent kernel
+    ws_uref<<<dim3(p->ny, nsnap), 96, 0, st>>>(u, p->nx, p->ny, p->nz, uref);
+    a->u = u; a->h = h; a->uref = uref; a->plane_mean = plane_mean; a->err = p->d_err;
+    a->nx = p->nx; a->ny = p->ny; a->nz = p->nz; a->nlx = p->nlx; a->nlz = p->nlz;
+    a->nchunk = w.nchunk; a->bshift = w.bshift; a->rx = p->rx.r; a->CB = w.CB; a->OP = w.OP;
+    for (int ph = 0; ph < 4; ph++) a->xc0[ph] = w.xc0[ph];
+    a->RZ = p->rz.r; a->KS = w.KS; a->zoff = w.zoff; a->nf = nf; a->nsnap = nsnap;
+    a->wait_limit = p->wait_limit > 0 ? p->wait_limit : fz::kWaitCycles;
+    a->afrag = reinterpret_cast<const uint4 *>(w.d_afrag);
+    a->bvar = reinterpret_cast<const uint4 *>(w.d_bvar);
+    return EF_OK;
+}
+
+static int ws_launch_class(const ws::WsMulti &m, int nz, int mode, int opc, cudaStream_t st)
+{
+    const cudaError_t e = mode == ws::MODE_TF32X2 ? ws_launch_tf32(m, nz, opc, st) : ws_launch_bf16(m, nz, opc, st);
+    return e == cudaSuccess ? EF_OK : cuda_fail(e, "xz_ws launch");
+}
 
 int ws_run(const ef_plan *p, int nsnap, const float *u, float *h, double *uref, double *plane_mean, int nf,
            cudaStream_t st)
 {
-    const WsHost &w = p->ws;
-    ws::WsArgs a;
-    memset(&a, 0, sizeof a);
-    a.box_rows = p->nz > 256 ? p->nz / 2 : p->nz;
-    int rc = encode_u_map(u, p->nx, p->ny, p->nz, nsnap, ws::CW, a.box_rows, &a.tmap);
+    ws::WsMulti m;
+    memset(&m, 0, sizeof m);
+    m.nplan = 1;
+    int rc = ws_prepare(p, nsnap, u, h, uref, plane_mean, nf, st, &m.plan[0]);
     if (rc) return rc;
-    // the reference profile first (1/nz of a plane read), then the persistent kernel
-    ws_uref<<<dim3(p->ny, nsnap), 96, 0, st>>>(u, p->nx, p->ny, p->nz, uref);
-    a.u = u; a.h = h; a.uref = uref; a.plane_mean = plane_mean; a.err = p->d_err;
-    a.nx = p->nx; a.ny = p->ny; a.nz = p->nz; a.nlx = p->nlx; a.nlz = p->nlz;
-    a.nchunk = w.nchunk; a.bshift = w.bshift; a.rx = p->rx.r; a.CB = w.CB; a.OP = w.OP;
-    for (int ph = 0; ph < 4; ph++) a.xc0[ph] = w.xc0[ph];
-    a.RZ = p->rz.r; a.KS = w.KS; a.zoff = w.zoff; a.nf = nf;
-    a.afrag = reinterpret_cast<const uint4 *>(w.d_afrag);
-    a.bvar = reinterpret_cast<const uint4 *>(w.d_bvar);
-    const cudaError_t e = w.mode == ws::MODE_TF32X2 ? ws_launch_tf32(a, p->nz, w.OPC, nsnap, st)
-                                                     : ws_launch_bf16(a, p->nz, w.OPC, nsnap, st);
-    if (e != cudaSuccess) return cuda_fail(e, "xz_ws launch");
+    return ws_launch_class(m, p->nz, p->ws.mode, p->ws.OPC, st);
+}
+
+// The x-z stage of several plans (each with nsnap[i] snapshots at u[i] and
+// its own scratch), one launch per kernel class (nz, precision, outputs per
+// chunk) of at most kWsMaxPlans plans.  Every plan must run the
+// warp-specialised kernel.
+int ws_run_batch(ef_plan *const *plans, const int *nsnap, const float *const *u, int n, int nf, cudaStream_t st)
+{
+    std::vector<bool> done(n, false);
+    for (int i = 0; i < n; i++) {
+        if (done[i]) continue;
+        const ef_plan *c = plans[i];
+        ws::WsMulti m;
+        memset(&m, 0, sizeof m);
+        for (int k = i; k < n && m.nplan < ws::kWsMaxPlans; k++) {
+            const ef_plan *q = plans[k];
+            if (done[k] || q->nz != c->nz || q->ws.mode != c->ws.mode || q->ws.OPC != c->ws.OPC) continue;
+            int rc = ws_prepare(q, nsnap[k], u[k], static_cast<float *>(q->d_h), q->d_uref, nullptr, nf, st,
+                                &m.plan[m.nplan++]);
+            if (rc) return rc;
+            done[k] = true;
+        }
+        int rc = ws_launch_class(m, c->nz, c->ws.mode, c->ws.OPC, st);
+        if (rc) return rc;
+    }
     return EF_OK;
 }
 
-cudaError_t ws_launch_bf16(const ws::WsArgs &a, int nz, int opc, int nsnap, cudaStream_t st)
+cudaError_t ws_launch_bf16(const ws::WsMulti &m, int nz, int opc, cudaStream_t st)
 {
     using namespace ws;
 #define ELES_WS_GO(NZ)                                                                                   \
-    if (nz == NZ) return opc == 2 ? ws_launch<NZ, MODE_BF16X3, 2>(a, nsnap, st)                          \
-                                  : ws_launch<NZ, MODE_BF16X3, 1>(a, nsnap, st);
+    if (nz == NZ) return opc == 2 ? ws_launch<NZ, MODE_BF16X3, 2>(m, st) : ws_launch<NZ, MODE_BF16X3, 1>(m, st);
     ELES_WS_NZ_LIST(ELES_WS_GO)
 #undef ELES_WS_GO
     return cudaErrorInvalidValue;

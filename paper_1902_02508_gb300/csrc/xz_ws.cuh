@@ -80,8 +80,20 @@ struct WsArgs {
     int RZ, KS, zoff;     // z phase: stride, k-steps per Z tile, window offset
     int nf;               // fields contracted in z (9, or 3 for the velocities only)
     int nsnap;            // snapshots (items are (snapshot, y-plane, phase))
+    long long wait_limit; // bound of one wait in SM clocks (kWaitCycles unless set for tests)
     const uint4 *afrag;   // z A fragments [KS][hi, lo][32 lanes] (pair order)
     const uint4 *bvar;    // x B fragments [OP][NR][32 lanes][Bw]
+};
+
+// One launch over the items of up to kWsMaxPlans plans of one kernel class
+// (nz, precision, outputs per chunk): CTAs cta0[i] .. cta0[i + 1] - 1 walk
+// plan i's items (a multiple of its OP), so each CTA loads its plan's
+// tables once.  Plans of different grids and filter widths share the launch.
+constexpr int kWsMaxPlans = 16;
+struct WsMulti {
+    WsArgs plan[kWsMaxPlans];
+    int nplan;
+    int cta0[kWsMaxPlans + 1];
 };
 
 __device__ __forceinline__ unsigned pack_f16(float lo_k, float hi_k)
@@ -206,17 +218,18 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Bounded wait shared by the roles.  Once any wait of the CTA has run out
-// the others return at once and the roles stop: the producer issues no new
-// stage and the consumers stop touching the stage and column buffers (a bulk
-// copy issued before may still be landing; the producer waits for those
-// with its own bound before the CTA exits).  The error word tells the host.
+// Bounded wait shared by the roles (at most `limit` SM clocks after a first
+// non-blocking test).  Once any wait of the CTA has run out the others return
+// at once and the roles stop: the producer issues no new stage and the
+// consumers stop touching the stage and column buffers (a bulk copy issued
+// before may still be landing; the producer waits for those, with the long
+// bound, before the CTA exits).  The error word tells the host.
 __device__ __forceinline__ bool wait_or_abort(unsigned long long *bar, unsigned parity, volatile int *abort_flag,
-                                              int *err)
+                                              int *err, long long limit)
 {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_test_wait(bar, parity)) return true;
     const long long t0 = clock64();
-    while (clock64() - t0 < kWaitCycles) {
+    while (clock64() - t0 < limit) {
         if (*abort_flag) return false;
         if (mbar_try_wait(bar, parity)) return true;
     }
@@ -304,8 +317,12 @@ struct Geo {
 };
 
 template <int NZ, int MODE, int OPC>
-__global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_constant__ WsArgs a)
+__global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_constant__ WsMulti mp)
 {
+    int pi = 0;
+    while (pi + 1 < mp.nplan && (int)blockIdx.x >= mp.cta0[pi + 1]) pi++;
+    const WsArgs &a = mp.plan[pi];
+    const int cta = (int)blockIdx.x - mp.cta0[pi], ncta = mp.cta0[pi + 1] - mp.cta0[pi];
     using G = Geo<NZ>;
     constexpr int LD = G::LD, NXW = G::NXW, STGF = G::STGF;
     constexpr int NR = 8 / OPC;                  // B rotations
@@ -327,9 +344,9 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
     __shared__ int abort_flag;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t = lane & 3;
-    // persistent: items (snapshot, plane, phase) = it, it + gridDim.x, ...;
-    // gridDim.x is a multiple of OP, so the phase of a CTA is fixed
-    const int p = blockIdx.x % a.OP;
+    // persistent: items (snapshot, plane, phase) = it, it + ncta, ... of the
+    // CTA's plan; ncta is a multiple of OP, so the phase of a CTA is fixed
+    const int p = cta % a.OP;
     const int nitems = a.ny * a.OP * a.nsnap;
     const size_t np = (size_t)a.nx * a.ny * NZ;
     const int nchunk = a.nchunk;
@@ -356,12 +373,12 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
     if (warp == 0) {   // producer: stage k = chunk k = x blocks CB k - bshift .. + CB - 1, item by item
         if (lane == 0) {
             int gk = 0;
-            for (int it = blockIdx.x; it < nitems && !*abort_v; it += gridDim.x) {
+            for (int it = cta; it < nitems && !*abort_v; it += ncta) {
                 const int j = (it / a.OP) % a.ny, s = it / (a.OP * a.ny);
                 const int pc0 = s * 3 * a.ny + j;   // TMA plane coordinate of component 0
                 for (int k = 0; k < nchunk; k++, gk++) {
                     const int st = gk % CSTG;
-                    if (gk >= CSTG && !wait_or_abort(&empty[st], ((gk / CSTG) - 1) & 1, abort_v, a.err)) break;
+                    if (gk >= CSTG && !wait_or_abort(&empty[st], ((gk / CSTG) - 1) & 1, abort_v, a.err, a.wait_limit)) break;
                     if (*abort_v) break;
                     int b = (a.CB * k - a.bshift) % a.nlx;   // a multiple of CB: the chunk never wraps
                     if (b < 0) b += a.nlx;
@@ -400,11 +417,11 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
             for (int c = 0; c < 3; c++) U[c] = it < nitems ? (float)a.uref[((size_t)s * 3 + c) * a.ny + j] : 0.f;
         };
         float Un[3];
-        uref_of(blockIdx.x, Un);
+        uref_of(cta, Un);
         int gc = 0;                               // chunks of this CTA so far
-        for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        for (int it = cta; it < nitems; it += ncta) {
             const float U[3] = {Un[0], Un[1], Un[2]};
-            uref_of(it + gridDim.x, Un);
+            uref_of(it + ncta, Un);
             float acc[2][NF][4];
 #pragma unroll
             for (int m = 0; m < 2; m++)
@@ -415,7 +432,7 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
             bool stop = false;
             for (int sidx = 0; sidx < nchunk; sidx++, gc++) {
                 const int st = gc % CSTG;
-                if (!wait_or_abort(&full[st], (gc / CSTG) & 1, abort_v, a.err)) { stop = true; break; }
+                if (!wait_or_abort(&full[st], (gc / CSTG) & 1, abort_v, a.err, a.wait_limit)) { stop = true; break; }
                 const int q = sidx % NR;
                 uint4 B[BW];
 #pragma unroll
@@ -439,7 +456,7 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
                 mbar_arrive(&empty[st]);
                 // the chunk completes phase outputs X0 + OP i, i < OPC (tile columns OPC q + i)
                 const int cb = gc & 1;
-                if (gc >= 2 && !wait_or_abort(&cempty[cb], ((gc >> 1) - 1) & 1, abort_v, a.err)) { stop = true; break; }
+                if (gc >= 2 && !wait_or_abort(&cempty[cb], ((gc >> 1) - 1) & 1, abort_v, a.err, a.wait_limit)) { stop = true; break; }
                 const int X0 = xc0 + a.OP * OPC * sidx;
                 const int b0 = a.CB * sidx - a.bshift;     // first x block of the chunk
                 float *colw = colw0 + (size_t)cb * NCBO * LD;
@@ -530,13 +547,13 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
     const int zw = warp - 1;
     const int nzt = a.nlz / 16;
     int gc = 0;
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    for (int it = cta; it < nitems; it += ncta) {
         const int j = (it / a.OP) % a.ny, s = it / (a.OP * a.ny);
         double pmean = 0.0;
         bool stop = false;
         for (int sidx = 0; sidx < nchunk; sidx++, gc++) {
             const int cb = gc & 1;
-            if (!wait_or_abort(&cfull[cb], (gc >> 1) & 1, abort_v, a.err)) { stop = true; break; }
+            if (!wait_or_abort(&cfull[cb], (gc >> 1) & 1, abort_v, a.err, a.wait_limit)) { stop = true; break; }
             const int X0 = xc0 + a.OP * OPC * sidx;
             const bool val0 = X0 >= 0 && X0 < a.nlx;
             const bool val1 = OPC == 2 && X0 + a.OP >= 0 && X0 + a.OP < a.nlx;
@@ -581,34 +598,43 @@ size_t ws_smem_bytes(int KS)
            sizeof(float) * ((size_t)2 * NCBO * G::LD + (size_t)CSTG * G::STGF);
 }
 
+// Launch over the plans of one class; the grid is as many CTAs as fit at
+// once, shared among the plans in proportion to their chunks (each share a
+// multiple of the plan's OP and at most its item count).  Dynamic shared
+// memory for the largest z-fragment table of the class.
 template <int NZ, int MODE, int OPC>
-cudaError_t ws_launch(const WsArgs &a, int nsnap, cudaStream_t st)
+cudaError_t ws_launch(WsMulti m, cudaStream_t st)
 {
-    const size_t smem = ws_smem_bytes<NZ, MODE, OPC>(a.KS);
+    size_t smem = 0;
+    for (int i = 0; i < m.nplan; i++) {
+        const size_t b = ws_smem_bytes<NZ, MODE, OPC>(m.plan[i].KS);
+        smem = b > smem ? b : smem;
+    }
     static size_t attr = 0;
     if (smem > attr) {
         cudaError_t e = cudaFuncSetAttribute(xz_ws<NZ, MODE, OPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = smem;
     }
-    // persistent grid: as many CTAs as fit at once, a multiple of OP (each CTA
-    // keeps one output phase), at most one per item
-    static int per_sm = 0, nsm = 0;
-    if (!per_sm) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xz_ws<NZ, MODE, OPC>, Geo<NZ>::THREADS, smem);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) per_sm = 1;
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xz_ws<NZ, MODE, OPC>, Geo<NZ>::THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    double work = 0.0;
+    for (int i = 0; i < m.nplan; i++) work += (double)m.plan[i].ny * m.plan[i].OP * m.plan[i].nsnap * m.plan[i].nchunk;
+    m.cta0[0] = 0;
+    for (int i = 0; i < m.nplan; i++) {
+        const WsArgs &a = m.plan[i];
+        const int nitems = a.ny * a.OP * a.nsnap;
+        const double w = (double)a.ny * a.OP * a.nsnap * a.nchunk;
+        int g = (int)((double)nsm * per_sm * w / work) / a.OP * a.OP;
+        if (g < a.OP) g = a.OP;
+        if (g > nitems) g = nitems;
+        m.cta0[i + 1] = m.cta0[i] + g;
     }
-    const int nitems = a.ny * a.OP * nsnap;
-    int grid = nsm * per_sm / a.OP * a.OP;
-    if (grid < a.OP) grid = a.OP;
-    if (grid > nitems) grid = nitems;
-    WsArgs b = a;
-    b.nsnap = nsnap;
-    xz_ws<NZ, MODE, OPC><<<grid, Geo<NZ>::THREADS, smem, st>>>(b);
+    xz_ws<NZ, MODE, OPC><<<m.cta0[m.nplan], Geo<NZ>::THREADS, smem, st>>>(m);
     return cudaGetLastError();
 }
 

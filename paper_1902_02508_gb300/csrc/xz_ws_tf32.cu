@@ -5,12 +5,11 @@
 
 namespace eles {
 
-cudaError_t ws_launch_tf32(const ws::WsArgs &a, int nz, int opc, int nsnap, cudaStream_t st)
+cudaError_t ws_launch_tf32(const ws::WsMulti &m, int nz, int opc, cudaStream_t st)
 {
     using namespace ws;
 #define ELES_WS_GO(NZ)                                                                                   \
-    if (nz == NZ) return opc == 2 ? ws_launch<NZ, MODE_TF32X2, 2>(a, nsnap, st)                          \
-                                  : ws_launch<NZ, MODE_TF32X2, 1>(a, nsnap, st);
+    if (nz == NZ) return opc == 2 ? ws_launch<NZ, MODE_TF32X2, 2>(m, st) : ws_launch<NZ, MODE_TF32X2, 1>(m, st);
     ELES_WS_NZ_LIST(ELES_WS_GO)
 #undef ELES_WS_GO
     return cudaErrorInvalidValue;

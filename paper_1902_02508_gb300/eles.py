@@ -35,7 +35,7 @@ EXPORTED = ("ef_filter_setup", "ef_plan_destroy", "ef_filter_fields", "ef_subfil
             "ef_check_device_error", "ef_plan_info", "ef_plan_weights", "ef_profile_enable",
             "ef_profile_read", "ef_last_error", "ef_version", "ef_closure_create", "ef_closure_destroy",
             "ef_closure_features", "ef_closure_fit_norm", "ef_closure_train", "ef_closure_infer",
-            "ef_closure_infer_exact",
+            "ef_closure_infer_exact", "ef_plan_set_wait_limit",
             "ef_closure_gradients", "ef_closure_param_count", "ef_closure_get_params", "ef_closure_set_params",
             "ef_closure_save", "ef_closure_load", "ef_batch_create", "ef_batch_run", "ef_batch_destroy",
             "ef_batch_captures", "ef_plan_autotune", "ef_plan_set_variant", "ef_closure_features_static", "ef_io_create",
@@ -114,6 +114,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             lib.ef_closure_infer.restype = i
             lib.ef_closure_infer_exact.argtypes = [vp, vp, vp, L, vp, vp, ctypes.POINTER(L), vp]
             lib.ef_closure_infer_exact.restype = i
+            lib.ef_plan_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
+            lib.ef_plan_set_wait_limit.restype = i
             lib.ef_selftest_wait.argtypes = [vp, ctypes.c_longlong, i, vp]
             lib.ef_selftest_wait.restype = i
             lib.ef_differential_unfilter.argtypes = [ctypes.POINTER(_Grid), d, i, vp, vp, vp]
@@ -261,6 +263,11 @@ def subfilter_stress_batch(plan: Plan, u, ubar, tau, plane_mean=None, stream=Non
 
 def plan_reserve(plan: Plan, max_snapshots: int) -> None:
     _check(load().ef_plan_reserve(plan.handle, int(max_snapshots)))
+
+
+def plan_set_wait_limit(plan: Plan, cycles: int) -> None:
+    """Bound of every wait in the warp-specialised x-z kernel (0: default)."""
+    _check(load().ef_plan_set_wait_limit(plan.handle, int(cycles)))
 
 
 def check_device_error(plan: Plan, stream=None) -> int:

@@ -137,3 +137,26 @@ def shifted(u: np.ndarray, sx: int, sz: int) -> np.ndarray:
 TWO_PI = 2.0 * math.pi
 BOX_SMALL = (TWO_PI, math.pi)          # 2 pi x 2 x pi (Sec. 3)
 BOX_LARGE = (2.0 * TWO_PI, TWO_PI)     # 4 pi x 2 x 2 pi
+
+
+# The batched configuration: snapshots of uneven channel grids, each with its
+# own constant filter width, in the 4 pi x 2 x 2 pi box; LES grid = DNS / 4 in
+# every direction (its y nodes are every fourth DNS node).
+BATCH_GRIDS = ((128, 97, 128), (192, 129, 192), (256, 193, 256))
+BATCH_WIDTHS = (16, 32, 48)          # Delta = Lx / w
+
+
+def batch_draws(n: int = 64, seed: int = 7):
+    """The (grid, width) of each of n snapshots: uniform draws over the three
+    grids and the three widths from a seeded PCG64 stream."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    g = rng.integers(0, len(BATCH_GRIDS), n)
+    w = rng.integers(0, len(BATCH_WIDTHS), n)
+    return [(BATCH_GRIDS[a], BATCH_WIDTHS[b]) for a, b in zip(g, w)]
+
+
+def batch_grids(shape):
+    """(dns, les) of one batched-configuration grid."""
+    nx, ny, nz = shape
+    dns = dns_grid(nx, ny, nz, *BOX_LARGE)
+    return dns, les_grid(dns, nx // 4, (ny - 1) // 4 + 1, nz // 4)

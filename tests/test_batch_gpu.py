@@ -118,3 +118,40 @@ def test_batch_recaptures_after_scratch_or_variant_change():
     for k, (dns, les, delta, u) in enumerate(cases):
         _, tau_ref = O.subfilter_stress(dns, les, delta, u[0])
         assert np.abs(taus[k][0].double().cpu().numpy() - tau_ref).max() <= 1e-4
+
+
+@pytest.mark.parametrize("prec", [eles.PREC_BF16X3, eles.PREC_TF32X2])
+def test_mixed_batch_of_the_batched_configuration(prec):
+    """Six items of the batched configuration (its three grids, LES = DNS / 4,
+    and its three filter widths; one snapshot each) in one batch: the x-z
+    stages share persistent launches per kernel class, every item matches
+    the oracle, and the result equals the plans called one by one bit for bit."""
+    dev = torch.device("cuda")
+    items = [((128, 97, 128), 16), ((128, 97, 128), 48), ((192, 129, 192), 32), ((192, 129, 192), 16),
+             ((256, 193, 256), 48), ((256, 193, 256), 32)]
+    plans, us, ubs, taus, cases = [], [], [], [], []
+    for k, (shape, w) in enumerate(items):
+        dns, les = I.batch_grids(shape)
+        delta = dns.Lx / w
+        plan = eles.filter_setup(dns, les, delta, precision=prec)
+        assert eles.plan_info(plan, 10) == 3
+        u = I.channel_velocity(dns, 700 + k)
+        plans.append(plan)
+        cases.append((dns, les, delta, u))
+        us.append(torch.from_numpy(u[None]).to(dev, torch.float32))
+        ubs.append(torch.full((1, 3, les.ny, les.nz, les.nx), float("nan"), device=dev))
+        taus.append(torch.full((1, 6, les.ny, les.nz, les.nx), float("nan"), device=dev))
+    batch = eles.batch_create(plans, [1] * len(items))
+    eles.batch_run(batch, us, ubs, taus)
+    eles.batch_run(batch, us, ubs, taus)
+    torch.cuda.synchronize()
+    for k, (dns, les, delta, u) in enumerate(cases):
+        assert eles.check_device_error(plans[k]) == 0
+        ub_ref, tau_ref = O.subfilter_stress(dns, les, delta, u)
+        assert np.abs(ubs[k][0].double().cpu().numpy() - ub_ref).max() <= 1e-4, k
+        assert np.abs(taus[k][0].double().cpu().numpy() - tau_ref).max() <= 1e-4, k
+        ub1 = torch.empty_like(ubs[k])
+        t1 = torch.empty_like(taus[k])
+        eles.subfilter_stress_batch(plans[k], us[k], ub1, t1)
+        torch.cuda.synchronize()
+        assert torch.equal(ub1, ubs[k]) and torch.equal(t1, taus[k]), k
