@@ -58,7 +58,8 @@ typedef enum {
     EF_ERR_NAN = 4,          /* non-finite values seen on the device */
     EF_ERR_TIMEOUT = 5,      /* a bounded device wait ran out */
     EF_ERR_OOM = 6,          /* device allocation failed in a setup call */
-    EF_ERR_UNSUPPORTED = 7   /* valid request the library does not implement */
+    EF_ERR_UNSUPPORTED = 7,  /* valid request the library does not implement */
+    EF_ERR_RANGE = 8         /* a global index failed its range check (range-checked build only) */
 } ef_status;
 
 /* Filter kernels.  The Gaussian, with the y integral of Eq. 2 on the
@@ -525,6 +526,15 @@ int ef_closure_set_params(ef_closure *closure, const float *params, const double
  * reproduces an uninterrupted run bit for bit. */
 int ef_closure_save(const ef_closure *closure, const char *path);
 int ef_closure_load(ef_closure *closure, const char *path);
+
+/*
+ * ef_debug_fail_alloc -- test hook: the n-th device allocation the library
+ * makes from now on (n = 0: the next one) fails as if the device were out of
+ * memory, so that the set-up calls' EF_ERR_OOM paths (and the release of
+ * what they had allocated) can be tested without exhausting the GPU; n = -1
+ * disables the hook.  Process-wide.  Errors: EF_ERR_ARG (n < -1).
+ */
+int ef_debug_fail_alloc(int n);
 
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char *ef_last_error(void);

@@ -18,6 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libeles.so")
+CHECK_DIR = os.path.join(HERE, "_lib_check")
+CHECK_LIB = os.path.join(CHECK_DIR, "libeles_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -40,17 +42,23 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, check: bool = False) -> str:
+    """Build libeles.so; with check=True the range-checked debug library
+    (-DELES_CHECK: every checked global index that falls outside its buffer
+    records EF_ERR_RANGE in the error word and skips the access) in
+    _lib_check/libeles_check.so, which eles.load() picks when the environment
+    variable ELES_CHECK is 1."""
+    out_dir, lib = (CHECK_DIR, CHECK_LIB) if check else (OUT_DIR, LIB)
+    os.makedirs(out_dir, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
                + glob.glob(os.path.join(INCLUDE, "*.h")))
-    objs = [os.path.join(OUT_DIR, os.path.basename(s)[:-3] + ".o") for s in sources]
+    objs = [os.path.join(out_dir, os.path.basename(s)[:-3] + ".o") for s in sources]
     todo = [(s, o) for s, o in zip(sources, objs) if force or _stale(o, [s, *headers])]
 
     def compile_one(so):
         s, o = so
-        cmd = [nvcc(), *_flags(), "-c", s, "-o", o + ".tmp"]
+        cmd = [nvcc(), *_flags(["-DELES_CHECK"] if check else []), "-c", s, "-o", o + ".tmp"]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -61,14 +69,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if todo:
         with cf.ThreadPoolExecutor(max_workers=min(len(todo), os.cpu_count() or 4)) as ex:
             list(ex.map(compile_one, todo))
-    if force or todo or _stale(LIB, objs):
-        tmp = LIB + f".{os.getpid()}.tmp"
+    if force or todo or _stale(lib, objs):
+        tmp = lib + f".{os.getpid()}.tmp"
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

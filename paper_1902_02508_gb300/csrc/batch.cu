@@ -176,7 +176,7 @@ int ef_plan_autotune(ef_plan *p, const void *u, void *ubar, void *tau, int reps,
         p->P = c.P;
         if (!p->fused && !p->d_g) {   // the unfused path needs its x scratch
             const size_t es = p->prec == EF_PREC_FP64 ? sizeof(double) : sizeof(float);
-            cudaError_t e = cudaMalloc(&p->d_g, es * 9 * (size_t)p->ny * p->nz * p->nlx);
+            cudaError_t e = dev_malloc(&p->d_g, es * 9 * (size_t)p->ny * p->nz * p->nlx);
             if (e != cudaSuccess) { rc = cuda_fail(e, "autotune scratch"); break; }
         }
         if (p->fused) {
@@ -225,7 +225,7 @@ static int set_x_variant(ef_plan *p, int choice)
     if (v == 0) {
         if (!p->d_g) {
             const size_t es = p->prec == EF_PREC_FP64 ? sizeof(double) : sizeof(float);
-            cudaError_t e = cudaMalloc(&p->d_g, es * 9 * (size_t)p->ny * p->nz * p->nlx);
+            cudaError_t e = dev_malloc(&p->d_g, es * 9 * (size_t)p->ny * p->nz * p->nlx);
             if (e != cudaSuccess) return cuda_fail(e, "ef_plan_set_variant");
         }
         p->fused = false;

@@ -302,15 +302,15 @@ int closure_alloc_batch(ef_closure *c, int cap)
     cudaFree(c->T); cudaFree(c->dA); cudaFree(c->dB); cudaFree(c->rowloss); cudaFree(c->idx); cudaFree(c->parts);
     cudaError_t e = cudaSuccess;
     for (int l = 0; l <= NLAYER && e == cudaSuccess; l++)
-        e = cudaMalloc(&c->H[l], sizeof(float) * (size_t)cap * (l == 0 ? NIN : (l == NLAYER ? NOUT : NH)));
-    for (int l = 0; l < NLAYER && e == cudaSuccess; l++) e = cudaMalloc(&c->Z[l], sizeof(float) * (size_t)cap * kLayerOut[l]);
-    if (e == cudaSuccess) e = cudaMalloc(&c->T, sizeof(float) * (size_t)cap * NOUT);
-    if (e == cudaSuccess) e = cudaMalloc(&c->dA, sizeof(float) * (size_t)cap * NH);
-    if (e == cudaSuccess) e = cudaMalloc(&c->dB, sizeof(float) * (size_t)cap * NH);
-    if (e == cudaSuccess) e = cudaMalloc(&c->rowloss, sizeof(float) * (size_t)cap);
-    if (e == cudaSuccess) e = cudaMalloc(&c->idx, sizeof(long) * (size_t)cap);
+        e = dev_malloc(&c->H[l], sizeof(float) * (size_t)cap * (l == 0 ? NIN : (l == NLAYER ? NOUT : NH)));
+    for (int l = 0; l < NLAYER && e == cudaSuccess; l++) e = dev_malloc(&c->Z[l], sizeof(float) * (size_t)cap * kLayerOut[l]);
+    if (e == cudaSuccess) e = dev_malloc(&c->T, sizeof(float) * (size_t)cap * NOUT);
+    if (e == cudaSuccess) e = dev_malloc(&c->dA, sizeof(float) * (size_t)cap * NH);
+    if (e == cudaSuccess) e = dev_malloc(&c->dB, sizeof(float) * (size_t)cap * NH);
+    if (e == cudaSuccess) e = dev_malloc(&c->rowloss, sizeof(float) * (size_t)cap);
+    if (e == cudaSuccess) e = dev_malloc(&c->idx, sizeof(long) * (size_t)cap);
     c->parts_len = (size_t)kSplitK * NH * NH;
-    if (e == cudaSuccess) e = cudaMalloc(&c->parts, sizeof(float) * c->parts_len);
+    if (e == cudaSuccess) e = dev_malloc(&c->parts, sizeof(float) * c->parts_len);
     if (e != cudaSuccess) return cuda_fail(e, "closure work buffers");
     c->cap = cap;
     return EF_OK;
@@ -407,11 +407,11 @@ int ef_closure_create(const ef_closure_cfg *cfg, ef_closure **out)
     cudaError_t e = cudaSuccess;
     float **bufs[5] = {&c->w, &c->wq, &c->m, &c->v, &c->g};
     for (auto b : bufs)
-        if (e == cudaSuccess) e = cudaMalloc(b, sizeof(float) * c->nparam);
-    if (e == cudaSuccess) e = cudaMalloc(&c->stats, sizeof(double) * 32);
-    if (e == cudaSuccess) e = cudaMalloc(&c->nfall, 2 * sizeof(int));
+        if (e == cudaSuccess) e = dev_malloc(b, sizeof(float) * c->nparam);
+    if (e == cudaSuccess) e = dev_malloc(&c->stats, sizeof(double) * 32);
+    if (e == cudaSuccess) e = dev_malloc(&c->nfall, 2 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->nfall, 0, 2 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&c->image, closure_tc_image_bytes());
+    if (e == cudaSuccess) e = dev_malloc(&c->image, closure_tc_image_bytes());
     if (e == cudaSuccess) e = cudaMemset(c->w, 0, sizeof(float) * c->nparam);
     if (e == cudaSuccess) e = cudaMemset(c->m, 0, sizeof(float) * c->nparam);
     if (e == cudaSuccess) e = cudaMemset(c->v, 0, sizeof(float) * c->nparam);
@@ -448,7 +448,7 @@ int ef_closure_features(const ef_grid *les, const float *ubar, double re_tau, in
     if (les->nx < 2 || les->nz < 2 || les->ny < 3) { set_error("ef_closure_features: grid too small"); return EF_ERR_SHAPE; }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double *dY = nullptr;
-    cudaError_t e = cudaMallocAsync(&dY, sizeof(double) * les->ny, s);
+    cudaError_t e = dev_malloc_async(&dY, sizeof(double) * les->ny, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dY, les->y, sizeof(double) * les->ny, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "ef_closure_features");
     const int flip = extension == EF_EXT_ODD_EVEN;

@@ -619,13 +619,13 @@ int diff_setup_typed(ef_plan *p, DiffPlan *d)
     const auto twx = twiddles<C>(p->nx), twz = twiddles<C>(p->nz);
     cudaError_t e = cudaSuccess;
 #define DK(x) if (e == cudaSuccess) e = (x)
-    DK(cudaMalloc(&d->twx, sizeof(C) * p->nx));
-    DK(cudaMalloc(&d->twz, sizeof(C) * p->nz));
-    DK(cudaMalloc(&d->spec, sizeof(C) * nspec * d->group));
-    DK(cudaMalloc(&d->fcp, sizeof(R) * 2 * nspec));
-    DK(cudaMalloc(&d->finv, sizeof(R) * 2 * nspec));
-    DK(cudaMalloc(&d->lesz, sizeof(C) * (size_t)p->nly * p->nlz * d->nxh * d->group));
-    DK(cudaMalloc(&d->fld, sizeof(R) * d->nfield * nles));
+    DK(dev_malloc(&d->twx, sizeof(C) * p->nx));
+    DK(dev_malloc(&d->twz, sizeof(C) * p->nz));
+    DK(dev_malloc(&d->spec, sizeof(C) * nspec * d->group));
+    DK(dev_malloc(&d->fcp, sizeof(R) * 2 * nspec));
+    DK(dev_malloc(&d->finv, sizeof(R) * 2 * nspec));
+    DK(dev_malloc(&d->lesz, sizeof(C) * (size_t)p->nly * p->nlz * d->nxh * d->group));
+    DK(dev_malloc(&d->fld, sizeof(R) * d->nfield * nles));
     DK(cudaMemcpy(d->twx, twx.data(), sizeof(C) * p->nx, cudaMemcpyHostToDevice));
     DK(cudaMemcpy(d->twz, twz.data(), sizeof(C) * p->nz, cudaMemcpyHostToDevice));
     const int zsm = (int)(2 * sizeof(C) * (size_t)p->nz * d->zcols);
@@ -641,10 +641,10 @@ int diff_setup_typed(ef_plan *p, DiffPlan *d)
         e = cudaGetLastError();
     }
     if (d->fp32) {
-        DK(cudaMalloc(&d->U, sizeof(double) * 3 * ny));
-        DK(cudaMalloc(&d->FU, sizeof(double) * 3 * p->nly));
-        DK(cudaMalloc(&d->FUU, sizeof(double) * 6 * p->nly));
-        DK(cudaMalloc(&d->pscr, sizeof(double) * 18 * ny));
+        DK(dev_malloc(&d->U, sizeof(double) * 3 * ny));
+        DK(dev_malloc(&d->FU, sizeof(double) * 3 * p->nly));
+        DK(dev_malloc(&d->FUU, sizeof(double) * 6 * p->nly));
+        DK(dev_malloc(&d->pscr, sizeof(double) * 18 * ny));
     }
     DK(cudaDeviceSynchronize());
 #undef DK
@@ -786,10 +786,10 @@ int diff_setup(ef_plan *p, const double *dns_y, const double *les_y)
         dyy[ny + j] = ce;
         dyy[2 * ny + j] = up;
     }
-    cudaError_t e = cudaMalloc(&d->k2x, sizeof(double) * d->nxh);
-    if (e == cudaSuccess) e = cudaMalloc(&d->k2z, sizeof(double) * p->nz);
-    if (e == cudaSuccess) e = cudaMalloc(&d->dyy, sizeof(double) * dyy.size());
-    if (e == cudaSuccess) e = cudaMalloc(&d->jy, sizeof(int) * p->nly);
+    cudaError_t e = dev_malloc(&d->k2x, sizeof(double) * d->nxh);
+    if (e == cudaSuccess) e = dev_malloc(&d->k2z, sizeof(double) * p->nz);
+    if (e == cudaSuccess) e = dev_malloc(&d->dyy, sizeof(double) * dyy.size());
+    if (e == cudaSuccess) e = dev_malloc(&d->jy, sizeof(int) * p->nly);
     if (e == cudaSuccess) e = cudaMemcpy(d->k2x, k2x.data(), sizeof(double) * d->nxh, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d->k2z, k2z.data(), sizeof(double) * p->nz, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d->dyy, dyy.data(), sizeof(double) * dyy.size(), cudaMemcpyHostToDevice);
@@ -863,7 +863,7 @@ extern "C" int ef_differential_unfilter(const ef_grid *g, double delta, int exte
     if (g->nx < 3 || g->nz < 3 || g->ny < 3) { set_error("ef_differential_unfilter: grid too small"); return EF_ERR_SHAPE; }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double *dy = nullptr;
-    cudaError_t e = cudaMallocAsync(&dy, sizeof(double) * g->ny, s);
+    cudaError_t e = dev_malloc_async(&dy, sizeof(double) * g->ny, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dy, g->y, sizeof(double) * g->ny, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "ef_differential_unfilter");
     const double hx = g->Lx / g->nx, hz = g->Lz / g->nz, a2 = delta * delta / 40.0;

@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <vector>
 
 #include "eles_internal.h"
@@ -19,6 +20,29 @@ void set_error(const char *fmt, ...)
     va_start(ap, fmt);
     vsnprintf(g_msg, sizeof g_msg, fmt, ap);
     va_end(ap);
+}
+
+static std::atomic<int> g_fail_alloc{-1};   // allocations to let through before one fails (-1: none fails)
+
+static bool alloc_should_fail()
+{
+    int n = g_fail_alloc.load();
+    while (n >= 0) {
+        if (g_fail_alloc.compare_exchange_weak(n, n - 1)) return n == 0;
+    }
+    return false;
+}
+
+cudaError_t dev_malloc_void(void **p, size_t bytes)
+{
+    if (alloc_should_fail()) { *p = nullptr; return cudaErrorMemoryAllocation; }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t dev_malloc_async_void(void **p, size_t bytes, cudaStream_t s)
+{
+    if (alloc_should_fail()) { *p = nullptr; return cudaErrorMemoryAllocation; }
+    return cudaMallocAsync(p, bytes, s);
 }
 
 int cuda_fail(cudaError_t e, const char *what)
@@ -128,7 +152,7 @@ int plan_reserve(ef_plan *p, int nsnap)
     };
     for (auto &r : req) {
         if (!r.bytes) continue;
-        e = cudaMalloc(r.ptr, r.bytes);
+        e = dev_malloc(r.ptr, r.bytes);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc scratch");
     }
     p->reserve = nsnap;
@@ -143,7 +167,21 @@ extern "C" {
 
 const char *ef_last_error(void) { return g_msg; }
 
-const char *ef_version(void) { return "eles-gb300 0.1 (sm_103a)"; }
+const char *ef_version(void)
+{
+#ifdef ELES_CHECK
+    return "eles-gb300 0.2 (sm_103a, range-checked build)";
+#else
+    return "eles-gb300 0.2 (sm_103a)";
+#endif
+}
+
+int ef_debug_fail_alloc(int n)
+{
+    if (n < -1) { set_error("ef_debug_fail_alloc: n must be >= -1"); return EF_ERR_ARG; }
+    g_fail_alloc.store(n);
+    return EF_OK;
+}
 
 void ef_plan_destroy(ef_plan *p)
 {
@@ -222,11 +260,11 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
     if (differential) {
         if ((rc = diff_setup(p, dns->y, les->y))) goto fail;
         p->reserve = 1;
-        CK(cudaMalloc(&p->d_err, sizeof(int)), "cudaMalloc error word");
+        CK(dev_malloc(&p->d_err, sizeof(int)), "cudaMalloc error word");
         CK(cudaMemset(p->d_err, 0, sizeof(int)), "clear error word");
         CK(cudaDeviceSynchronize(), "setup");
     } else {
-        CK(cudaMalloc(&p->d_ygrid, sizeof(double) * p->ny), "cudaMalloc y");
+        CK(dev_malloc(&p->d_ygrid, sizeof(double) * p->ny), "cudaMalloc y");
         CK(cudaMemcpy(p->d_ygrid, dns->y, sizeof(double) * p->ny, cudaMemcpyHostToDevice), "copy y");
         if ((rc = build_periodic_band(p->nx, p->Lx, p->nlx, delta, &p->bx))) goto fail;
         if ((rc = build_periodic_band(p->nz, p->Lz, p->nlz, delta, &p->bz))) goto fail;
@@ -269,7 +307,7 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
                     p->tc.KS = KS;
                     p->tc.zoff = zoff;
                     if (KS > 0) {
-                        CK(cudaMalloc(&p->d_zfrag, sizeof(unsigned) * zf.size()), "cudaMalloc z fragments");
+                        CK(dev_malloc(&p->d_zfrag, sizeof(unsigned) * zf.size()), "cudaMalloc z fragments");
                         CK(cudaMemcpy(p->d_zfrag, zf.data(), sizeof(unsigned) * zf.size(), cudaMemcpyHostToDevice),
                            "copy z fragments");
                         p->tc.afrag = p->d_zfrag;
@@ -293,7 +331,7 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
         }
         p->nzw = (p->nz + 31) / 32;
         if ((rc = plan_reserve(p, 1))) goto fail;
-        CK(cudaMalloc(&p->d_err, sizeof(int)), "cudaMalloc error word");
+        CK(dev_malloc(&p->d_err, sizeof(int)), "cudaMalloc error word");
         CK(cudaMemset(p->d_err, 0, sizeof(int)), "clear error word");
         CK(cudaDeviceSynchronize(), "setup");
     }

@@ -132,6 +132,7 @@ struct YTcArgs {
     float *tmp;                    // [S][kYTmp][nly][nplane]
     int ny, nly, nplane, stress, flip;
     int nlz, nlx, ptrans;          // ptrans: h planes in (X, Z) order; outputs are written in (Z, X) order
+    int nsnap;                     // snapshots of the launch (range checks)
     int *err;
 };
 bool ytc_geometry(const std::vector<int> &ystart, const std::vector<int> &ycount, int ny, int nplane, YTcGeom *g);
@@ -215,6 +216,32 @@ struct ef_plan {
 };
 
 namespace eles {
+
+// Every device allocation of the library goes through these, so that a test
+// hook (ef_debug_fail_alloc) can make the n-th next one fail.
+cudaError_t dev_malloc_void(void **p, size_t bytes);
+cudaError_t dev_malloc_async_void(void **p, size_t bytes, cudaStream_t s);
+template <typename T>
+inline cudaError_t dev_malloc(T **p, size_t bytes) { return dev_malloc_void(reinterpret_cast<void **>(p), bytes); }
+template <typename T>
+inline cudaError_t dev_malloc_async(T **p, size_t bytes, cudaStream_t s)
+{
+    return dev_malloc_async_void(reinterpret_cast<void **>(p), bytes, s);
+}
+
+// Range checks of global indices in the debug build (-DELES_CHECK): a
+// violation records EF_ERR_RANGE in the error word and the access is skipped;
+// nothing traps.  In the normal build the check is the constant true.
+#ifdef ELES_CHECK
+__device__ __forceinline__ bool in_range(size_t i, size_t n, int *err)
+{
+    if (i < n) return true;
+    if (err) atomicCAS(err, 0, (int)EF_ERR_RANGE);
+    return false;
+}
+#else
+__device__ __forceinline__ constexpr bool in_range(size_t, size_t, int *) { return true; }
+#endif
 
 void set_error(const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);

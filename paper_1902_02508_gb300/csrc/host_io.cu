@@ -62,10 +62,10 @@ int ef_io_create(ef_plan *p, int chunk, ef_io **out)
     const size_t nl = (size_t)p->nlx * p->nly * p->nlz * chunk;
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 2 && e == cudaSuccess; k++) {
-        e = cudaMalloc(&io->u[k], nu);
-        if (e == cudaSuccess) e = cudaMalloc(&io->ubar[k], es * 3 * nl);
-        if (e == cudaSuccess) e = cudaMalloc(&io->tau[k], es * 6 * nl);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&io->pm[k], sizeof(double) * 3 * p->ny * chunk);
+        e = dev_malloc(&io->u[k], nu);
+        if (e == cudaSuccess) e = dev_malloc(&io->ubar[k], es * 3 * nl);
+        if (e == cudaSuccess) e = dev_malloc(&io->tau[k], es * 6 * nl);
+        if (e == cudaSuccess) e = dev_malloc((void **)&io->pm[k], sizeof(double) * 3 * p->ny * chunk);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io->ev_in[k], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io->ev_comp[k], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io->ev_out[k], cudaEventDisableTiming);

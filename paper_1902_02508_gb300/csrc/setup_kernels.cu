@@ -195,9 +195,9 @@ int build_periodic_band(int n, double L, int nl, double delta, Band *b)
     int T = 2 * K + 2;
     b->n = n; b->nl = nl; b->T = T;
     cudaError_t e;
-    if ((e = cudaMalloc(&b->d_start, sizeof(int) * nl)) != cudaSuccess) return cuda_fail(e, "cudaMalloc band");
-    if ((e = cudaMalloc(&b->d_w64, sizeof(double) * (size_t)nl * T)) != cudaSuccess) return cuda_fail(e, "cudaMalloc band");
-    if ((e = cudaMalloc(&b->d_w32, sizeof(float) * (size_t)nl * T)) != cudaSuccess) return cuda_fail(e, "cudaMalloc band");
+    if ((e = dev_malloc(&b->d_start, sizeof(int) * nl)) != cudaSuccess) return cuda_fail(e, "cudaMalloc band");
+    if ((e = dev_malloc(&b->d_w64, sizeof(double) * (size_t)nl * T)) != cudaSuccess) return cuda_fail(e, "cudaMalloc band");
+    if ((e = dev_malloc(&b->d_w32, sizeof(float) * (size_t)nl * T)) != cudaSuccess) return cuda_fail(e, "cudaMalloc band");
     periodic_rows_kernel<<<(nl + 127) / 128, 128>>>(n, L, nl, delta, K, T, b->d_start, b->d_w64, b->d_w32);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "periodic_rows_kernel");
     return EF_OK;
@@ -241,15 +241,15 @@ int build_wall_rows(ef_plan *p, const double *h_les_y)
     cudaError_t e;
     double *dY = nullptr;
     size_t dense = (size_t)p->nly * p->ny;
-    if ((e = cudaMalloc(&dY, sizeof(double) * p->nly)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = dev_malloc(&dY, sizeof(double) * p->nly)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     e = cudaMemcpy(dY, h_les_y, sizeof(double) * p->nly, cudaMemcpyHostToDevice);
     for (int q = 0; q < 2 && e == cudaSuccess; q++) {
-        e = cudaMalloc(&p->d_yw64[q], sizeof(double) * dense);
-        if (e == cudaSuccess) e = cudaMalloc(&p->d_yw32[q], sizeof(float) * dense);
+        e = dev_malloc(&p->d_yw64[q], sizeof(double) * dense);
+        if (e == cudaSuccess) e = dev_malloc(&p->d_yw32[q], sizeof(float) * dense);
         if (e == cudaSuccess) e = cudaMemset(p->d_yw64[q], 0, sizeof(double) * dense);
     }
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_ystart, sizeof(int) * p->nly);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_ycount, sizeof(int) * p->nly);
+    if (e == cudaSuccess) e = dev_malloc(&p->d_ystart, sizeof(int) * p->nly);
+    if (e == cudaSuccess) e = dev_malloc(&p->d_ycount, sizeof(int) * p->nly);
     if (e != cudaSuccess) { cudaFree(dY); return cuda_fail(e, "allocate y operator"); }
     int truncated = (p->ext == EF_EXT_NONE) ? 1 : 0;
     wall_rows_kernel<<<(p->nly + 63) / 64, 64>>>(p->d_ygrid, p->ny, dY, p->nly, p->delta, truncated, p->yquad,

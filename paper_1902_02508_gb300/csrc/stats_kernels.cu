@@ -163,9 +163,9 @@ int ef_stats_create(const ef_grid *g, int precision, ef_stats **out)
     }
     ef_stats *st = new ef_stats();
     st->nx = g->nx; st->ny = ny; st->nz = g->nz; st->prec = precision;
-    cudaError_t e = cudaMalloc(&st->d_wy, sizeof(double) * ny);
-    if (e == cudaSuccess) e = cudaMalloc(&st->d_wh, sizeof(double) * ny);
-    if (e == cudaSuccess) e = cudaMalloc(&st->d_part, sizeof(double) * 2 * kStatBlocks);
+    cudaError_t e = dev_malloc(&st->d_wy, sizeof(double) * ny);
+    if (e == cudaSuccess) e = dev_malloc(&st->d_wh, sizeof(double) * ny);
+    if (e == cudaSuccess) e = dev_malloc(&st->d_part, sizeof(double) * 2 * kStatBlocks);
     if (e == cudaSuccess) e = cudaMemcpy(st->d_wy, wy.data(), sizeof(double) * ny, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(st->d_wh, wh.data(), sizeof(double) * ny, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {

@@ -79,14 +79,18 @@ double bweight(const Ring &r, int xi, int n, int xc0, int OP, int bshift)
 
 // Reference profile U_c(y_j): the mean of z-row 0 of each plane, one warp
 // per (component, plane, snapshot), FP64 sum.
-__global__ void __launch_bounds__(96) ws_uref(const float *__restrict__ u, int nx, int ny, int nz, double *uref)
+__global__ void __launch_bounds__(96) ws_uref(const float *__restrict__ u, int nx, int ny, int nz, double *uref,
+                                               int *err)
 {
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31, j = blockIdx.x, s = blockIdx.y;
-    const float *r0 = u + (((size_t)s * 3 + c) * ny + j) * (size_t)nz * nx;
+    const size_t r0 = (((size_t)s * 3 + c) * ny + j) * (size_t)nz * nx;
+    const size_t nu = (size_t)gridDim.y * 3 * ny * nz * nx;
     double acc = 0.0;
-    for (int i = lane; i < nx; i += 32) acc += (double)r0[i];
+    for (int i = lane; i < nx; i += 32)
+        if (in_range(r0 + i, nu, err)) acc += (double)u[r0 + i];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) uref[((size_t)s * 3 + c) * ny + j] = (double)(float)(acc / nx);
+    const size_t k = ((size_t)s * 3 + c) * ny + j;
+    if (lane == 0 && in_range(k, (size_t)gridDim.y * 3 * ny, err)) uref[k] = (double)(float)(acc / nx);
 }
 
 }  // namespace
@@ -245,11 +249,11 @@ int ws_setup(ef_plan *p, const char **why)
                 }
             }
     cudaError_t e;
-    if ((e = cudaMalloc(&w.d_afrag, sizeof(unsigned) * zf.size())) != cudaSuccess)
+    if ((e = dev_malloc(&w.d_afrag, sizeof(unsigned) * zf.size())) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc z fragments");
     if ((e = cudaMemcpy(w.d_afrag, zf.data(), sizeof(unsigned) * zf.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "copy z fragments");
-    if ((e = cudaMalloc(&w.d_bvar, sizeof(unsigned) * bv.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc x fragments");
+    if ((e = dev_malloc(&w.d_bvar, sizeof(unsigned) * bv.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc x fragments");
     if ((e = cudaMemcpy(w.d_bvar, bv.data(), sizeof(unsigned) * bv.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "copy x fragments");
     w.mode = mode;
@@ -288,7 +292,7 @@ static int ws_prepare(const ef_plan *p, int nsnap, const float *u, float *h, dou
     int rc = encode_u_map(u, p->nx, p->ny, p->nz, nsnap, ws::CW, a->box_rows, &a->tmap);
     if (rc) return rc;
     // the reference profile first (1/nz of a plane read), then the persistent kernel
-    ws_uref<<<dim3(p->ny, nsnap), 96, 0, st>>>(u, p->nx, p->ny, p->nz, uref);
+    ws_uref<<<dim3(p->ny, nsnap), 96, 0, st>>>(u, p->nx, p->ny, p->nz, uref, p->d_err);
     a->u = u; a->h = h; a->uref = uref; a->plane_mean = plane_mean; a->err = p->d_err;
     a->nx = p->nx; a->ny = p->ny; a->nz = p->nz; a->nlx = p->nlx; a->nlz = p->nlz;
     a->nchunk = w.nchunk; a->bshift = w.bshift; a->rx = p->rx.r; a->CB = w.CB; a->OP = w.OP;

@@ -294,10 +294,13 @@ __device__ __forceinline__ void z_tile(const WsArgs &a, const float *colb, const
             const int n = cc >= NF ? 1 : 0, f = cc - n * NF;
             if (f >= a.nf || !(n ? val1 : val0)) continue;
             // h plane in (X, Z) order, Z fastest: the 8 rows g of a store are contiguous
-            float *hout = a.h + (((size_t)s * NF + f) * a.ny + j) * ((size_t)a.nlz * a.nlx) +
-                          (size_t)(X0 + a.OP * n) * a.nlz + 16 * zt;
-            hout[g] = (acc[i][0][e] + acc[i][1][e]) + acc[i][2][e];
-            hout[g + 8] = (acc[i][0][2 + e] + acc[i][1][2 + e]) + acc[i][2][2 + e];
+            const size_t o = (((size_t)s * NF + f) * a.ny + j) * ((size_t)a.nlz * a.nlx) +
+                             (size_t)(X0 + a.OP * n) * a.nlz + 16 * zt;
+            const size_t nh = (size_t)a.nsnap * NF * a.ny * a.nlz * a.nlx;
+            if (in_range(o + g + 8, nh, a.err)) {
+                a.h[o + g] = (acc[i][0][e] + acc[i][1][e]) + acc[i][2][e];
+                a.h[o + g + 8] = (acc[i][0][2 + e] + acc[i][1][2 + e]) + acc[i][2][2 + e];
+            }
         }
 }
 
@@ -414,7 +417,10 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
         auto uref_of = [&](int it, float (&U)[3]) {
             const int j = (it / a.OP) % a.ny, s = it / (a.OP * a.ny);
 #pragma unroll
-            for (int c = 0; c < 3; c++) U[c] = it < nitems ? (float)a.uref[((size_t)s * 3 + c) * a.ny + j] : 0.f;
+            for (int c = 0; c < 3; c++) {
+                const size_t k = ((size_t)s * 3 + c) * a.ny + j;
+                U[c] = it < nitems && in_range(k, (size_t)a.nsnap * 3 * a.ny, a.err) ? (float)a.uref[k] : 0.f;
+            }
         };
         float Un[3];
         uref_of(cta, Un);
@@ -579,10 +585,9 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
         if (stop) break;
         if (pm && zw < 3) {
             for (int o = 16; o > 0; o >>= 1) pmean += __shfl_xor_sync(0xffffffffu, pmean, o);
-            if (lane == 0) {
-                const size_t k = ((size_t)s * 3 + zw) * a.ny + j;
+            const size_t k = ((size_t)s * 3 + zw) * a.ny + j;
+            if (lane == 0 && in_range(k, (size_t)a.nsnap * 3 * a.ny, a.err))
                 a.plane_mean[k] = (double)(float)a.uref[k] + pmean / ((double)a.nx * NZ);
-            }
         }
     }
 }

@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(YT) ypass_kernel(const __grid_constant__ YArgs
             for (int c = 0; c < 3; c++) {
                 const double v = AU[c * a.nly + J] + (double)q[b][c];
                 bad |= !isfinite(v);
-                a.ubar[((size_t)s * 3 + c) * nl + oo] = (T)v;
+                if (in_range(((size_t)s * 3 + c) * nl + oo, (size_t)gridDim.z * 3 * nl, a.err))
+                    a.ubar[((size_t)s * 3 + c) * nl + oo] = (T)v;
             }
             if (cross) {
 #pragma unroll
@@ -207,7 +208,8 @@ __global__ void __launch_bounds__(YT) ypass_kernel(const __grid_constant__ YArgs
                 const double v = (AUU[k * a.nly + J] - Ai * Am) + (Cim - Ai * qv[m])
                                + (Cmi - Am * qv[i]) + ((double)q[b][k] - qv[i] * qv[m]);
                 bad |= !isfinite(v);
-                a.tau[((size_t)s * 6 + k) * nl + oo] = (T)v;
+                if (in_range(((size_t)s * 6 + k) * nl + oo, (size_t)gridDim.z * 6 * nl, a.err))
+                    a.tau[((size_t)s * 6 + k) * nl + oo] = (T)v;
             }
         }
     }

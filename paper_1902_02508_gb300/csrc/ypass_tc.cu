@@ -212,12 +212,16 @@ __global__ void __launch_bounds__(YTW * 32, 5) ytc_kernel(const __grid_constant_
                     if (p >= nplane) continue;
                     float *tmp = a.tmp + (size_t)s * kYTmp * nl + o0 + p;
                     const float v = acc[n][2 * hr + e];
+                    if (!in_range((size_t)s * kYTmp * nl + o0 + p + (size_t)(kYTmp - 1) * nl, (size_t)a.nsnap * kYTmp * nl,
+                                  a.err))
+                        continue;
                     if constexpr (NOPS == 5) {
                         if (o == 0) {
                             const float ub = (float)a.AU[((size_t)s * 3 + F) * a.nly + J] + v;
                             bad |= !isfinite(ub);
                             const int po = a.ptrans ? (p % a.nlz) * a.nlx + p / a.nlz : p;
-                            a.ubar[((size_t)s * 3 + F) * nl + o0 + po] = ub;
+                            if (in_range(((size_t)s * 3 + F) * nl + o0 + po, (size_t)a.nsnap * 3 * nl, a.err))
+                                a.ubar[((size_t)s * 3 + F) * nl + o0 + po] = ub;
                         }
                         if (a.stress) {
                             const int slot = o == 0 ? F : o == 1 ? 12 + F : 3 + 3 * (o - 2) + F;
@@ -287,7 +291,8 @@ __global__ void yrecover_kernel(const __grid_constant__ YTcArgs a, int nsnap)
     float out[6];
     const bool bad = recover_point(a, s, J, r - (size_t)J * a.nplane, out);
 #pragma unroll
-    for (int k = 0; k < 6; k++) a.tau[((size_t)s * 6 + k) * nl + r] = out[k];
+    for (int k = 0; k < 6; k++)
+        if (in_range(((size_t)s * 6 + k) * nl + r, (size_t)nsnap * 6 * nl, a.err)) a.tau[((size_t)s * 6 + k) * nl + r] = out[k];
     if (bad && a.err) atomicCAS(a.err, 0, (int)EF_ERR_NAN);
 }
 
@@ -315,8 +320,10 @@ __global__ void __launch_bounds__(256) yrecover_t_kernel(const __grid_constant__
         const int Z = Z0 + ty, X = X0 + tx;
         if (X < a.nlx && Z < a.nlz) {
 #pragma unroll
-            for (int k = 0; k < 6; k++)
-                a.tau[((size_t)s * 6 + k) * nl + (size_t)J * a.nplane + (size_t)Z * a.nlx + X] = tile[k][ty][tx];
+            for (int k = 0; k < 6; k++) {
+                const size_t o = ((size_t)s * 6 + k) * nl + (size_t)J * a.nplane + (size_t)Z * a.nlx + X;
+                if (in_range(o, (size_t)a.nsnap * 6 * nl, a.err)) a.tau[o] = tile[k][ty][tx];
+            }
         }
     }
     if (bad && a.err) atomicCAS(a.err, 0, (int)EF_ERR_NAN);
@@ -412,14 +419,18 @@ int encode_h_map(const float *h, int nplane, int ny, int nsnap, int box_rows, CU
 
 cudaError_t launch_ytc(const YTcArgs &a, int nsnap, cudaStream_t st)
 {
-    cudaError_t e = launch_part<5, 4>(a, nsnap, 3, st);
+    YTcArgs c = a;
+    c.nsnap = nsnap;
+    cudaError_t e = launch_part<5, 4>(c, nsnap, 3, st);
     if (e != cudaSuccess || !a.stress) return e;
-    if ((e = launch_part<1, 2>(a, nsnap, 6, st)) != cudaSuccess) return e;
+    if ((e = launch_part<1, 2>(c, nsnap, 6, st)) != cudaSuccess) return e;
+    YTcArgs b = a;
+    b.nsnap = nsnap;
     if (a.ptrans) {
-        yrecover_t_kernel<<<dim3((a.nlx + 15) / 16, (a.nlz + 15) / 16, a.nly * nsnap), 256, 0, st>>>(a);
+        yrecover_t_kernel<<<dim3((a.nlx + 15) / 16, (a.nlz + 15) / 16, a.nly * nsnap), 256, 0, st>>>(b);
     } else {
         const size_t n = (size_t)a.nly * a.nplane * nsnap;
-        yrecover_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, nsnap);
+        yrecover_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(b, nsnap);
     }
     return cudaGetLastError();
 }

@@ -17,11 +17,12 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libeles.so")
+LIB_PATH = (os.path.join(_HERE, "_lib_check", "libeles_check.so") if os.environ.get("ELES_CHECK") == "1"
+            else os.path.join(_HERE, "_lib", "libeles.so"))
 
 EF_OK = 0
 STATUS = {0: "EF_OK", 1: "EF_ERR_ARG", 2: "EF_ERR_SHAPE", 3: "EF_ERR_CUDA", 4: "EF_ERR_NAN",
-          5: "EF_ERR_TIMEOUT", 6: "EF_ERR_OOM", 7: "EF_ERR_UNSUPPORTED"}
+          5: "EF_ERR_TIMEOUT", 6: "EF_ERR_OOM", 7: "EF_ERR_UNSUPPORTED", 8: "EF_ERR_RANGE"}
 KERNEL_GAUSSIAN = 0
 KERNEL_GAUSSIAN_HAT = 1      # y integral exact against the piecewise-linear interpolant
 KERNEL_DIFFERENTIAL = 2      # (1 - a^2 lap) ubar = u, a^2 = delta^2 / 40 (FP64)
@@ -35,7 +36,7 @@ EXPORTED = ("ef_filter_setup", "ef_plan_destroy", "ef_filter_fields", "ef_subfil
             "ef_check_device_error", "ef_plan_info", "ef_plan_weights", "ef_profile_enable",
             "ef_profile_read", "ef_last_error", "ef_version", "ef_closure_create", "ef_closure_destroy",
             "ef_closure_features", "ef_closure_fit_norm", "ef_closure_train", "ef_closure_infer",
-            "ef_closure_infer_exact", "ef_plan_set_wait_limit",
+            "ef_closure_infer_exact", "ef_plan_set_wait_limit", "ef_debug_fail_alloc",
             "ef_closure_gradients", "ef_closure_param_count", "ef_closure_get_params", "ef_closure_set_params",
             "ef_closure_save", "ef_closure_load", "ef_batch_create", "ef_batch_run", "ef_batch_destroy",
             "ef_batch_captures", "ef_plan_autotune", "ef_plan_set_variant", "ef_closure_features_static", "ef_io_create",
@@ -116,6 +117,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             lib.ef_closure_infer_exact.restype = i
             lib.ef_plan_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
             lib.ef_plan_set_wait_limit.restype = i
+            lib.ef_debug_fail_alloc.argtypes = [i]
+            lib.ef_debug_fail_alloc.restype = i
             lib.ef_selftest_wait.argtypes = [vp, ctypes.c_longlong, i, vp]
             lib.ef_selftest_wait.restype = i
             lib.ef_differential_unfilter.argtypes = [ctypes.POINTER(_Grid), d, i, vp, vp, vp]
@@ -263,6 +266,11 @@ def subfilter_stress_batch(plan: Plan, u, ubar, tau, plane_mean=None, stream=Non
 
 def plan_reserve(plan: Plan, max_snapshots: int) -> None:
     _check(load().ef_plan_reserve(plan.handle, int(max_snapshots)))
+
+
+def debug_fail_alloc(n: int) -> None:
+    """Make the n-th device allocation of the library from now fail (-1: off)."""
+    _check(load().ef_debug_fail_alloc(int(n)))
 
 
 def plan_set_wait_limit(plan: Plan, cycles: int) -> None:
