@@ -142,7 +142,10 @@ __device__ __forceinline__ void zphase(const FusedArgs &a, const float *colbuf, 
 // (32 bytes) of every row, one box per component and row half, completion on
 // an mbarrier per stage.  Every wait is bounded: on expiry the kernel records
 // EF_ERR_TIMEOUT and carries on (the results are then garbage, but nothing
-// hangs).
+// hangs).  A stage whose wait ran out may still be landing afterwards: the
+// kernels that use these stages wait once more, with the same bound, for every
+// stage they issued before the CTA exits, so no bulk copy outlives its CTA
+// unless it never completes at all.
 namespace eles {
 namespace fz {
 

@@ -291,6 +291,10 @@ __global__ void __launch_bounds__(kFusedMaxRows) xz_fused_tc(const __grid_consta
                                        stage_x(k), pc0, a.ny);
         }
     }
+    // no bulk copy may outlive the CTA: the last stages issued (a wait that
+    // ran out above may have left one landing)
+    if (tid == 0)
+        for (int k = nts > TSTG ? nts - TSTG : 0; k < nts; k++) mbar_wait(&full[k % TSTG], (k / TSTG) & 1, a.err);
     if (a.plane_mean) {
         double d[3] = {psum[0], psum[1], psum[2]};
         for (int o = 16; o > 0; o >>= 1)
