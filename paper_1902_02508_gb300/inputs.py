@@ -86,7 +86,12 @@ def _modes(nx: int, nz: int):
 
 
 def fluctuation(grid: Grid, seed: int, rms: float = RMS) -> np.ndarray:
-    """Solenoidal, no-slip random field u'[3][ny][nz][nx] with the stated rms."""
+    """Solenoidal, no-slip random field u'[3][ny][nz][nx] with the stated rms.
+
+    u' = curl psi with psi = sum_m (1 - y^2)^2 (a_m + b_m y) e^{i(k_x x + k_z z)}
+    (real part).  Every mode has the same four y shapes, P, P y, P' and P' y
+    with P = (1 - y^2)^2, so each component is four x-z fields (one inverse
+    FFT each) weighted by those shapes at every y node."""
     nx, ny, nz = grid.nx, grid.ny, grid.nz
     rng = np.random.Generator(np.random.PCG64(seed))
     MX, MZ = _modes(nx, nz)
@@ -97,25 +102,33 @@ def fluctuation(grid: Grid, seed: int, rms: float = RMS) -> np.ndarray:
     amp = kmag ** (-7.0 / 3.0)
     a = (rng.standard_normal((3, nm)) + 1j * rng.standard_normal((3, nm))) * amp
     b = (rng.standard_normal((3, nm)) + 1j * rng.standard_normal((3, nm))) * amp
-    ix = np.mod(MX, nx)
-    iz = np.mod(MZ, nz)
-    out = np.empty((3, ny, nz, nx), dtype=np.float64)
-    for j in range(ny):
-        yv = grid.y[j]
-        P = (1.0 - yv * yv) ** 2
-        dP = -4.0 * yv * (1.0 - yv * yv)
-        psi = P * (a + b * yv)                     # (3, nm)
-        dpsi = dP * (a + b * yv) + P * b           # d/dy
-        ik_x, ik_z = 1j * kx, 1j * kz
-        uh = np.empty((3, nm), dtype=np.complex128)
-        uh[0] = dpsi[2] - ik_z * psi[1]
-        uh[1] = ik_z * psi[0] - ik_x * psi[2]
-        uh[2] = ik_x * psi[1] - dpsi[0]
-        spec = np.zeros((3, nz, nx), dtype=np.complex128)
-        # f = Re sum_m c_m e^{i theta} = sum_m (c_m e^{i theta} + conj(c_m) e^{-i theta}) / 2
-        np.add.at(spec, (slice(None), iz, ix), 0.5 * uh)
-        np.add.at(spec, (slice(None), np.mod(-MZ, nz), np.mod(-MX, nx)), 0.5 * np.conj(uh))
-        out[:, j] = np.fft.ifft2(spec, axes=(-2, -1)).real * (nx * nz)
+    ik_x, ik_z = 1j * kx, 1j * kz
+    # u'_hat = sum_s f_s(y) C[c][s] with f = (P, P y, P', P' y), from
+    # psi = P a + P y b and dpsi/dy = P' a + (P' y + P) b:
+    #   u'_hat_0 = dpsi_2/dy - i k_z psi_1
+    #   u'_hat_1 = i k_z psi_0 - i k_x psi_2
+    #   u'_hat_2 = i k_x psi_1 - dpsi_0/dy
+    zero = np.zeros(nm, dtype=np.complex128)
+    C = [[b[2] - ik_z * a[1], -ik_z * b[1], a[2], b[2]],
+         [ik_z * a[0] - ik_x * a[2], ik_z * b[0] - ik_x * b[2], zero, zero],
+         [ik_x * a[1] - b[0], ik_x * b[1], -a[0], -b[0]]]
+    ix, iz = np.mod(MX, nx), np.mod(MZ, nz)
+    jx, jz = np.mod(-MX, nx), np.mod(-MZ, nz)
+    y = grid.y
+    P = (1.0 - y * y) ** 2
+    dP = -4.0 * y * (1.0 - y * y)
+    shapes = (P, P * y, dP, dP * y)
+    out = np.zeros((3, ny, nz, nx), dtype=np.float64)
+    for c in range(3):
+        for sh in range(4):
+            if not np.any(C[c][sh]):
+                continue
+            # f = Re sum_m c_m e^{i theta} = sum_m (c_m e^{i theta} + conj(c_m) e^{-i theta}) / 2
+            spec = np.zeros((nz, nx), dtype=np.complex128)
+            np.add.at(spec, (iz, ix), 0.5 * C[c][sh])
+            np.add.at(spec, (jz, jx), 0.5 * np.conj(C[c][sh]))
+            F = np.fft.ifft2(spec).real * (nx * nz)
+            out[c] += shapes[sh][:, None, None] * F[None]
     scale = rms / math.sqrt(float(np.mean(out * out)))
     out *= scale
     return out
