@@ -18,10 +18,11 @@ inputs and outputs, the copies in and out overlapped with the compute of
 other snapshots) inside the timed region.  `roofline` reports the
 x-contraction kernel (the dominant phase) against the measured HBM copy
 bandwidth.  `cpu_baseline` times the CPU oracle on a bounded sample.
-`closure` reports the learned closure on the same workload: trained on the
-exact T_ij of snapshot 0, its error against the exact T_ij of snapshot 1 (a
-field of another seed), and tensor-core inference on 2^20 LES points with its
-roofline against the measured bf16 tensor peak.  `differential` times the
+`closure` reports the learned closure in its own configuration: trained on the
+exact T_ij of 32 seeded 256 x 193 x 256 snapshots filtered to 64 x 65 x 48 at
+Delta = Lx / 32, its error per component on two held-out seeds beside the
+gradient model's, the training rate, and tensor-core inference on 2^20 LES
+points with its roofline.  `differential` times the
 paper's own filter (Sec. 3, a = 0.1) on one snapshot in FP64 against the FP64
 arithmetic bound.  `split_forms` runs the other split-precision form on the
 same snapshots, and both forms with the configuration's other filter width
@@ -393,43 +394,104 @@ CLOSURE_POINTS = 1 << 20
 CLOSURE_SFU_CLK_PER_POINT = 384 * (1 / 32 + 1 / 16)
 
 
-def closure_measure(eles, torch, les, ub, tau, stream, timed, exact_ms_per_les_point, peaks, re_tau):
-    """The learned closure on this workload's exact stress: train on snapshot
-    0, report the error against the exact T_ij of snapshot 1 (a field of
-    another seed), and time tensor-core inference on 2^20 LES points."""
+CLOSURE_DNS = (256, 193, 256)      # 4 pi x 2 x 2 pi channel
+CLOSURE_LES = (64, 65, 48)
+CLOSURE_TRAIN, CLOSURE_HELDOUT, CLOSURE_EPOCHS = 32, 2, 8
+# training flop per point and epoch, one product per multiply: forward (all
+# four layers), weight gradients (all four) and input gradients (layers 1-3)
+CLOSURE_TRAIN_FLOP_PER_POINT = 2 * CLOSURE_FLOP_PER_POINT + 2 * (128 * 128 + 128 * 128 + 128 * 6)
+CLOSURE_LAUNCHES_PER_TRAIN_STEP = 34
+
+
+def closure_measure(eles, torch, stream, peaks):
+    """The learned closure in the configuration it is specified for: exact
+    T_ij of 32 seeded 256 x 193 x 256 channel snapshots (4 pi x 2 x 2 pi)
+    filtered to 64 x 65 x 48 at Delta = Lx / 32 train the network; two more
+    seeds are held out.  Reports the held-out error per component against the
+    exact stress for the network, the gradient model (formed from the same
+    features) and no model; the training rate; and tensor-core inference on
+    2^20 LES points.  Rank 0 only: its timings are local."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_1902_02508_gb300 import inputs as I
+    dev = torch.device("cuda", torch.cuda.current_device())
+    dns = I.dns_grid(*CLOSURE_DNS, *I.BOX_LARGE)
+    les = I.les_grid(dns, *CLOSURE_LES)
+    delta = dns.Lx / 32
+    plan = eles.filter_setup(dns, les, delta, precision=eles.PREC_FP32)
     n = les.nx * les.ny * les.nz
-    feats = []
-    with torch.cuda.stream(stream):          # every tensor op below is ordered with the library calls
-        for s in (0, 1):
-            f = torch.empty((n, 10), device=ub.device)
-            eles.closure_features(les, ub[s].float().contiguous(), f, re_tau=re_tau, stream=stream)
-            feats.append(f)
-        t_ex = [tau[s].reshape(6, n).float().contiguous() for s in (0, 1)]
+    seeds = [5000 + s for s in range(CLOSURE_TRAIN)] + [6000 + s for s in range(CLOSURE_HELDOUT)]
+
+    def local_ms(fn, k, warm=2):
+        for _ in range(warm):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(k):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    feats, taus = [], []
+    t0 = time.perf_counter()
+    exact_ms = None
+    with ThreadPoolExecutor(8) as ex, torch.cuda.stream(stream):
+        for i in range(0, len(seeds), 8):
+            for u in ex.map(lambda sd: I.channel_velocity(dns, sd).astype(np.float32), seeds[i:i + 8]):
+                ud = torch.from_numpy(u).to(dev)
+                ub = torch.empty((3, les.ny, les.nz, les.nx), device=dev)
+                tau = torch.empty((6, les.ny, les.nz, les.nx), device=dev)
+                call = lambda: eles.subfilter_stress(plan, ud, ub, tau, stream=stream)
+                if exact_ms is None:
+                    exact_ms = local_ms(call, 5)
+                call()
+                f = torch.empty((n, 10), device=dev)
+                eles.closure_features(les, ub, f, re_tau=I.RE_TAU, stream=stream)
+                feats.append(f)
+                taus.append(tau.reshape(6, n))
+    torch.cuda.synchronize()
+    data_s = time.perf_counter() - t0
+    ftr = torch.cat(feats[:CLOSURE_TRAIN], 0).contiguous()
+    ttr = torch.cat(taus[:CLOSURE_TRAIN], 1).contiguous()
+    ntr = ftr.shape[0]
     cl = eles.closure_create(batch=4096, lr=2e-3, seed=3)
     t0 = time.perf_counter()
-    epochs = 15
-    loss = eles.closure_train(cl, feats[0], t_ex[0], epochs=epochs, stream=stream)
-    train_s = time.perf_counter() - t0
-    with torch.cuda.stream(stream):
-        pred = torch.empty((6, n), device=ub.device)
-        nfall = eles.closure_infer(cl, feats[1], pred, stream=stream)
-        diff = (pred.double() - t_ex[1].double())
-        rel = float(diff.norm() / t_ex[1].double().norm())
-        rel_c = [float(diff[q].norm() / t_ex[1][q].double().norm()) for q in range(6)]
-        # inference throughput: the held-out features repeated to 2^20 points
-        reps = (CLOSURE_POINTS + n - 1) // n
-        f1m = feats[1].repeat(reps, 1)[:CLOSURE_POINTS].contiguous()
-        out = torch.empty((6, CLOSURE_POINTS), device=ub.device)
+    loss = eles.closure_train(cl, ftr, ttr, epochs=CLOSURE_EPOCHS, stream=stream)
     torch.cuda.synchronize()
-    k = 20
-    ms = timed(lambda: eles.closure_infer(cl, f1m, out, stream=stream, count=False), k, 3) / k
+    train_s = time.perf_counter() - t0
+    del ftr, ttr
+    fho = torch.cat(feats[CLOSURE_TRAIN:], 0).contiguous()
+    tho = torch.cat(taus[CLOSURE_TRAIN:], 1).contiguous().double()
+    nho = fho.shape[0]
+    with torch.cuda.stream(stream):
+        pred = torch.empty((6, nho), device=dev)
+        nfall = eles.closure_infer(cl, fho, pred, stream=stream)
+        # the gradient model T_ij = Delta^2 / 12 g_ik g_jk from the same features
+        g = fho[:, :9].double().reshape(nho, 3, 3)
+        pairs = ((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))
+        gm = torch.stack([delta * delta / 12.0 * (g[:, i, :] * g[:, j, :]).sum(dim=1) for i, j in pairs])
+
+        def rel(a):
+            d = a - tho
+            return float(d.norm() / tho.norm()), [float(d[q].norm() / tho[q].norm()) for q in range(6)]
+        mlp_rel, mlp_c = rel(pred.double())
+        gm_rel, gm_c = rel(gm)
+        reps = (CLOSURE_POINTS + nho - 1) // nho
+        f1m = fho.repeat(reps, 1)[:CLOSURE_POINTS].contiguous()
+        out = torch.empty((6, CLOSURE_POINTS), device=dev)
+    torch.cuda.synchronize()
+    ms = local_ms(lambda: eles.closure_infer(cl, f1m, out, stream=stream, count=False), 20, 3)
     assert eles.closure_check_device_error(cl, stream) == 0
     tflops = CLOSURE_FLOP_PER_POINT * CLOSURE_POINTS / (ms / 1e3) / 1e12
     tpeak = peaks.get("bf16_tflops", 1900.0)
-    nsm = torch.cuda.get_device_properties(ub.device).multi_processor_count
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_hz = peaks.get("sm_max_mhz", 2070.0) * 1e6
     pts = CLOSURE_POINTS / (ms / 1e3)
     sfu_peak = nsm * sm_hz / CLOSURE_SFU_CLK_PER_POINT
+    train_pts = ntr * CLOSURE_EPOCHS / train_s
+    train_tflops = train_pts * CLOSURE_TRAIN_FLOP_PER_POINT / 1e12
     # the FP64 reference forward pass on a bounded sample of the same features
     from oracle import mlp as M
     params, stats = eles.closure_get_params(cl)
@@ -442,9 +504,12 @@ def closure_measure(eles, torch, les, ub, tau, stream, timed, exact_ms_per_les_p
     dt = time.perf_counter() - t0
     cpu = {"value": ncpu / dt, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
            "sample": f"{ncpu} points, NumPy FP64 forward pass, {dt:.2f} s"}
-    return {"workload": f"MLP 10-128-128-128-6 (SiLU) inference on {CLOSURE_POINTS} LES points "
-                        f"(features of the held-out snapshot, repeated)",
-            "ms_per_call": ms, "points_per_s": CLOSURE_POINTS / (ms / 1e3),
+    order = ["11", "12", "13", "22", "23", "33"]
+    return {"workload": f"MLP 10-128-128-128-6 (SiLU) trained on the exact T_ij of {CLOSURE_TRAIN} synthetic "
+                        f"{'x'.join(map(str, CLOSURE_DNS))} channel snapshots (4 pi x 2 x 2 pi) filtered to "
+                        f"{'x'.join(map(str, CLOSURE_LES))} at Delta = Lx/32 ({ntr} LES points); inference on "
+                        f"{CLOSURE_POINTS} LES points (held-out features, repeated)",
+            "ms_per_call": ms, "points_per_s": pts,
             "precision": "BF16 weights, split-BF16 activations, FP32 accumulation (tcgen05, TMEM)",
             "roofline": {"bound": "alu", "achieved": pts, "peak": sfu_peak, "unit": "points/s",
                          "frac": pts / sfu_peak,
@@ -455,12 +520,22 @@ def closure_measure(eles, torch, les, ub, tau, stream, timed, exact_ms_per_les_p
                                     "peak_source": "measured bf16 burst" if "bf16_tflops" in peaks else "fallback",
                                     "flop_per_point": CLOSURE_FLOP_PER_POINT},
                          "traffic": traffic_from_profile("closure_mlp_tc_1m", CLOSURE_POINTS, "closure")},
-            "error_vs_exact": {"rel_l2": rel, "rel_l2_per_component": rel_c, "no_model_rel_l2": 1.0,
-                               "tau_order": ["11", "12", "13", "22", "23", "33"],
-                               "train": f"snapshot 0 ({n} LES points), {epochs} epochs, {train_s:.1f} s, "
-                                        f"final loss {loss:.4f} (standardised)",
-                               "test": "snapshot 1 (another seed)", "guarded_points": nfall},
-            "speedup_vs_exact_per_les_point": exact_ms_per_les_point / (ms / CLOSURE_POINTS), "cpu_baseline": cpu,
+            "error_vs_exact": {"rel_l2": mlp_rel, "rel_l2_per_component": mlp_c,
+                               "gradient_model_rel_l2": gm_rel, "gradient_model_rel_l2_per_component": gm_c,
+                               "no_model_rel_l2": 1.0, "tau_order": order,
+                               "test": f"{CLOSURE_HELDOUT} held-out seeds ({nho} LES points)",
+                               "guarded_points": nfall},
+            "train": {"points": ntr, "epochs": CLOSURE_EPOCHS, "batch": 4096, "s": train_s,
+                      "points_per_s": train_pts, "final_loss_standardised": loss,
+                      "gemms": "mma.sync m16n8k16 BF16, split-BF16 activations and gradients, FP32 accumulation, "
+                               "fixed-order split-K",
+                      "tflops_algorithmic": train_tflops, "flop_per_point": CLOSURE_TRAIN_FLOP_PER_POINT,
+                      "tensor_frac": train_tflops / tpeak,
+                      "launches_per_step": CLOSURE_LAUNCHES_PER_TRAIN_STEP,
+                      "data": f"{len(seeds)} snapshots generated and filtered in {data_s:.1f} s "
+                              f"(FP32 plan: the LES z nodes are not DNS nodes)"},
+            "exact_ms_per_snapshot": exact_ms,
+            "speedup_vs_exact_per_les_point": (exact_ms / n) / (ms / CLOSURE_POINTS), "cpu_baseline": cpu,
             "gpu_launches_per_call": 2}
 
 
@@ -748,12 +823,10 @@ def main():
     if not args.no_fp64:
         differential = differential_measure(eles, torch, dns, les, u[0], stream, timed, from_json)
 
-    # --- the learned closure (trained on this workload's exact stress)
+    # --- the learned closure, in its own configuration (rank 0)
     closure = None
-    if not args.no_closure and ns >= 2:
-        closure = closure_measure(eles, torch, les, ub, tau, stream, timed,
-                                  (ms / args.steps) / (ns * les.nx * les.ny * les.nz), from_json,
-                                  180.0 if args.workload == "re180" else 550.0)
+    if not args.no_closure and rank == 0:
+        closure = closure_measure(eles, torch, stream, from_json)
 
     # --- accuracy at the stated tolerance: snapshot 0 against the CPU oracle
     err = None

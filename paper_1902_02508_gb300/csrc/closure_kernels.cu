@@ -22,6 +22,8 @@
 
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "eles_internal.h"
 
 namespace eles {
@@ -126,50 +128,108 @@ __global__ void gather_batch(const float *__restrict__ F, const float *__restric
 }
 
 // ------------------------------------------------------------------ GEMM --
-// C[m][n] (+)= sum_k A(m, k) B(k, n), FP32 with generic strides: A(m, k) =
-// A[m * sam + k * sak], B(k, n) = B[k * sbk + n * sbn].  Tiles of 64 x 64,
-// k-slices of 16, 256 threads with 4 x 4 outputs each.  With gridDim.z > 1
+// C[m][n] = sum_k A(m, k) B(k, n) on the tensor cores, with generic strides:
+// A(m, k) = A[m * sam + k * sak], B(k, n) = B[k * sbk + n * sbn].
+//
+// mma.sync m16n8k16 BF16 with FP32 accumulation.  Each FP32 operand is split
+// into BF16 words hi = rn(x), lo = rn(x - hi) (16 significant bits together)
+// and the products hi*hi + lo*hi + hi*lo are accumulated; an operand that is
+// exact in BF16 (the rounded weights, BLO = false) has no lo word and its
+// product is dropped.  Tiles of 64 x 64 outputs, k-slices of 32 staged in
+// shared memory as BF16 (A as [m][k], B as [n][k], so a fragment register is
+// one 32-bit load), 4 warps with 32 x 32 outputs each.  With gridDim.z > 1
 // the k range is split and slice z writes its partial to C + z * M * N
 // (reduced afterwards in a fixed order).
-constexpr int GT = 64, GK = 16;
+constexpr int GT = 64, GK = 32, GKP = GK + 8;   // row pitch 40 BF16 = 20 words: conflict-free fragments
 
-__global__ void __launch_bounds__(256) gemm_kernel(const float *__restrict__ A, long sam, long sak,
-                                                   const float *__restrict__ B, long sbk, long sbn, float *C,
-                                                   int M, int N, long K, long kchunk)
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
 {
-    __shared__ float As[GK][GT + 4], Bs[GK][GT + 4];
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void split_store(__nv_bfloat16 *hi, __nv_bfloat16 *lo, int at, float x, bool keep_lo)
+{
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[at] = h;
+    if (keep_lo) lo[at] = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
+template <bool BLO>
+__global__ void __launch_bounds__(128) gemm_tc_kernel(const float *__restrict__ A, long sam, long sak,
+                                                      const float *__restrict__ B, long sbk, long sbn, float *C,
+                                                      int M, int N, long K, long kchunk)
+{
+    __shared__ __align__(16) __nv_bfloat16 Ah[GT * GKP], Al[GT * GKP], Bh[GT * GKP], Bl[BLO ? GT * GKP : 2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
     const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
     const long k0 = (long)blockIdx.z * kchunk, k1 = min(K, k0 + kchunk);
-    float acc[4][4] = {};
+    float acc[2][4][4] = {};
     for (long kb = k0; kb < k1; kb += GK) {
-        for (int i = threadIdx.x; i < GK * GT; i += 256) {
-            const int kk = i / GT, mm = i % GT;
+        for (int i = threadIdx.x; i < GK * GT; i += 128) {
+            // the contiguous index runs fastest across the threads
+            const int kk = sak == 1 ? i % GK : i / GT, mm = sak == 1 ? i / GK : i % GT;
             const long k = kb + kk;
-            As[kk][mm] = (m0 + mm < M && k < k1) ? A[(long)(m0 + mm) * sam + k * sak] : 0.f;
-            Bs[kk][mm] = (n0 + mm < N && k < k1) ? B[k * sbk + (long)(n0 + mm) * sbn] : 0.f;
+            const float x = (m0 + mm < M && k < k1) ? A[(long)(m0 + mm) * sam + k * sak] : 0.f;
+            split_store(Ah, Al, mm * GKP + kk, x, true);
+        }
+        for (int i = threadIdx.x; i < GK * GT; i += 128) {
+            const int kk = sbk == 1 ? i % GK : i / GT, nn = sbk == 1 ? i / GK : i % GT;
+            const long k = kb + kk;
+            const float x = (n0 + nn < N && k < k1) ? B[k * sbk + (long)(n0 + nn) * sbn] : 0.f;
+            split_store(Bh, Bl, nn * GKP + kk, x, BLO);
         }
         __syncthreads();
 #pragma unroll
-        for (int kk = 0; kk < GK; kk++) {
-            float a[4], b[4];
+        for (int ks = 0; ks < GK; ks += 16) {
+            unsigned ah[2][4], al[2][4], bh[4][2], bl[4][2];
 #pragma unroll
-            for (int i = 0; i < 4; i++) { a[i] = As[kk][ty * 4 + i]; b[i] = Bs[kk][tx * 4 + i]; }
+            for (int mt = 0; mt < 2; mt++) {
+                const int r = (wm + mt * 16 + g) * GKP + ks + 2 * t;
+                ah[mt][0] = *reinterpret_cast<const unsigned *>(Ah + r);
+                ah[mt][1] = *reinterpret_cast<const unsigned *>(Ah + r + 8 * GKP);
+                ah[mt][2] = *reinterpret_cast<const unsigned *>(Ah + r + 8);
+                ah[mt][3] = *reinterpret_cast<const unsigned *>(Ah + r + 8 * GKP + 8);
+                al[mt][0] = *reinterpret_cast<const unsigned *>(Al + r);
+                al[mt][1] = *reinterpret_cast<const unsigned *>(Al + r + 8 * GKP);
+                al[mt][2] = *reinterpret_cast<const unsigned *>(Al + r + 8);
+                al[mt][3] = *reinterpret_cast<const unsigned *>(Al + r + 8 * GKP + 8);
+            }
 #pragma unroll
-            for (int i = 0; i < 4; i++)
+            for (int nt = 0; nt < 4; nt++) {
+                const int r = (wn + nt * 8 + g) * GKP + ks + 2 * t;
+                bh[nt][0] = *reinterpret_cast<const unsigned *>(Bh + r);
+                bh[nt][1] = *reinterpret_cast<const unsigned *>(Bh + r + 8);
+                if constexpr (BLO) {
+                    bl[nt][0] = *reinterpret_cast<const unsigned *>(Bl + r);
+                    bl[nt][1] = *reinterpret_cast<const unsigned *>(Bl + r + 8);
+                }
+            }
 #pragma unroll
-                for (int jj = 0; jj < 4; jj++) acc[i][jj] = fmaf(a[i], b[jj], acc[i][jj]);
+            for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+                for (int nt = 0; nt < 4; nt++) {
+                    // small products first
+                    if constexpr (BLO) mma_bf16(acc[mt][nt], ah[mt], bl[nt][0], bl[nt][1]);
+                    mma_bf16(acc[mt][nt], al[mt], bh[nt][0], bh[nt][1]);
+                    mma_bf16(acc[mt][nt], ah[mt], bh[nt][0], bh[nt][1]);
+                }
         }
         __syncthreads();
     }
     float *Cz = C + (long)blockIdx.z * M * N;
 #pragma unroll
-    for (int i = 0; i < 4; i++)
+    for (int mt = 0; mt < 2; mt++)
 #pragma unroll
-        for (int jj = 0; jj < 4; jj++) {
-            const int m = m0 + ty * 4 + i, nn = n0 + tx * 4 + jj;
-            if (m < M && nn < N) Cz[(long)m * N + nn] = acc[i][jj];
-        }
+        for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const int m = m0 + wm + mt * 16 + g + (i >> 1) * 8, nn = n0 + wn + nt * 8 + 2 * t + (i & 1);
+                if (m < M && nn < N) Cz[(long)m * N + nn] = acc[mt][nt][i];
+            }
 }
 
 __global__ void reduce_parts(const float *__restrict__ P, int nparts, long len, float *out)
@@ -206,20 +266,38 @@ __global__ void mse_grad(const float *__restrict__ Y, const float *__restrict__ 
     rowloss[r] = s;
 }
 
+// *acc += sum of v[0 .. n) in a fixed order (one block).
+__global__ void sum_into(const float *__restrict__ v, int n, double *acc)
+{
+    __shared__ double part[256];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) t += (double)v[i];
+    part[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *acc += part[0];
+}
+
 __global__ void mul_silu_d(float *dH, const float *__restrict__ Z, long n)
 {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dH[i] *= silu_d(Z[i]);
 }
 
-// Column sums of dZ [rows][cols] (bias gradients), one thread per column.
-__global__ void col_sum(const float *__restrict__ dZ, long rows, int cols, float *out)
+// Column sums of dZ [rows][cols] (bias gradients): block z sums rows
+// [z * chunk, (z + 1) * chunk) with one thread per column (coalesced); the
+// partials [gridDim.x][cols] are then reduced in a fixed order.
+__global__ void col_sum_parts(const float *__restrict__ dZ, long rows, int cols, long chunk, float *parts)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = threadIdx.x;
     if (c >= cols) return;
+    const long r0 = (long)blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
     float s = 0.f;
-    for (long r = 0; r < rows; r++) s += dZ[r * cols + c];
-    out[c] = s;
+    for (long r = r0; r < r1; r++) s += dZ[r * cols + c];
+    parts[(long)blockIdx.x * cols + c] = s;
 }
 
 // Adam on the FP32 master parameters; the working copy Wq is the BF16-rounded master.
@@ -316,20 +394,19 @@ int closure_alloc_batch(ef_closure *c, int cap)
     return EF_OK;
 }
 
-// C[M][N] = A(m,k) B(k,n) with a deterministic split over k when K is long.
-void gemm(const float *A, long sam, long sak, const float *B, long sbk, long sbn, float *C, int M, int N, long K,
-          float *parts, cudaStream_t s)
+// C[M][N] = A(m,k) B(k,n) with a deterministic split over k when K is long;
+// b_exact: B holds BF16-exact values (the rounded weights).
+void gemm(const float *A, long sam, long sak, const float *B, long sbk, long sbn, bool b_exact, float *C, int M,
+          int N, long K, float *parts, cudaStream_t s)
 {
     int splits = 1;
-    if (K > 4096) splits = kSplitK;
+    if (K > 1024) splits = kSplitK;
     const long kchunk = ((K + splits - 1) / splits + GK - 1) / GK * GK;
     dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT, splits);
-    if (splits == 1) {
-        gemm_kernel<<<grid, 256, 0, s>>>(A, sam, sak, B, sbk, sbn, C, M, N, K, kchunk);
-    } else {
-        gemm_kernel<<<grid, 256, 0, s>>>(A, sam, sak, B, sbk, sbn, parts, M, N, K, kchunk);
-        reduce_parts<<<grid1((long)M * N), 256, 0, s>>>(parts, splits, (long)M * N, C);
-    }
+    float *out = splits == 1 ? C : parts;
+    if (b_exact) gemm_tc_kernel<false><<<grid, 128, 0, s>>>(A, sam, sak, B, sbk, sbn, out, M, N, K, kchunk);
+    else gemm_tc_kernel<true><<<grid, 128, 0, s>>>(A, sam, sak, B, sbk, sbn, out, M, N, K, kchunk);
+    if (splits > 1) reduce_parts<<<grid1((long)M * N), 256, 0, s>>>(parts, splits, (long)M * N, C);
 }
 
 // Forward pass of nb rows already in H[0]; Y in H[NLAYER].
@@ -338,7 +415,7 @@ void forward(ef_closure *c, int nb, cudaStream_t s)
     for (int l = 0; l < NLAYER; l++) {
         const int K = kLayerIn[l], N = kLayerOut[l];
         // Z = H W^T: A = H [nb][K], B(k, n) = W[n][k]
-        gemm(c->H[l], K, 1, c->wq + c->off_w[l], 1, K, c->Z[l], nb, N, K, c->parts, s);
+        gemm(c->H[l], K, 1, c->wq + c->off_w[l], 1, K, true, c->Z[l], nb, N, K, c->parts, s);
         const bool act = l < NLAYER - 1;
         bias_act<<<grid1((long)nb * N), 256, 0, s>>>(c->Z[l], act ? c->H[l + 1] : nullptr, c->wq + c->off_b[l],
                                                       nb, N, act ? 1 : 0);
@@ -354,11 +431,15 @@ void backward(ef_closure *c, int nb, cudaStream_t s)
     for (int l = NLAYER - 1; l >= 0; l--) {
         const int K = kLayerIn[l], N = kLayerOut[l];
         // dW[n][k] = sum_b d[b][n] H[b][k]: A(m=n, k=b) = d[b][n], B(k=b, n=k) = H[b][k]
-        gemm(d, 1, N, c->H[l], K, 1, c->g + c->off_w[l], N, K, nb, c->parts, s);
-        col_sum<<<grid1(N, 128), 128, 0, s>>>(d, nb, N, c->g + c->off_b[l]);
+        gemm(d, 1, N, c->H[l], K, 1, false, c->g + c->off_w[l], N, K, nb, c->parts, s);
+        {
+            const long chunk = (nb + kSplitK - 1) / kSplitK;
+            col_sum_parts<<<kSplitK, 128, 0, s>>>(d, nb, N, chunk, c->parts);
+            reduce_parts<<<grid1(N), 256, 0, s>>>(c->parts, kSplitK, N, c->g + c->off_b[l]);
+        }
         if (l > 0) {
             // dH[b][k] = sum_n d[b][n] W[n][k]
-            gemm(d, N, 1, c->wq + c->off_w[l], K, 1, dn, nb, K, N, c->parts, s);
+            gemm(d, N, 1, c->wq + c->off_w[l], K, 1, true, dn, nb, K, N, c->parts, s);
             mul_silu_d<<<grid1((long)nb * K), 256, 0, s>>>(dn, c->Z[l - 1], (long)nb * K);
             float *t = d; d = dn; dn = t;
         }
@@ -530,26 +611,33 @@ int ef_closure_train(ef_closure *c, const float *feats, const float *tau, long n
     if (!c->fitted && (rc = ef_closure_fit_norm(c, feats, tau, n, stream))) return rc;
     const int B = c->cfg.batch;
     const long nbatch = (n + B - 1) / B;
-    std::vector<long> perm(n), bidx(B);
-    double loss_sum = 0.0;
-    long loss_cnt = 0;
-    std::vector<float> rl(B);
-    for (int ep = 0; ep < epochs; ep++) {
-        // deterministic order: sort points by a hash of (seed, epoch index, point)
+    std::vector<long> perm(n);
+    long *d_perm = nullptr;
+    double *d_loss = nullptr;
+    cudaError_t e = dev_malloc(&d_perm, sizeof(long) * (size_t)n);
+    if (e == cudaSuccess) e = dev_malloc(&d_loss, sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_loss, 0, sizeof(double), s);
+    if (e != cudaSuccess) {
+        cudaFree(d_perm);
+        return cuda_fail(e, "ef_closure_train buffers");
+    }
+    for (int ep = 0; ep < epochs && e == cudaSuccess; ep++) {
+        // deterministic order: sort points by a hash of (seed, epoch index,
+        // point).  The shuffle only decides which points share a batch, so a
+        // set that fits one batch is taken in its stored order.
         const unsigned long long key = mix(c->cfg.seed ^ mix(0x5eedull + (unsigned long long)(c->step / nbatch)));
         for (long i = 0; i < n; i++) perm[i] = i;
-        for (long i = n - 1; i > 0; i--) {
+        for (long i = nbatch > 1 ? n - 1 : 0; i > 0; i--) {
             const long j = (long)(mix(key + (unsigned long long)i) % (unsigned long long)(i + 1));
             const long t = perm[i]; perm[i] = perm[j]; perm[j] = t;
         }
-        loss_sum = 0.0;
-        loss_cnt = 0;
-        for (long bt = 0; bt < nbatch; bt++) {
+        // the host buffer is refilled next epoch: the copy must have landed
+        e = cudaMemcpyAsync(d_perm, perm.data(), sizeof(long) * (size_t)n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        for (long bt = 0; bt < nbatch && e == cudaSuccess; bt++) {
             const int nb = (int)(bt + 1 < nbatch ? B : n - bt * B);
-            cudaError_t e = cudaMemcpyAsync(c->idx, perm.data() + bt * B, sizeof(long) * nb, cudaMemcpyHostToDevice, s);
-            if (e != cudaSuccess) return cuda_fail(e, "batch indices");
-            gather_batch<<<grid1(nb), 256, 0, s>>>(feats, tau, n, c->idx, nb, c->stats, c->stats + 10, c->stats + 20,
-                                                   c->stats + 26, c->H[0], c->T);
+            gather_batch<<<grid1(nb), 256, 0, s>>>(feats, tau, n, d_perm + bt * B, nb, c->stats, c->stats + 10,
+                                                   c->stats + 20, c->stats + 26, c->H[0], c->T);
             forward(c, nb, s);
             mse_grad<<<grid1(nb), 256, 0, s>>>(c->H[NLAYER], c->T, c->dA, c->rowloss, nb);
             backward(c, nb, s);
@@ -558,18 +646,17 @@ int ef_closure_train(ef_closure *c, const float *feats, const float *tau, long n
             const float c1 = 1.f - powf(b1, (float)c->step), c2 = 1.f - powf(b2, (float)c->step);
             adam_step<<<grid1(c->nparam), 256, 0, s>>>(c->w, c->wq, c->g, c->m, c->v, c->nparam, c->cfg.lr, b1, b2,
                                                       1e-8f, c1, c2);
-            if (ep == epochs - 1) {
-                e = cudaMemcpyAsync(rl.data(), c->rowloss, sizeof(float) * nb, cudaMemcpyDeviceToHost, s);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-                if (e != cudaSuccess) return cuda_fail(e, "loss readback");
-                for (int i = 0; i < nb; i++) loss_sum += rl[i];
-                loss_cnt += (long)nb * NOUT;
-            }
+            if (ep == epochs - 1) sum_into<<<1, 256, 0, s>>>(c->rowloss, nb, d_loss);
+            e = cudaGetLastError();
         }
     }
-    cudaError_t e = cudaGetLastError();
+    double loss_sum = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&loss_sum, d_loss, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_perm);
+    cudaFree(d_loss);
     if (e != cudaSuccess) return cuda_fail(e, "ef_closure_train");
-    if (loss_out) *loss_out = loss_cnt ? (float)(loss_sum / loss_cnt) : 0.f;
+    if (loss_out) *loss_out = epochs > 0 ? (float)(loss_sum / ((double)n * NOUT)) : 0.f;
     return EF_OK;
 }
 

@@ -6,7 +6,8 @@
 * training lowers the loss; resuming from a checkpoint reproduces an
   uninterrupted run bit for bit;
 * the gain: on a held-out snapshot the trained network's error against the
-  exact T_ij is well below that of the model-free LES (T = 0), and the
+  exact T_ij is well below that of the model-free LES (T = 0) and below that
+  of the gradient model (oracle/mlp.gradient_model), and the
   guarded inference falls back to the exact stress where asked.
 """
 import math
@@ -117,8 +118,14 @@ def test_training_gain_and_fallback():
     err_mlp = np.linalg.norm(pred - exact) / np.linalg.norm(exact)
     gm = M.gradient_model(ubs[4].double().cpu().numpy(), les, delta).reshape(6, -1)
     err_grad = np.linalg.norm(gm - exact) / np.linalg.norm(exact)
-    print(f"relative error: MLP {err_mlp:.3f}, gradient model {err_grad:.3f}, no model 1.000")
+    per = [np.linalg.norm(pred[q] - exact[q]) / np.linalg.norm(exact[q]) for q in range(6)]
+    per_g = [np.linalg.norm(gm[q] - exact[q]) / np.linalg.norm(exact[q]) for q in range(6)]
+    print(f"relative error: MLP {err_mlp:.3f}, gradient model {err_grad:.3f}, no model 1.000; per component "
+          f"MLP {np.round(per, 3)}, gradient model {np.round(per_g, 3)}")
+    # the gain over the model-free LES (T = 0, error 1) and over the gradient model
     assert err_mlp < 0.5
+    assert err_mlp < err_grad
+    assert max(per) < 1.0
     # guard: a tiny threshold sends (almost) every point to the exact stress
     cl2 = eles.closure_create(batch=4096, lr=2e-3, seed=3, guard_sigma=1e-3)
     p, st = eles.closure_get_params(cl)
