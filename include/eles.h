@@ -100,22 +100,27 @@ enum {
  * reference profile U(y) (the mean of each plane's z-row 0; exact algebra of
  * Eq. 6) on the tensor cores with FP32 accumulation, and form ~bar(u) and T
  * from FP64 profile terms:
- *   EF_PREC_BF16X3  x: every field and weight split into two BF16 parts,
- *                   three products (A_hi B_hi + A_lo B_hi + A_hi B_lo);
+ *   EF_PREC_BF16X3  the velocity fluctuations u'_a and the weights split
+ *                   into two BF16 parts, three products (A_hi B_hi + A_lo
+ *                   B_hi + A_hi B_lo), in x and in z;
  *   EF_PREC_TF32X2  x: the velocity fluctuations and the weights split into
- *                   two TF32 parts (three products); the six product fields
- *                   u'_a u'_b rounded once to TF32 against the split weights
- *                   (two products);
- * in both, z and y contract in split BF16 (three products).  A plan of either
- * form runs the x-z contraction on the tensor cores or is refused with
- * EF_ERR_UNSUPPORTED: the warp-specialised kernel needs LES x and z nodes at
+ *                   two TF32 parts (three products); z as BF16X3;
+ *   both: the six product fields u'_a u'_b are rounded once to an 11-bit
+ *   significand (FP16, TF32's precision) before x and again before z, each
+ *   time against weights split into two FP16 parts (two products); the y
+ *   contraction is split BF16 (three products) for every field.  Measured
+ *   on the 512 x 257 x 384 channel at Delta = Lx/64: max |T - FP64| per
+ *   component 1.4e-5 u_tau^2 or less.
+ * A plan of either form runs the x-z contraction on the tensor cores or is
+ * refused with EF_ERR_UNSUPPORTED: the warp-specialised kernel needs LES x
+ * and z nodes at
  * every r-th DNS node (x stride 4, 8 or 16), nz in {64, 128, 192, 256, 384},
  * nlz a multiple of 16, nlx a multiple of 16 / (x stride), and a filter that
  * fits its window (2.5 Delta at most about 13 x strides; wider x filters are
  * split into 2 or 4 output phases, each a CTA that re-reads the plane);
  * BF16X3 plans outside it may still run the earlier tensor-core kernel
- * (x stride 8 with at most 7 outputs per input).  ef_plan_info index 10
- * tells which kernel runs. */
+ * (x stride 8 with at most 7 outputs per input; it splits every field in x
+ * and z into BF16 parts).  ef_plan_info index 10 tells which kernel runs. */
 enum {
     EF_PREC_FP64 = 0,        /* double in, double out, FP64 throughout */
     EF_PREC_FP32 = 1,        /* float in/out, FP32 contractions on CUDA cores, FP64 recovery */

@@ -98,8 +98,10 @@ __global__ void __launch_bounds__(96) ws_uref(const float *__restrict__ u, int n
 // z-operator A fragments for the tensor-core z phase: k-step kk, lane
 // (g, t) holds A[g][2t..2t+1], A[g+8][2t..2t+1], A[g][2t+8..2t+9],
 // A[g+8][2t+8..2t+9] with A[m][k] = w[16 kk + r(k) - RZ m - zoff], split into
-// hi and lo bf16 pairs; r(2i + e) = i + 8e is the row order of the pre-split
-// parked pairs.  Returns KS (0 if the z operator does not qualify).
+// hi and lo pairs twice: bf16 (for the velocity columns) and FP16 (for the
+// product columns); r(2i + e) = i + 8e is the row order of the parked pairs.
+// Layout [KS][bf16 hi, bf16 lo, f16 hi, f16 lo][32 lanes] uint4.  Returns
+// KS (0 if the z operator does not qualify).
 int ws_zfrags(const Ring &rz, int nlz, std::vector<unsigned> &out, int *zoff_out)
 {
     if (!rz.ok || nlz % 16 != 0) return 0;
@@ -112,24 +114,26 @@ int ws_zfrags(const Ring &rz, int nlz, std::vector<unsigned> &out, int *zoff_out
         const int dd = (e - o) / RZ - rz.dmin;
         return (dd >= 0 && dd < rz.D) ? rz.W64[e * rz.D + dd] : 0.0;
     };
-    out.assign((size_t)KS * 32 * 8, 0u);
+    out.assign((size_t)KS * 4 * 32 * 4, 0u);
     for (int kk = 0; kk < KS; kk++)
         for (int lane = 0; lane < 32; lane++) {
             const int g = lane / 4, t = lane % 4;
             const int rows[4] = {g, g + 8, g, g + 8}, kofs[4] = {0, 0, 8, 8};
             for (int r = 0; r < 4; r++) {
-                unsigned hi = 0, lo = 0;
+                unsigned bh = 0, bl = 0, fh = 0, fl = 0;
                 for (int e = 0; e < 2; e++) {
                     const int k = 2 * t + kofs[r] + e;
                     const int row = (k >> 1) + 8 * (k & 1);
                     const double v = w(16 * kk + row - RZ * rows[r] - zoff);
-                    const unsigned short h = bf16_bits(v);
-                    const unsigned short l = bf16_bits(v - bf16_value(h));
-                    hi |= (unsigned)h << (16 * e);
-                    lo |= (unsigned)l << (16 * e);
+                    const unsigned short h = bf16_bits(v), l = bf16_bits(v - bf16_value(h));
+                    const unsigned short h16 = f16_bits(v), l16 = f16_bits(v - f16_value(h16));
+                    bh |= (unsigned)h << (16 * e);
+                    bl |= (unsigned)l << (16 * e);
+                    fh |= (unsigned)h16 << (16 * e);
+                    fl |= (unsigned)l16 << (16 * e);
                 }
-                out[((size_t)(2 * kk + 0) * 32 + lane) * 4 + r] = hi;
-                out[((size_t)(2 * kk + 1) * 32 + lane) * 4 + r] = lo;
+                const unsigned words[4] = {bh, bl, fh, fl};
+                for (int wd = 0; wd < 4; wd++) out[((size_t)(4 * kk + wd) * 32 + lane) * 4 + r] = words[wd];
             }
         }
     *zoff_out = zoff;
@@ -201,8 +205,9 @@ int ws_setup(ef_plan *p, const char **why)
         *why = "the kernel's shared memory exceeds 227 KB for this grid";
         return EF_OK;
     }
-    // rotated B fragments per phase: [OP][NR][32][BW] uint4
-    const int BW = mode == ws::MODE_TF32X2 ? 3 : 1;
+    // rotated B fragments per phase: [OP][NR][32][BW] uint4, the velocities'
+    // words first, the products' FP16 words last
+    const int BW = mode == ws::MODE_TF32X2 ? 3 : 2;
     std::vector<unsigned> bv((size_t)OP * NR * 32 * BW * 4, 0u);
     for (int ph = 0; ph < OP; ph++)
         for (int q = 0; q < NR; q++)
@@ -233,19 +238,20 @@ int ws_setup(ef_plan *p, const char **why)
                             o[4 * k2 + e] = h;
                             o[4 * k2 + 2 + e] = tf32_bits(v - tf32_value(h));
                         }
-                    // products, FP16 MMA: k slots as the BF16X3 words
-                    for (int kq = 0; kq < 2; kq++) {
-                        unsigned hi = 0, lo = 0;
-                        for (int e = 0; e < 2; e++) {
-                            const double v = bweight(rx, 4 * t + 2 * kq + e, n, xc0[ph], OP, bshift);
-                            const unsigned short h = f16_bits(v);
-                            const unsigned short l = f16_bits(v - f16_value(h));
-                            hi |= (unsigned)h << (16 * e);
-                            lo |= (unsigned)l << (16 * e);
-                        }
-                        o[8 + kq] = hi;
-                        o[8 + 2 + kq] = lo;
+                }
+                // products, FP16 MMA: k slots as the BF16 words
+                unsigned *of = o + 4 * (BW - 1);
+                for (int kq = 0; kq < 2; kq++) {
+                    unsigned hi = 0, lo = 0;
+                    for (int e = 0; e < 2; e++) {
+                        const double v = bweight(rx, 4 * t + 2 * kq + e, n, xc0[ph], OP, bshift);
+                        const unsigned short h = f16_bits(v);
+                        const unsigned short l = f16_bits(v - f16_value(h));
+                        hi |= (unsigned)h << (16 * e);
+                        lo |= (unsigned)l << (16 * e);
                     }
+                    of[kq] = hi;
+                    of[2 + kq] = lo;
                 }
             }
     cudaError_t e;

@@ -30,18 +30,20 @@
 //
 // Fields: u'_c = u_c - U_c(y) (U_c the mean of the plane's z-row 0) and the
 // six products u'_a u'_b, formed in registers.
-//   BF16X3: every field x = hi + lo (bf16 pair), weights likewise; the
+//   Velocities, BF16X3: x = hi + lo (bf16 pair), weights likewise; the
 //           products Ahi Bhi + Alo Bhi + Ahi Blo (m16n8k16).
-//   TF32X2: the three velocities split as hi = x with its 13 low bits
-//           cleared (TF32), lo = x - hi (exact; no conversion instruction),
-//           against TF32 hi + lo weights: Ahi Bhi + Alo Bhi + Ahi Blo
-//           (m16n8k8).  The six product fields are rounded once to an 11-bit
-//           significand (the TF32 precision) and contracted against hi + lo
-//           weights of the same precision: A Bhi + A Blo.  They travel in the
-//           FP16 format (m16n8k16), whose significand is TF32's: one
-//           conversion per pair of values (a TF32 rounding costs several
-//           instructions per value), exact range for |u'_a u'_b| < 65504,
-//           and values below 2^-14 kept to 2^-25 absolute as subnormals.
+//   Velocities, TF32X2: hi = x with its 13 low bits cleared (TF32), lo = x -
+//           hi (exact; no conversion instruction), against TF32 hi + lo
+//           weights: Ahi Bhi + Alo Bhi + Ahi Blo (m16n8k8).
+//   Products, both forms: rounded once to an 11-bit significand (the FP16
+//           format, TF32's precision: one conversion per pair of values)
+//           and contracted against FP16 hi + lo weights: A Bhi + A Blo
+//           (m16n8k16).  Exact range for |u'_a u'_b| < 65504; values below
+//           2^-14 are kept to 2^-25 absolute as subnormals.
+// The z contraction takes the parked x results the same way: the velocity
+// columns as bf16 (hi, lo) pairs against bf16 hi + lo weights (three
+// products), the product columns rounded once to FP16 against FP16 hi + lo
+// weights (two products).
 #pragma once
 
 #include "eles_internal.h"
@@ -55,13 +57,26 @@ using namespace fz;
 constexpr int kZW = 3;               // z warps
 constexpr int CW = 16;               // floats per row per TMA stage: one chunk
 constexpr int CSTG = 2;              // stages in flight
-constexpr int NCB = 2 * NF + 3;      // parked columns per buffer: two outputs x NF fields, 3 row sums
 enum { MODE_BF16X3 = 0, MODE_TF32X2 = 1 };
 
-// B words per lane and rotation: one uint4 (BF16X3), or three (TF32X2: two
-// TF32 k-halves for the velocities, one FP16 word set for the products).
+// B words per lane and rotation: the velocities' set (one uint4 of bf16 hi,
+// lo words for BF16X3; two TF32 k-halves for TF32X2), then the products'
+// FP16 hi, lo words (the last uint4).
 template <int MODE>
-struct Bw { static constexpr int n = MODE == MODE_TF32X2 ? 3 : 1; };
+struct Bw { static constexpr int n = MODE == MODE_TF32X2 ? 3 : 2; };
+
+// Parked columns of one buffer (floats): the velocity columns (3 per output,
+// LD floats: a (row g, row g + 8) pair as two FP32 values, split in place
+// into bf16 (hi, lo) words), the product columns (6 per output, LD / 2
+// words: a pair as one FP16x2 word) and the three row-sum columns (LD).
+template <int OPC>
+struct Park {
+    static constexpr int NV = 3 * OPC, NP = 6 * OPC;   // velocity, product columns
+    static constexpr int NVT = 1, NPT = (NP + 7) / 8;  // column tiles of each kind
+    __host__ __device__ static constexpr size_t floats(int LD) { return (size_t)(NV + 3) * LD + (size_t)NP * (LD / 2); }
+    __host__ __device__ static constexpr size_t prod0(int LD) { return (size_t)NV * LD; }
+    __host__ __device__ static constexpr size_t sum0(int LD) { return (size_t)NV * LD + (size_t)NP * (LD / 2); }
+};
 
 struct WsArgs {
     CUtensorMap tmap;     // TMA view of u: {nx, nz, 3 ny S} floats, box {16, box_rows, 1}
@@ -81,7 +96,7 @@ struct WsArgs {
     int nf;               // fields contracted in z (9, or 3 for the velocities only)
     int nsnap;            // snapshots (items are (snapshot, y-plane, phase))
     long long wait_limit; // bound of one wait in SM clocks (kWaitCycles unless set for tests)
-    const uint4 *afrag;   // z A fragments [KS][hi, lo][32 lanes] (pair order)
+    const uint4 *afrag;   // z A fragments [KS][bf16 hi, bf16 lo, f16 hi, f16 lo][32 lanes] (pair order)
     const uint4 *bvar;    // x B fragments [OP][NR][32 lanes][Bw]
 };
 
@@ -176,7 +191,16 @@ __host__ __device__ constexpr int next_field()
 template <int MODE, int F>
 __device__ __forceinline__ void x_mma(float (&acc)[NF][4], const float2 (&v)[3][2][2], const uint4 (&B)[Bw<MODE>::n])
 {
-    if constexpr (MODE == MODE_BF16X3) {
+    if constexpr (F >= 3) {
+        // products: one rounding to an 11-bit significand (FP16); k slots as the BF16 velocities
+        constexpr int FB = Bw<MODE>::n - 1;
+        const unsigned a0 = pack_f16_2(field2<F>(v[0][0][0], v[1][0][0], v[2][0][0]));   // row g,     k 2t, 2t+1
+        const unsigned a1 = pack_f16_2(field2<F>(v[0][1][0], v[1][1][0], v[2][1][0]));   // row g + 8, k 2t, 2t+1
+        const unsigned a2 = pack_f16_2(field2<F>(v[0][0][1], v[1][0][1], v[2][0][1]));   // row g,     k 2t+8, 2t+9
+        const unsigned a3 = pack_f16_2(field2<F>(v[0][1][1], v[1][1][1], v[2][1][1]));   // row g + 8, k 2t+8, 2t+9
+        mma_f16(acc[F], a0, a1, a2, a3, B[FB].z, B[FB].w);
+        mma_f16(acc[F], a0, a1, a2, a3, B[FB].x, B[FB].y);
+    } else if constexpr (MODE == MODE_BF16X3) {
         unsigned ah[4], al[4];
         split2(field2<F>(v[0][0][0], v[1][0][0], v[2][0][0]), ah[0], al[0]);   // row g,     k 2t, 2t+1
         split2(field2<F>(v[0][1][0], v[1][1][0], v[2][1][0]), ah[1], al[1]);   // row g + 8, k 2t, 2t+1
@@ -185,7 +209,7 @@ __device__ __forceinline__ void x_mma(float (&acc)[NF][4], const float2 (&v)[3][
         mma_bf16(acc[F], ah[0], ah[1], ah[2], ah[3], B[0].x, B[0].y);
         mma_bf16(acc[F], al[0], al[1], al[2], al[3], B[0].x, B[0].y);
         mma_bf16(acc[F], ah[0], ah[1], ah[2], ah[3], B[0].z, B[0].w);
-    } else if constexpr (F < 3) {
+    } else {
 #pragma unroll
         for (int k2 = 0; k2 < 2; k2++) {
             const float2 x0 = v[F][0][k2], x1 = v[F][1][k2];     // rows g, g + 8
@@ -200,14 +224,6 @@ __device__ __forceinline__ void x_mma(float (&acc)[NF][4], const float2 (&v)[3][
                      __float_as_uint(l1.y), b.x, b.y);
             mma_tf32(acc[F], h00, h10, h01, h11, b.z, b.w);
         }
-    } else {
-        // products: one rounding to an 11-bit significand (FP16 carrier); k slots as BF16X3
-        const unsigned a0 = pack_f16_2(field2<F>(v[0][0][0], v[1][0][0], v[2][0][0]));   // row g,     k 2t, 2t+1
-        const unsigned a1 = pack_f16_2(field2<F>(v[0][1][0], v[1][1][0], v[2][1][0]));   // row g + 8, k 2t, 2t+1
-        const unsigned a2 = pack_f16_2(field2<F>(v[0][0][1], v[1][0][1], v[2][0][1]));   // row g,     k 2t+8, 2t+9
-        const unsigned a3 = pack_f16_2(field2<F>(v[0][1][1], v[1][1][1], v[2][1][1]));   // row g + 8, k 2t+8, 2t+9
-        mma_f16(acc[F], a0, a1, a2, a3, B[2].x, B[2].y);
-        mma_f16(acc[F], a0, a1, a2, a3, B[2].z, B[2].w);
     }
     constexpr int nx = next_field<F>();
     if constexpr (nx >= 0) x_mma<MODE, nx>(acc, v, B);
@@ -238,69 +254,103 @@ __device__ __forceinline__ bool wait_or_abort(unsigned long long *bar, unsigned 
     return false;
 }
 
-// z work: Z tile zt (16 outputs) x column tiles nt0 .. nt0 + NT - 1 (8 of
-// the OPC NF parked columns each, column c = j NF + f for output X0 + OP j),
-// KS k-steps over the tile's z window.  The parked columns hold, per 16-row
-// block and pair i < 8, the split (hi, lo) bf16 words of rows (i, i + 8);
-// the k index of a k-step runs over the block's rows in the order
-// k = 2i + e -> row i + 8e, which the A fragments follow.  One A fragment
-// load per k-step feeds all NT column tiles.  The window starts on a 16-row
-// boundary (zoff is a multiple of 16), so a k-step wraps periodically as a
-// whole or not at all.  Lanes whose column is idle use zeros.  Outputs go to
-// h in (X, Z) plane order (Z fastest), so that each store instruction writes
-// 4 runs of 8 consecutive floats instead of 32 scattered ones (a chunk
-// completes whole Z columns of one or two X); the y passes transpose back.
-template <int OPC, int NT, int LD>
+// z work: Z tile zt (16 outputs) of the velocity column tile (DOV) and of
+// product column tiles pt0 .. pt0 + NPTW - 1 (8 columns each; velocity
+// column c = 3 n + f, product column c = 6 n + f - 3, for output X0 + OP n),
+// KS k-steps over the tile's z window, each A fragment loaded once per
+// k-step for all the tiles.  A parked column holds, per 16-row block and pair
+// i < 8, rows (i, i + 8): a velocity pair as its bf16 (hi, lo) words, a
+// product pair as one FP16x2 word; the k index of a k-step runs over the
+// block's rows in the order k = 2i + e -> row i + 8e, which the A fragments
+// follow.  The window starts on a 16-row boundary (zoff is a multiple of 16),
+// so a k-step wraps periodically as a whole or not at all.  Lanes whose
+// column is idle use zeros.  Outputs go to h in (X, Z) plane order (Z
+// fastest), so that each store instruction writes 4 runs of 8 consecutive
+// floats instead of 32 scattered ones (a chunk completes whole Z columns of
+// one or two X); the y passes transpose back.
+template <int OPC, int LD, bool DOV, int NPTW>
 __device__ __forceinline__ void z_tile(const WsArgs &a, const float *colb, const uint4 *afrag,
-                                       int s, int j, int X0, bool val0, bool val1, int zt, int nt0, int lane)
+                                       int s, int j, int X0, bool val0, bool val1, int zt, int pt0, int lane)
 {
+    using PK = Park<OPC>;
+    constexpr int NPA = NPTW > 0 ? NPTW : 1;
     const int g = lane >> 2, t = lane & 3;
-    const uint2 *cp[NT];
-    unsigned keep[NT];                            // all ones for a live column, zero for an idle one
-#pragma unroll
-    for (int i = 0; i < NT; i++) {
-        const int c = (nt0 + i) * 8 + g;          // this lane's B column
-        const bool bval = c < OPC * NF && (c < NF ? val0 : val1);
-        cp[i] = reinterpret_cast<const uint2 *>(colb + (size_t)(bval ? c : 0) * LD) + t;
-        keep[i] = bval ? 0xffffffffu : 0u;
+    const uint2 *vp = nullptr;
+    unsigned vkeep = 0u;                          // all ones for a live column, zero for an idle one
+    if constexpr (DOV) {
+        const bool live = g < PK::NV && (g < 3 ? val0 : val1);
+        vp = reinterpret_cast<const uint2 *>(colb + (size_t)(live ? g : 0) * LD) + t;
+        vkeep = live ? 0xffffffffu : 0u;
     }
-    float acc[NT][3][4];   // one accumulator per split product: independent chains
+    const unsigned *pp[NPA];
+    unsigned pkeep[NPA];
 #pragma unroll
-    for (int i = 0; i < NT; i++)
+    for (int i = 0; i < NPTW; i++) {
+        const int c = (pt0 + i) * 8 + g;
+        const bool live = c < PK::NP && (c < 6 ? val0 : val1);
+        pp[i] = reinterpret_cast<const unsigned *>(colb + PK::prod0(LD)) + (size_t)(live ? c : 0) * (LD / 2) + t;
+        pkeep[i] = live ? 0xffffffffu : 0u;
+    }
+    float av[3][4], ap[NPA][2][4];   // one accumulator per split product: independent chains
 #pragma unroll
-        for (int r = 0; r < 3; r++)
+    for (int r = 0; r < 3; r++)
 #pragma unroll
-            for (int e = 0; e < 4; e++) acc[i][r][e] = 0.f;
+        for (int e = 0; e < 4; e++) av[r][e] = 0.f;
+#pragma unroll
+    for (int i = 0; i < NPA; i++)
+#pragma unroll
+        for (int r = 0; r < 2; r++)
+#pragma unroll
+            for (int e = 0; e < 4; e++) ap[i][r][e] = 0.f;
     int z0 = 16 * a.RZ * zt - a.zoff;
 #pragma unroll 2
     for (int kk = 0; kk < a.KS; kk++, z0 += 16) {
-        const int zr = (z0 < 0 ? z0 + a.nz : (z0 >= a.nz ? z0 - a.nz : z0)) >> 1;   // in 8-byte words
-        const uint4 ah = afrag[(2 * kk) * 32 + lane], al = afrag[(2 * kk + 1) * 32 + lane];
+        const int zr = (z0 < 0 ? z0 + a.nz : (z0 >= a.nz ? z0 - a.nz : z0)) >> 1;   // pair index
+        if constexpr (DOV) {
+            const uint4 ah = afrag[(4 * kk) * 32 + lane], al = afrag[(4 * kk + 1) * 32 + lane];
+            uint2 w0 = vp[zr], w1 = vp[zr + 4];           // pairs t and t + 4: (hi, lo)
+            w0.x &= vkeep; w0.y &= vkeep; w1.x &= vkeep; w1.y &= vkeep;
+            mma_bf16(av[0], ah.x, ah.y, ah.z, ah.w, w0.x, w1.x);
+            mma_bf16(av[1], al.x, al.y, al.z, al.w, w0.x, w1.x);
+            mma_bf16(av[2], ah.x, ah.y, ah.z, ah.w, w0.y, w1.y);
+        }
+        if constexpr (NPTW > 0) {
+            const uint4 fh = afrag[(4 * kk + 2) * 32 + lane], fl = afrag[(4 * kk + 3) * 32 + lane];
 #pragma unroll
-        for (int i = 0; i < NT; i++) {
-            uint2 w0 = cp[i][zr], w1 = cp[i][zr + 4];           // pairs t and t + 4: (hi, lo)
-            w0.x &= keep[i]; w0.y &= keep[i]; w1.x &= keep[i]; w1.y &= keep[i];
-            mma_bf16(acc[i][0], ah.x, ah.y, ah.z, ah.w, w0.x, w1.x);
-            mma_bf16(acc[i][1], al.x, al.y, al.z, al.w, w0.x, w1.x);
-            mma_bf16(acc[i][2], ah.x, ah.y, ah.z, ah.w, w0.y, w1.y);
+            for (int i = 0; i < NPTW; i++) {
+                const unsigned b0 = pp[i][zr] & pkeep[i], b1 = pp[i][zr + 4] & pkeep[i];
+                mma_f16(ap[i][0], fl.x, fl.y, fl.z, fl.w, b0, b1);
+                mma_f16(ap[i][1], fh.x, fh.y, fh.z, fh.w, b0, b1);
+            }
+        }
+    }
+    const size_t nh = (size_t)a.nsnap * NF * a.ny * a.nlz * a.nlx;
+    // h plane in (X, Z) order, Z fastest: the 8 rows g of a store are contiguous
+    auto put = [&](int f, int n, float r0, float r8) {
+        const size_t o = (((size_t)s * NF + f) * a.ny + j) * ((size_t)a.nlz * a.nlx) +
+                         (size_t)(X0 + a.OP * n) * a.nlz + 16 * zt;
+        if (in_range(o + g + 8, nh, a.err)) {
+            a.h[o + g] = r0;
+            a.h[o + g + 8] = r8;
+        }
+    };
+    if constexpr (DOV) {
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            const int cc = 2 * t + e;
+            const int n = cc >= 3 ? 1 : 0;
+            if (cc < PK::NV && (n ? val1 : val0))
+                put(cc - 3 * n, n, (av[0][e] + av[1][e]) + av[2][e], (av[0][2 + e] + av[1][2 + e]) + av[2][2 + e]);
         }
     }
 #pragma unroll
-    for (int i = 0; i < NT; i++)
+    for (int i = 0; i < NPTW; i++)
 #pragma unroll
         for (int e = 0; e < 2; e++) {
-            const int cc = (nt0 + i) * 8 + 2 * t + e;
-            if (cc >= OPC * NF) continue;
-            const int n = cc >= NF ? 1 : 0, f = cc - n * NF;
-            if (f >= a.nf || !(n ? val1 : val0)) continue;
-            // h plane in (X, Z) order, Z fastest: the 8 rows g of a store are contiguous
-            const size_t o = (((size_t)s * NF + f) * a.ny + j) * ((size_t)a.nlz * a.nlx) +
-                             (size_t)(X0 + a.OP * n) * a.nlz + 16 * zt;
-            const size_t nh = (size_t)a.nsnap * NF * a.ny * a.nlz * a.nlx;
-            if (in_range(o + g + 8, nh, a.err)) {
-                a.h[o + g] = (acc[i][0][e] + acc[i][1][e]) + acc[i][2][e];
-                a.h[o + g + 8] = (acc[i][0][2 + e] + acc[i][1][2 + e]) + acc[i][2][2 + e];
-            }
+            const int cc = (pt0 + i) * 8 + 2 * t + e;
+            const int n = cc >= 6 ? 1 : 0;
+            if (cc < PK::NP && (n ? val1 : val0))
+                put(3 + cc - 6 * n, n, ap[i][0][e] + ap[i][1][e], ap[i][0][2 + e] + ap[i][1][2 + e]);
         }
 }
 
@@ -330,16 +380,16 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
     constexpr int LD = G::LD, NXW = G::NXW, STGF = G::STGF;
     constexpr int NR = 8 / OPC;                  // B rotations
     constexpr int BW = Bw<MODE>::n;
-    constexpr int NCOL = OPC * NF;               // output columns parked per chunk
-    constexpr int NCBO = NCOL + 3;               // with the three row sums
+    using PK = Park<OPC>;
+    constexpr size_t PF = PK::floats(LD);        // floats per parked-column buffer
     extern __shared__ float4 smem_dyn[];
     const int KS = a.KS;
-    uint4 *afrag = reinterpret_cast<uint4 *>(smem_dyn);        // [KS][hi, lo][32 lanes]
-    uint4 *bvar = afrag + KS * 64;                              // [NR][32 lanes][BW]
-    float *colbuf = reinterpret_cast<float *>(bvar + NR * 32 * BW);   // [2 buffers][NCBO][LD]
+    uint4 *afrag = reinterpret_cast<uint4 *>(smem_dyn);        // [KS][4][32 lanes]
+    uint4 *bvar = afrag + KS * 128;                             // [NR][32 lanes][BW]
+    float *colbuf = reinterpret_cast<float *>(bvar + NR * 32 * BW);   // [2 buffers][PF]
     float *stg;                                                 // [CSTG][3][NZ][CW], 128-B aligned
     {
-        char *end = reinterpret_cast<char *>(colbuf + (size_t)2 * NCBO * LD);
+        char *end = reinterpret_cast<char *>(colbuf + 2 * PF);
         const unsigned sa = smem_u32(end);
         stg = reinterpret_cast<float *>(end + (((sa + 127u) & ~127u) - sa));
     }
@@ -403,7 +453,7 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
     // x and z warps: z fragments, this phase's rotated x fragments
     constexpr int nwork = G::THREADS - 32;
     const int wtid = tid - 32;
-    for (int i = wtid; i < KS * 64; i += nwork) afrag[i] = a.afrag[i];
+    for (int i = wtid; i < KS * 128; i += nwork) afrag[i] = a.afrag[i];
     for (int i = wtid; i < NR * 32 * BW; i += nwork) bvar[i] = a.bvar[(size_t)p * NR * 32 * BW + i];
     named_sync(1, nwork);
 
@@ -411,7 +461,7 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
     const int xw = warp - 1 - kZW;                // x warp index (rows 32 xw ..)
     if (xw >= 0) {   // ---------------- x warps
         const float *xrow = stg + (size_t)(xw * 32 + g) * CW + 4 * t;   // this lane's row g, inputs 4t..
-        float *colw0 = colbuf + xw * 32 + 2 * g;
+        float *colw0 = colbuf + xw * 32 + 2 * g;  // pair g of the warp's first block, velocity column 0
         // the reference profile U_c(y_j) of each item (uref, written by the
         // launch before), the next item's read one item ahead
         auto uref_of = [&](int it, float (&U)[3]) {
@@ -465,10 +515,20 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
                 if (gc >= 2 && !wait_or_abort(&cempty[cb], ((gc >> 1) - 1) & 1, abort_v, a.err, a.wait_limit)) { stop = true; break; }
                 const int X0 = xc0 + a.OP * OPC * sidx;
                 const int b0 = a.CB * sidx - a.bshift;     // first x block of the chunk
-                float *colw = colw0 + (size_t)cb * NCBO * LD;
+                float *colw = colw0 + (size_t)cb * PF;
+                unsigned *prodw = reinterpret_cast<unsigned *>(colbuf + (size_t)cb * PF + PK::prod0(LD)) + xw * 16 + g;
                 const int csum = (OPC * q + 7) & 7;        // the idle column: row sums
-                // rows (g, g + 8) of each 16-row block as one pair
-                auto park = [&](float *dst, float r0, float r8) { *reinterpret_cast<float2 *>(dst) = make_float2(r0, r8); };
+                // rows (g, g + 8) of each 16-row block as one pair: velocities as two
+                // FP32 values, products as one FP16x2 word
+                auto park = [&](int n, int m, int e) {
+#pragma unroll
+                    for (int f = 0; f < 3; f++)
+                        *reinterpret_cast<float2 *>(colw + (3 * n + f) * LD + 16 * m) =
+                            make_float2(acc[m][f][e], acc[m][f][2 + e]);
+#pragma unroll
+                    for (int f = 3; f < NF; f++)
+                        prodw[(6 * n + f - 3) * (LD / 2) + 8 * m] = pack_f16(acc[m][f][e], acc[m][f][2 + e]);
+                };
                 if constexpr (OPC == 2) {
                     // columns 2q, 2q + 1 (lanes t == q, elements 0 and 1)
                     if (t == q) {
@@ -476,10 +536,7 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
                         for (int n = 0; n < 2; n++)
                             if (X0 + a.OP * n >= 0 && X0 + a.OP * n < a.nlx) {
 #pragma unroll
-                                for (int m = 0; m < 2; m++)
-#pragma unroll
-                                    for (int f = 0; f < NF; f++)
-                                        park(colw + (n * NF + f) * LD + 16 * m, acc[m][f][n], acc[m][f][2 + n]);
+                                for (int m = 0; m < 2; m++) park(n, m, n);
                             }
                     }
                 } else {
@@ -487,18 +544,14 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
                     if (t == (q >> 1) && X0 >= 0 && X0 < a.nlx) {
                         if (q & 1) {
 #pragma unroll
-                            for (int m = 0; m < 2; m++)
-#pragma unroll
-                                for (int f = 0; f < NF; f++) park(colw + f * LD + 16 * m, acc[m][f][1], acc[m][f][3]);
+                            for (int m = 0; m < 2; m++) park(0, m, 1);
                         } else {
 #pragma unroll
-                            for (int m = 0; m < 2; m++)
-#pragma unroll
-                                for (int f = 0; f < NF; f++) park(colw + f * LD + 16 * m, acc[m][f][0], acc[m][f][2]);
+                            for (int m = 0; m < 2; m++) park(0, m, 0);
                         }
                     }
                 }
-                // row sums of fields 0-2 (the idle column) go to parked columns NCOL + c
+                // row sums of fields 0-2 (the idle column) go to the row-sum columns
                 // when the chunk's blocks are owned (each input counted once)
                 if (pm && t == (csum >> 1) && b0 >= 0 && b0 < a.nlx) {
                     const int es = csum & 1;
@@ -506,7 +559,7 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
                     for (int m = 0; m < 2; m++)
 #pragma unroll
                         for (int c = 0; c < 3; c++)
-                            *reinterpret_cast<float2 *>(colw + (NCOL + c) * LD + 16 * m) =
+                            *reinterpret_cast<float2 *>(colw + PK::sum0(LD) + c * LD + 16 * m) =
                                 es ? make_float2(acc[m][c][1], acc[m][c][3]) : make_float2(acc[m][c][0], acc[m][c][2]);
                 }
                 // clear the completed columns and the sum column without a branch; a
@@ -523,15 +576,16 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
                             acc[m][f][0] = lo.x; acc[m][f][1] = lo.y; acc[m][f][2] = hi.x; acc[m][f][3] = hi.y;
                         }
                 }
-                // split the warp's parked pairs into (hi, lo) bf16 words in place, all
-                // lanes sharing the work: NCOL columns x 2 blocks x 8 pairs
+                // split the warp's parked velocity pairs into (hi, lo) bf16 words in
+                // place, all lanes sharing the work: NV columns x 2 blocks x 8 pairs
                 __syncwarp();
                 {
-                    float *cw = colbuf + (size_t)cb * NCBO * LD + xw * 32;
+                    float *cw = colbuf + (size_t)cb * PF + xw * 32;
+                    constexpr int NPAIR = PK::NV * 16;
 #pragma unroll
-                    for (int r = 0; r < (NCOL * 16 + 31) / 32; r++) {
+                    for (int r = 0; r < (NPAIR + 31) / 32; r++) {
                         const int pidx = lane + 32 * r, col = pidx >> 4, off = pidx & 15;
-                        if (NCOL * 16 % 32 == 0 || pidx < NCOL * 16) {
+                        if (NPAIR % 32 == 0 || pidx < NPAIR) {
                             float2 *pp = reinterpret_cast<float2 *>(cw + (size_t)col * LD) + off;
                             unsigned hi, lo;
                             split2(*pp, hi, lo);
@@ -547,9 +601,10 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
     }
 
     // ---------------- z warps: with as many Z tiles as z warps, z warp zw takes
-    // tile zw and every column tile; otherwise the (Z tile, column tile) pairs
+    // tile zw and every column tile; otherwise the (Z tile, column tile) units
     // round robin.  z warp c < 3 also sums the parked row sums of component c.
-    constexpr int NCT = (NCOL + 7) / 8;          // column tiles
+    constexpr int NPT = PK::NPT;
+    const int npt = a.nf > 3 ? NPT : 0;          // product tiles only when the products are contracted
     const int zw = warp - 1;
     const int nzt = a.nlz / 16;
     int gc = 0;
@@ -563,21 +618,26 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
             const int X0 = xc0 + a.OP * OPC * sidx;
             const bool val0 = X0 >= 0 && X0 < a.nlx;
             const bool val1 = OPC == 2 && X0 + a.OP >= 0 && X0 + a.OP < a.nlx;
-            const float *colb = colbuf + (size_t)cb * NCBO * LD;
+            const float *colb = colbuf + (size_t)cb * PF;
             if (pm && zw < 3) {
                 const int b0 = a.CB * sidx - a.bshift;
                 if (b0 >= 0 && b0 < a.nlx) {
                     float ssum = 0.f;
-                    for (int z = lane; z < NZ; z += 32) ssum += colb[(NCOL + zw) * LD + z];
+                    for (int z = lane; z < NZ; z += 32) ssum += colb[PK::sum0(LD) + zw * LD + z];
                     pmean += (double)ssum;
                 }
             }
             if (val0 || val1) {
                 if (nzt == kZW) {
-                    z_tile<OPC, NCT, LD>(a, colb, afrag, s, j, X0, val0, val1, zw, 0, lane);
+                    if (npt) z_tile<OPC, LD, true, NPT>(a, colb, afrag, s, j, X0, val0, val1, zw, 0, lane);
+                    else z_tile<OPC, LD, true, 0>(a, colb, afrag, s, j, X0, val0, val1, zw, 0, lane);
                 } else {
-                    for (int w = zw; w < NCT * nzt; w += kZW)
-                        z_tile<OPC, 1, LD>(a, colb, afrag, s, j, X0, val0, val1, w / NCT, w % NCT, lane);
+                    const int nu = 1 + npt;          // per Z tile: the velocity tile, then each product tile
+                    for (int w = zw; w < nu * nzt; w += kZW) {
+                        const int u = w % nu, zt = w / nu;
+                        if (u == 0) z_tile<OPC, LD, true, 0>(a, colb, afrag, s, j, X0, val0, val1, zt, 0, lane);
+                        else z_tile<OPC, LD, false, 1>(a, colb, afrag, s, j, X0, val0, val1, zt, u - 1, lane);
+                    }
                 }
             }
             mbar_arrive(&cempty[cb]);
@@ -598,9 +658,8 @@ template <int NZ, int MODE, int OPC>
 size_t ws_smem_bytes(int KS)
 {
     using G = Geo<NZ>;
-    constexpr int NCBO = OPC * NF + 3;
-    return sizeof(uint4) * (64 * (size_t)KS + (8 / OPC) * 32 * Bw<MODE>::n) + 128 +
-           sizeof(float) * ((size_t)2 * NCBO * G::LD + (size_t)CSTG * G::STGF);
+    return sizeof(uint4) * (128 * (size_t)KS + (8 / OPC) * 32 * Bw<MODE>::n) + 128 +
+           sizeof(float) * (2 * Park<OPC>::floats(G::LD) + (size_t)CSTG * G::STGF);
 }
 
 // Launch over the plans of one class; the grid is as many CTAs as fit at
