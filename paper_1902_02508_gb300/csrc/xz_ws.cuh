@@ -10,7 +10,7 @@
 //   * one producer warp streams the plane through TMA stages of one chunk
 //     (16 x-inputs of every row, three components) with a full and an empty
 //     barrier per stage;
-//   * kZW z warps contract z (split BF16, tensor cores) for the outputs each
+//   * ZW z warps contract z (split BF16, tensor cores) for the outputs each
 //     chunk completes, from a double-buffered column buffer.  (An FP32 z
 //     phase on the CUDA cores was measured 2.4 times slower: the z warps are
 //     few, and a 63-tap FP32 dot product per output outweighs the banded MMAs.)
@@ -54,7 +54,6 @@ namespace ws {
 
 using namespace fz;
 
-constexpr int kZW = 3;               // z warps
 constexpr int CW = 16;               // floats per row per TMA stage: one chunk
 constexpr int CSTG = 2;              // stages in flight
 enum { MODE_BF16X3 = 0, MODE_TF32X2 = 1 };
@@ -360,12 +359,20 @@ __device__ __forceinline__ void named_sync(int id, int nthreads)
 }
 
 // Column stride of the parked columns (floats): +8 makes the 8-byte B loads
-// of the z warps conflict-free.
+// of the z warps conflict-free.  z warps: the z work of a chunk grows with
+// the LES z count, a larger share of the rows on the narrower grids (64 Z
+// outputs for 256 rows at stride 4, against 48 for 384 at stride 8), so the
+// 192- and 256-row kernels take as many z warps as their (Z tile, column
+// tile) units at stride 4 allow within the 512 threads that one CTA per SM
+// can hold at 128 registers (9 and 6); the 64- and 128-row kernels keep 3,
+// which lets two or three CTAs share an SM.
 template <int NZ>
 struct Geo {
     static constexpr int LD = NZ + 8;
     static constexpr int NXW = NZ / 32;                    // x warps
-    static constexpr int THREADS = NZ + 32 * (1 + kZW);
+    static constexpr int ZW = NZ == 192 ? 9 : NZ == 256 ? 6 : 3;   // z warps
+    static constexpr int THREADS = NZ + 32 * (1 + ZW);
+    static_assert(THREADS <= 512, "one CTA of at most 512 threads per SM");
     static constexpr int STGF = 3 * NZ * CW;               // floats per stage
 };
 
@@ -377,7 +384,7 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
     const WsArgs &a = mp.plan[pi];
     const int cta = (int)blockIdx.x - mp.cta0[pi], ncta = mp.cta0[pi + 1] - mp.cta0[pi];
     using G = Geo<NZ>;
-    constexpr int LD = G::LD, NXW = G::NXW, STGF = G::STGF;
+    constexpr int LD = G::LD, NXW = G::NXW, STGF = G::STGF, kZW = G::ZW;
     constexpr int NR = 8 / OPC;                  // B rotations
     constexpr int BW = Bw<MODE>::n;
     using PK = Park<OPC>;
