@@ -65,16 +65,23 @@ template <int MODE>
 struct Bw { static constexpr int n = MODE == MODE_TF32X2 ? 3 : 2; };
 
 // Parked columns of one buffer (floats): the velocity columns (3 per output,
-// LD floats: a (row g, row g + 8) pair as two FP32 values, split in place
-// into bf16 (hi, lo) words), the product columns (6 per output, LD / 2
-// words: a pair as one FP16x2 word) and the three row-sum columns (LD).
+// LD floats), the product columns (6 per output, LDP(LD) words) and the three
+// row-sum columns (LD).  Per 16-row block, pair i < 8 stands for rows
+// (i, i + 8).  A velocity block is parked as 8 FP32 pairs and then split into
+// bf16 words, stored as 8 uint2 slots: slot i' < 4 holds (hi of pair i', hi
+// of pair i' + 4) and slot 4 + i' the two lo words, so that one 8-byte load
+// is the B operand (k rows 2t, 2t + 1 and 2t + 8, 2t + 9) of one split
+// product.  A product block is 8 FP16x2 words in the order pair 0, 4, 1, 5,
+// 2, 6, 3, 7 (one 8-byte load per B operand likewise).  Column strides of 8
+// (mod 32) words keep the z warps' 8-byte loads conflict-free.
 template <int OPC>
 struct Park {
     static constexpr int NV = 3 * OPC, NP = 6 * OPC;   // velocity, product columns
     static constexpr int NVT = 1, NPT = (NP + 7) / 8;  // column tiles of each kind
-    __host__ __device__ static constexpr size_t floats(int LD) { return (size_t)(NV + 3) * LD + (size_t)NP * (LD / 2); }
+    __host__ __device__ static constexpr int LDP(int LD) { return LD / 2 + 4; }   // product column stride
+    __host__ __device__ static constexpr size_t floats(int LD) { return (size_t)(NV + 3) * LD + (size_t)NP * LDP(LD); }
     __host__ __device__ static constexpr size_t prod0(int LD) { return (size_t)NV * LD; }
-    __host__ __device__ static constexpr size_t sum0(int LD) { return (size_t)NV * LD + (size_t)NP * (LD / 2); }
+    __host__ __device__ static constexpr size_t sum0(int LD) { return (size_t)NV * LD + (size_t)NP * LDP(LD); }
 };
 
 struct WsArgs {
@@ -257,38 +264,31 @@ __device__ __forceinline__ bool wait_or_abort(unsigned long long *bar, unsigned 
 // product column tiles pt0 .. pt0 + NPTW - 1 (8 columns each; velocity
 // column c = 3 n + f, product column c = 6 n + f - 3, for output X0 + OP n),
 // KS k-steps over the tile's z window, each A fragment loaded once per
-// k-step for all the tiles.  A parked column holds, per 16-row block and pair
-// i < 8, rows (i, i + 8): a velocity pair as its bf16 (hi, lo) words, a
-// product pair as one FP16x2 word; the k index of a k-step runs over the
-// block's rows in the order k = 2i + e -> row i + 8e, which the A fragments
-// follow.  The window starts on a 16-row boundary (zoff is a multiple of 16),
-// so a k-step wraps periodically as a whole or not at all.  Lanes whose
-// column is idle use zeros.  Outputs go to h in (X, Z) plane order (Z
-// fastest), so that each store instruction writes 4 runs of 8 consecutive
-// floats instead of 32 scattered ones (a chunk completes whole Z columns of
-// one or two X); the y passes transpose back.
+// k-step for all the tiles.  The k index of a k-step runs over a 16-row
+// block's rows in the order k = 2i + e -> row i + 8e (pair i, element e),
+// which the A fragments follow; each B operand is one 8-byte load (the slot
+// order of Park).  The window starts on a 16-row boundary (zoff is a multiple
+// of 16), so a k-step wraps periodically as a whole or not at all.  Lanes
+// whose column is idle read column 0: an MMA's output column depends on its
+// own B column only, and idle output columns are never stored.  Outputs go to
+// h in (X, Z) plane order (Z fastest), so that each store instruction writes
+// 4 runs of 8 consecutive floats instead of 32 scattered ones (a chunk
+// completes whole Z columns of one or two X); the y passes transpose back.
 template <int OPC, int LD, bool DOV, int NPTW>
 __device__ __forceinline__ void z_tile(const WsArgs &a, const float *colb, const uint4 *afrag,
                                        int s, int j, int X0, bool val0, bool val1, int zt, int pt0, int lane)
 {
     using PK = Park<OPC>;
     constexpr int NPA = NPTW > 0 ? NPTW : 1;
+    constexpr int LDP = PK::LDP(LD);
     const int g = lane >> 2, t = lane & 3;
-    const uint2 *vp = nullptr;
-    unsigned vkeep = 0u;                          // all ones for a live column, zero for an idle one
-    if constexpr (DOV) {
-        const bool live = g < PK::NV && (g < 3 ? val0 : val1);
-        vp = reinterpret_cast<const uint2 *>(colb + (size_t)(live ? g : 0) * LD) + t;
-        vkeep = live ? 0xffffffffu : 0u;
-    }
-    const unsigned *pp[NPA];
-    unsigned pkeep[NPA];
+    const uint2 *vp = nullptr;                    // slot t of each block: +8 per 16 rows
+    if constexpr (DOV) vp = reinterpret_cast<const uint2 *>(colb + (size_t)(g < PK::NV ? g : 0) * LD) + t;
+    const uint2 *pp[NPA];                         // word pair t of each block: +4 per 16 rows
 #pragma unroll
     for (int i = 0; i < NPTW; i++) {
         const int c = (pt0 + i) * 8 + g;
-        const bool live = c < PK::NP && (c < 6 ? val0 : val1);
-        pp[i] = reinterpret_cast<const unsigned *>(colb + PK::prod0(LD)) + (size_t)(live ? c : 0) * (LD / 2) + t;
-        pkeep[i] = live ? 0xffffffffu : 0u;
+        pp[i] = reinterpret_cast<const uint2 *>(colb + PK::prod0(LD) + (size_t)(c < PK::NP ? c : 0) * LDP) + t;
     }
     float av[3][4], ap[NPA][2][4];   // one accumulator per split product: independent chains
 #pragma unroll
@@ -301,36 +301,40 @@ __device__ __forceinline__ void z_tile(const WsArgs &a, const float *colb, const
         for (int r = 0; r < 2; r++)
 #pragma unroll
             for (int e = 0; e < 4; e++) ap[i][r][e] = 0.f;
-    int z0 = 16 * a.RZ * zt - a.zoff;
+    // 16-row block index of the first k-step, periodic in the nz / 16 blocks
+    const int nb = a.nz >> 4;
+    int blk = (16 * a.RZ * zt - a.zoff) >> 4;
+    if (blk < 0) blk += nb;
+    const uint4 *af = afrag + lane;
 #pragma unroll 2
-    for (int kk = 0; kk < a.KS; kk++, z0 += 16) {
-        const int zr = (z0 < 0 ? z0 + a.nz : (z0 >= a.nz ? z0 - a.nz : z0)) >> 1;   // pair index
+    for (int kk = 0; kk < a.KS; kk++, af += 128) {
         if constexpr (DOV) {
-            const uint4 ah = afrag[(4 * kk) * 32 + lane], al = afrag[(4 * kk + 1) * 32 + lane];
-            uint2 w0 = vp[zr], w1 = vp[zr + 4];           // pairs t and t + 4: (hi, lo)
-            w0.x &= vkeep; w0.y &= vkeep; w1.x &= vkeep; w1.y &= vkeep;
-            mma_bf16(av[0], ah.x, ah.y, ah.z, ah.w, w0.x, w1.x);
-            mma_bf16(av[1], al.x, al.y, al.z, al.w, w0.x, w1.x);
-            mma_bf16(av[2], ah.x, ah.y, ah.z, ah.w, w0.y, w1.y);
+            const uint4 ah = af[0], al = af[32];
+            const uint2 bh = vp[8 * blk], bl = vp[8 * blk + 4];   // (hi, hi) and (lo, lo) of pairs t, t + 4
+            mma_bf16(av[0], ah.x, ah.y, ah.z, ah.w, bh.x, bh.y);
+            mma_bf16(av[1], al.x, al.y, al.z, al.w, bh.x, bh.y);
+            mma_bf16(av[2], ah.x, ah.y, ah.z, ah.w, bl.x, bl.y);
         }
         if constexpr (NPTW > 0) {
-            const uint4 fh = afrag[(4 * kk + 2) * 32 + lane], fl = afrag[(4 * kk + 3) * 32 + lane];
+            const uint4 fh = af[64], fl = af[96];
 #pragma unroll
             for (int i = 0; i < NPTW; i++) {
-                const unsigned b0 = pp[i][zr] & pkeep[i], b1 = pp[i][zr + 4] & pkeep[i];
-                mma_f16(ap[i][0], fl.x, fl.y, fl.z, fl.w, b0, b1);
-                mma_f16(ap[i][1], fh.x, fh.y, fh.z, fh.w, b0, b1);
+                const uint2 b = pp[i][4 * blk];
+                mma_f16(ap[i][0], fl.x, fl.y, fl.z, fl.w, b.x, b.y);
+                mma_f16(ap[i][1], fh.x, fh.y, fh.z, fh.w, b.x, b.y);
             }
         }
+        if (++blk == nb) blk = 0;
     }
-    const size_t nh = (size_t)a.nsnap * NF * a.ny * a.nlz * a.nlx;
     // h plane in (X, Z) order, Z fastest: the 8 rows g of a store are contiguous
+    const size_t nh = (size_t)a.nsnap * NF * a.ny * a.nlz * a.nlx;
+    const size_t fstride = (size_t)a.ny * a.nlz * a.nlx;
+    const size_t base = ((size_t)s * NF * a.ny + j) * ((size_t)a.nlz * a.nlx) + (size_t)X0 * a.nlz + 16 * zt + g;
     auto put = [&](int f, int n, float r0, float r8) {
-        const size_t o = (((size_t)s * NF + f) * a.ny + j) * ((size_t)a.nlz * a.nlx) +
-                         (size_t)(X0 + a.OP * n) * a.nlz + 16 * zt;
-        if (in_range(o + g + 8, nh, a.err)) {
-            a.h[o + g] = r0;
-            a.h[o + g + 8] = r8;
+        const size_t o = base + (size_t)f * fstride + (size_t)(a.OP * n) * a.nlz;
+        if (in_range(o + 8, nh, a.err)) {
+            a.h[o] = r0;
+            a.h[o + 8] = r8;
         }
     };
     if constexpr (DOV) {
@@ -523,7 +527,9 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
                 const int X0 = xc0 + a.OP * OPC * sidx;
                 const int b0 = a.CB * sidx - a.bshift;     // first x block of the chunk
                 float *colw = colw0 + (size_t)cb * PF;
-                unsigned *prodw = reinterpret_cast<unsigned *>(colbuf + (size_t)cb * PF + PK::prod0(LD)) + xw * 16 + g;
+                // product pair g of a block goes to word 2 (g mod 4) + g / 4 (Park's order)
+                unsigned *prodw = reinterpret_cast<unsigned *>(colbuf + (size_t)cb * PF + PK::prod0(LD)) + xw * 16 +
+                                  2 * (g & 3) + (g >> 2);
                 const int csum = (OPC * q + 7) & 7;        // the idle column: row sums
                 // rows (g, g + 8) of each 16-row block as one pair: velocities as two
                 // FP32 values, products as one FP16x2 word
@@ -534,7 +540,7 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
                             make_float2(acc[m][f][e], acc[m][f][2 + e]);
 #pragma unroll
                     for (int f = 3; f < NF; f++)
-                        prodw[(6 * n + f - 3) * (LD / 2) + 8 * m] = pack_f16(acc[m][f][e], acc[m][f][2 + e]);
+                        prodw[(6 * n + f - 3) * PK::LDP(LD) + 8 * m] = pack_f16(acc[m][f][e], acc[m][f][2 + e]);
                 };
                 if constexpr (OPC == 2) {
                     // columns 2q, 2q + 1 (lanes t == q, elements 0 and 1)
@@ -583,20 +589,25 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
                             acc[m][f][0] = lo.x; acc[m][f][1] = lo.y; acc[m][f][2] = hi.x; acc[m][f][3] = hi.y;
                         }
                 }
-                // split the warp's parked velocity pairs into (hi, lo) bf16 words in
-                // place, all lanes sharing the work: NV columns x 2 blocks x 8 pairs
+                // split the warp's parked velocity pairs into (hi, lo) bf16 words,
+                // all lanes sharing the work (NV columns x 2 blocks x 8 pairs), and
+                // store them in Park's slot order within each block (a round reads
+                // its blocks whole before any lane writes)
                 __syncwarp();
                 {
                     float *cw = colbuf + (size_t)cb * PF + xw * 32;
                     constexpr int NPAIR = PK::NV * 16;
 #pragma unroll
                     for (int r = 0; r < (NPAIR + 31) / 32; r++) {
-                        const int pidx = lane + 32 * r, col = pidx >> 4, off = pidx & 15;
-                        if (NPAIR % 32 == 0 || pidx < NPAIR) {
-                            float2 *pp = reinterpret_cast<float2 *>(cw + (size_t)col * LD) + off;
-                            unsigned hi, lo;
-                            split2(*pp, hi, lo);
-                            *reinterpret_cast<uint2 *>(pp) = make_uint2(hi, lo);
+                        const int pidx = lane + 32 * r, col = pidx >> 4, off = pidx & 15, i = off & 7;
+                        const bool act = NPAIR % 32 == 0 || pidx < NPAIR;
+                        unsigned *blk = reinterpret_cast<unsigned *>(cw + (size_t)(act ? col : 0) * LD + 16 * (off >> 3));
+                        unsigned hi = 0u, lo = 0u;
+                        if (act) split2(*reinterpret_cast<const float2 *>(blk + 2 * i), hi, lo);
+                        __syncwarp();
+                        if (act) {
+                            blk[2 * (i & 3) + (i >> 2)] = hi;
+                            blk[8 + 2 * (i & 3) + (i >> 2)] = lo;
                         }
                     }
                 }
