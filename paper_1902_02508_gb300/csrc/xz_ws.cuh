@@ -235,6 +235,60 @@ __device__ __forceinline__ void x_mma(float (&acc)[NF][4], const float2 (&v)[3][
     if constexpr (nx >= 0) x_mma<MODE, nx>(acc, v, B);
 }
 
+// BF16X3 x contraction with the MMAs of two fields interleaved, so that the
+// dependent MMAs of one accumulator are issued apart: (u'1, u'1u'1),
+// (u'1u'2, u'1u'3), (u'2, u'2u'2), (u'3, u'2u'3), u'3u'3.
+template <int F>
+__device__ __forceinline__ void vel_split(const float2 (&v)[3][2][2], unsigned (&ah)[4], unsigned (&al)[4])
+{
+    split2(field2<F>(v[0][0][0], v[1][0][0], v[2][0][0]), ah[0], al[0]);
+    split2(field2<F>(v[0][1][0], v[1][1][0], v[2][1][0]), ah[1], al[1]);
+    split2(field2<F>(v[0][0][1], v[1][0][1], v[2][0][1]), ah[2], al[2]);
+    split2(field2<F>(v[0][1][1], v[1][1][1], v[2][1][1]), ah[3], al[3]);
+}
+template <int F>
+__device__ __forceinline__ void prod_pack(const float2 (&v)[3][2][2], unsigned (&a)[4])
+{
+    a[0] = pack_f16_2(field2<F>(v[0][0][0], v[1][0][0], v[2][0][0]));
+    a[1] = pack_f16_2(field2<F>(v[0][1][0], v[1][1][0], v[2][1][0]));
+    a[2] = pack_f16_2(field2<F>(v[0][0][1], v[1][0][1], v[2][0][1]));
+    a[3] = pack_f16_2(field2<F>(v[0][1][1], v[1][1][1], v[2][1][1]));
+}
+template <int FV, int FP>
+__device__ __forceinline__ void vp_pair(float (&acc)[NF][4], const float2 (&v)[3][2][2], const uint4 &bv, const uint4 &bp)
+{
+    unsigned ah[4], al[4], a[4];
+    vel_split<FV>(v, ah, al);
+    prod_pack<FP>(v, a);
+    mma_bf16(acc[FV], ah[0], ah[1], ah[2], ah[3], bv.x, bv.y);
+    mma_f16(acc[FP], a[0], a[1], a[2], a[3], bp.z, bp.w);
+    mma_bf16(acc[FV], al[0], al[1], al[2], al[3], bv.x, bv.y);
+    mma_f16(acc[FP], a[0], a[1], a[2], a[3], bp.x, bp.y);
+    mma_bf16(acc[FV], ah[0], ah[1], ah[2], ah[3], bv.z, bv.w);
+}
+template <int F1, int F2>
+__device__ __forceinline__ void pp_pair(float (&acc)[NF][4], const float2 (&v)[3][2][2], const uint4 &bp)
+{
+    unsigned a[4], b[4];
+    prod_pack<F1>(v, a);
+    prod_pack<F2>(v, b);
+    mma_f16(acc[F1], a[0], a[1], a[2], a[3], bp.z, bp.w);
+    mma_f16(acc[F2], b[0], b[1], b[2], b[3], bp.z, bp.w);
+    mma_f16(acc[F1], a[0], a[1], a[2], a[3], bp.x, bp.y);
+    mma_f16(acc[F2], b[0], b[1], b[2], b[3], bp.x, bp.y);
+}
+__device__ __forceinline__ void x_mma_il(float (&acc)[NF][4], const float2 (&v)[3][2][2], const uint4 (&B)[2])
+{
+    vp_pair<0, 3>(acc, v, B[0], B[1]);
+    pp_pair<4, 5>(acc, v, B[1]);
+    vp_pair<1, 6>(acc, v, B[0], B[1]);
+    vp_pair<2, 7>(acc, v, B[0], B[1]);
+    unsigned a[4];
+    prod_pack<8>(v, a);
+    mma_f16(acc[8], a[0], a[1], a[2], a[3], B[1].z, B[1].w);
+    mma_f16(acc[8], a[0], a[1], a[2], a[3], B[1].x, B[1].y);
+}
+
 __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
@@ -518,7 +572,8 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
                             v[c][h][1] = __fadd2_rn(make_float2(x.z, x.w), nU);
                         }
                     }
-                    x_mma<MODE, 0>(acc[m], v, B);
+                    if constexpr (MODE == MODE_BF16X3) x_mma_il(acc[m], v, B);
+                    else x_mma<MODE, 0>(acc[m], v, B);
                 }
                 mbar_arrive(&empty[st]);
                 // the chunk completes phase outputs X0 + OP i, i < OPC (tile columns OPC q + i)
@@ -544,13 +599,14 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
                 };
                 if constexpr (OPC == 2) {
                     // columns 2q, 2q + 1 (lanes t == q, elements 0 and 1)
+                    // block m = 0 first: its MMAs were issued before those of m = 1
                     if (t == q) {
+                        const bool ok0 = X0 >= 0 && X0 < a.nlx, ok1 = X0 + a.OP >= 0 && X0 + a.OP < a.nlx;
 #pragma unroll
-                        for (int n = 0; n < 2; n++)
-                            if (X0 + a.OP * n >= 0 && X0 + a.OP * n < a.nlx) {
-#pragma unroll
-                                for (int m = 0; m < 2; m++) park(n, m, n);
-                            }
+                        for (int m = 0; m < 2; m++) {
+                            if (ok0) park(0, m, 0);
+                            if (ok1) park(1, m, 1);
+                        }
                     }
                 } else {
                     // column q (lanes t == q / 2, element q % 2)
