@@ -454,9 +454,11 @@ int ef_closure_features(const ef_grid *les, const float *ubar, double re_tau, in
  * fixed device array of 4096 doubles (32 KB) that every device loading the
  * library holds until exit; les->ny above 4096 is rejected with EF_ERR_ARG.
  * The first call on a device looks up that array's address (make it before
- * any stream capture).  All calls share the array: calls that overlap on the
- * GPU race, so issue them on one stream.  Other arguments and errors as
- * ef_closure_features.
+ * any stream capture).  Every call copies les->y from the caller's host
+ * memory into the array with cudaMemcpyAsync on `stream`, so the host array
+ * must stay valid until that copy has run.  All calls share the array: calls
+ * that overlap on the GPU race, so issue them on one stream.  Other
+ * arguments and errors as ef_closure_features.
  */
 int ef_closure_features_static(const ef_grid *les, const float *ubar, double re_tau, int extension, float *feats,
                                void *stream);
