@@ -121,6 +121,7 @@ struct YTcGeom {
     int koff[kYMaxTiles] = {};     // their offset in the fragment table
     int kstot = 0;                 // k-steps of all tiles
     int box_rows = 0;              // TMA box rows (two boxes stage the band rows of every tile)
+    int dzero[kYMaxTiles] = {};    // 1: A_y^- = A_y^+ on every row of tile mt (its wall term d is zero)
 };
 struct YTcArgs {
     CUtensorMap hmap;              // TMA view of h: {nplane, 9 ny S} floats, box {36, box_rows}

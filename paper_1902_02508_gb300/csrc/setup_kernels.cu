@@ -268,6 +268,20 @@ int build_wall_rows(ef_plan *p, const double *h_les_y)
     e = cudaMemcpy(sta.data(), p->d_ystart, sizeof(int) * p->nly, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "read y starts");
     p->ytc_fit = (p->prec == EF_PREC_BF16X3 || p->prec == EF_PREC_TF32X2) && ytc_geometry(sta, cnt, p->ny, p->nlz * p->nlx, &p->ytc);
+    if (p->ytc_fit) {
+        // row tiles whose filter never meets a wall: A_y^- and A_y^+ agree on every
+        // row, so the wall term d = (A^- - A^+) h is zero there
+        std::vector<double> we(dense), wo(dense);
+        e = cudaMemcpy(we.data(), p->d_yw64[0], sizeof(double) * dense, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(wo.data(), p->d_yw64[1], sizeof(double) * dense, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "read y operators");
+        for (int mt = 0; mt < p->ytc.nmt; mt++) {
+            bool same = true;
+            for (int J = 16 * mt; J < 16 * mt + 16 && J < p->nly && same; J++)
+                for (int j = 0; j < p->ny && same; j++) same = we[(size_t)J * p->ny + j] == wo[(size_t)J * p->ny + j];
+            p->ytc.dzero[mt] = same ? 1 : 0;
+        }
+    }
     p->ytc_ok = p->ytc_fit;
     return EF_OK;
 }

@@ -78,7 +78,10 @@ double bweight(const Ring &r, int xi, int n, int xc0, int OP, int bshift)
 }
 
 // Reference profile U_c(y_j): the mean of z-row 0 of each plane, one warp
-// per (component, plane, snapshot), FP64 sum.
+// per (component, plane, snapshot).  Any profile makes the decomposition
+// exact; this one is stored rounded to FP32, and the kernel and the recovery
+// both use the stored value.  Each lane sums its 16-byte pieces of the row in
+// FP32 (four for nx = 512), the lanes' sums are added in FP64.
 __global__ void __launch_bounds__(96) ws_uref(const float *__restrict__ u, int nx, int ny, int nz, double *uref,
                                                int *err)
 {
@@ -86,8 +89,20 @@ __global__ void __launch_bounds__(96) ws_uref(const float *__restrict__ u, int n
     const size_t r0 = (((size_t)s * 3 + c) * ny + j) * (size_t)nz * nx;
     const size_t nu = (size_t)gridDim.y * 3 * ny * nz * nx;
     double acc = 0.0;
-    for (int i = lane; i < nx; i += 32)
-        if (in_range(r0 + i, nu, err)) acc += (double)u[r0 + i];
+    if ((nx & 3) == 0) {   // rows start on 16-byte boundaries (u is 16-byte aligned for TMA)
+        const float4 *q = reinterpret_cast<const float4 *>(u + r0);
+        float part = 0.f;
+#pragma unroll 4
+        for (int i = lane; i < nx / 4; i += 32)
+            if (in_range(r0 + 4 * (size_t)i + 3, nu, err)) {
+                const float4 v = __ldg(q + i);
+                part += (v.x + v.y) + (v.z + v.w);
+            }
+        acc = part;
+    } else {
+        for (int i = lane; i < nx; i += 32)
+            if (in_range(r0 + i, nu, err)) acc += (double)u[r0 + i];
+    }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     const size_t k = ((size_t)s * 3 + c) * ny + j;
     if (lane == 0 && in_range(k, (size_t)gridDim.y * 3 * ny, err)) uref[k] = (double)(float)(acc / nx);

@@ -73,7 +73,8 @@ __device__ __forceinline__ void tma_load2(void *dst, const CUtensorMap *map, uns
 // Parity index (0 even, 1 odd) of the product of components a and b.
 __host__ __device__ constexpr int pprod(int a, int b) { return ((a == 1) != (b == 1)) ? 1 : 0; }
 
-// Operator fragments: block (k-step kg of all tiles, operator op, snapshot s),
+// Operator fragments: block (k-step kg of all tiles, operator op, snapshot s;
+// the operators 0-2 for snapshot 0 only),
 // lane (g, t) holds A[g][2t..2t+1], A[g+8][2t..2t+1], A[g][2t+8..2t+9],
 // A[g+8][2t+8..2t+9] of the tile's k-step, A[m][k] = op(J = 16 mt + m,
 // j = jb + 16 kk + k), the operators numbered as above.
@@ -82,6 +83,7 @@ __global__ void yfrag_kernel(const YTcGeom g, const double *__restrict__ we, con
                              uint4 *frag)
 {
     const int kg = blockIdx.x, op = blockIdx.y, s = blockIdx.z, lane = threadIdx.x;
+    if (op < 3 && s > 0) return;   // A_y^+, A_y^-, A_y^- - A_y^+ do not depend on U: snapshot 0's serve all
     int mt = 0;
     while (mt + 1 < g.nmt && g.koff[mt + 1] <= kg) mt++;
     const int kk = kg - g.koff[mt];
@@ -177,9 +179,11 @@ __global__ void __launch_bounds__(YTW * 32, 5) ytc_kernel(const __grid_constant_
         const int opo = NOPS == 5 ? (o == 0 ? ((F == 1) != (a.flip != 0) ? 1 : 0)
                                    : o == 1 ? 2 : 3 + 2 * (o - 2) + pprod(o - 2, F))
                                   : ((F == 4 || F == 7) ? 1 : 0);
-        const uint4 *fo = a.frag + (((size_t)s * kYOps + opo) * geo.kstot + geo.koff[mt]) * 64 + lane;
+        const size_t sf = opo < 3 ? 0 : s;            // the U-free operators are built for snapshot 0 only
+        const uint4 *fo = a.frag + ((sf * kYOps + opo) * geo.kstot + geo.koff[mt]) * 64 + lane;
         uint4 ah = __ldg(fo), al = __ldg(fo + 32);
-        const int ks = geo.ks[mt];
+        // the wall term d of a row tile that never meets a wall is zero: no MMAs
+        const int ks = NOPS == 5 && o == 1 && geo.dzero[mt] ? 0 : geo.ks[mt];
         for (int kk = 0; kk < ks; kk++) {
             uint4 nah = ah, nal = al;
             if (kk + 1 < ks) {
