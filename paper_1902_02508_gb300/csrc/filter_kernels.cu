@@ -439,7 +439,8 @@ int y_stage(ef_plan *p, int ns, T *ubar, T *tau, bool stress, cudaStream_t s, co
     cudaError_t e = cudaSuccess;
     T *wy = static_cast<T *>(p->d_wy);
     e = launch_yprofile<T>(p->d_uref, p->d_ystart, p->d_ycount, p->d_yw64[0], p->d_yw64[1], p->ny, p->nly,
-                           p->ext == EF_EXT_ODD_EVEN, ns, p->d_AU, p->d_AUU, wy, p->d_Kab, s);
+                           p->ext == EF_EXT_ODD_EVEN, ns, p->d_AU, p->d_AUU,
+                           sizeof(T) == 4 && p->ytc_ok ? nullptr : wy, p->d_Kab, s);
     if (e != cudaSuccess) return cuda_fail(e, "yprofile launch");
     if constexpr (sizeof(T) == 4) {
         if (p->ytc_ok) {   // tensor-core y passes (split-precision plans)

@@ -289,6 +289,47 @@ __device__ __forceinline__ void x_mma_il(float (&acc)[NF][4], const float2 (&v)[
     mma_f16(acc[8], a[0], a[1], a[2], a[3], B[1].x, B[1].y);
 }
 
+// TF32X2 x contraction with the first k-half of each velocity field
+// interleaved with the MMAs of a product field (same pairs as x_mma_il).
+template <int FV>
+__device__ __forceinline__ void tf32_half(const float2 (&v)[3][2][2], int k2, unsigned (&h)[4], unsigned (&l)[4])
+{
+    const float2 x0 = v[FV][0][k2], x1 = v[FV][1][k2];     // rows g, g + 8
+    h[0] = __float_as_uint(x0.x) & 0xffffe000u; h[2] = __float_as_uint(x0.y) & 0xffffe000u;
+    h[1] = __float_as_uint(x1.x) & 0xffffe000u; h[3] = __float_as_uint(x1.y) & 0xffffe000u;
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 l0 = __ffma2_rn(make_float2(__uint_as_float(h[0]), __uint_as_float(h[2])), m1, x0);
+    const float2 l1 = __ffma2_rn(make_float2(__uint_as_float(h[1]), __uint_as_float(h[3])), m1, x1);
+    l[0] = __float_as_uint(l0.x); l[1] = __float_as_uint(l1.x); l[2] = __float_as_uint(l0.y); l[3] = __float_as_uint(l1.y);
+}
+template <int FV, int FP>
+__device__ __forceinline__ void vp_pair_tf32(float (&acc)[NF][4], const float2 (&v)[3][2][2], const uint4 (&B)[3])
+{
+    unsigned h[4], l[4], a[4];
+    tf32_half<FV>(v, 0, h, l);
+    prod_pack<FP>(v, a);
+    mma_tf32(acc[FV], h[0], h[1], h[2], h[3], B[0].x, B[0].y);
+    mma_f16(acc[FP], a[0], a[1], a[2], a[3], B[2].z, B[2].w);
+    mma_tf32(acc[FV], l[0], l[1], l[2], l[3], B[0].x, B[0].y);
+    mma_f16(acc[FP], a[0], a[1], a[2], a[3], B[2].x, B[2].y);
+    mma_tf32(acc[FV], h[0], h[1], h[2], h[3], B[0].z, B[0].w);
+    tf32_half<FV>(v, 1, h, l);
+    mma_tf32(acc[FV], h[0], h[1], h[2], h[3], B[1].x, B[1].y);
+    mma_tf32(acc[FV], l[0], l[1], l[2], l[3], B[1].x, B[1].y);
+    mma_tf32(acc[FV], h[0], h[1], h[2], h[3], B[1].z, B[1].w);
+}
+__device__ __forceinline__ void x_mma_il_tf32(float (&acc)[NF][4], const float2 (&v)[3][2][2], const uint4 (&B)[3])
+{
+    vp_pair_tf32<0, 3>(acc, v, B);
+    pp_pair<4, 5>(acc, v, B[2]);
+    vp_pair_tf32<1, 6>(acc, v, B);
+    vp_pair_tf32<2, 7>(acc, v, B);
+    unsigned a[4];
+    prod_pack<8>(v, a);
+    mma_f16(acc[8], a[0], a[1], a[2], a[3], B[2].z, B[2].w);
+    mma_f16(acc[8], a[0], a[1], a[2], a[3], B[2].x, B[2].y);
+}
+
 __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
@@ -573,7 +614,7 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
                         }
                     }
                     if constexpr (MODE == MODE_BF16X3) x_mma_il(acc[m], v, B);
-                    else x_mma<MODE, 0>(acc[m], v, B);
+                    else x_mma_il_tf32(acc[m], v, B);
                 }
                 mbar_arrive(&empty[st]);
                 // the chunk completes phase outputs X0 + OP i, i < OPC (tile columns OPC q + i)

@@ -32,16 +32,17 @@ __global__ void __launch_bounds__(YPT) yprofile_kernel(const double *__restrict_
     const double *U = uref + (size_t)s * 3 * ny;
     double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     const int st = ystart[J], cnt = ycount[J];
-    T *out = wy + ((size_t)s * nly + J) * ny * 8;
     for (int t = threadIdx.x; t < cnt; t += YPT) {
         const int j = st + t;
         const double wev = we[(size_t)J * ny + j], wod = wo[(size_t)J * ny + j];
         const double u[3] = {U[j], U[ny + j], U[2 * ny + j]};
         for (int c = 0; c < 3; c++) acc[c] += (pv[c] > 0 ? wev : wod) * u[c];
         for (int k = 0; k < 6; k++) acc[3 + k] += (pv[PI[k]] * pv[PJ[k]] > 0 ? wev : wod) * u[PI[k]] * u[PJ[k]];
-        T *o = out + (size_t)t * 8;
-        o[0] = (T)wev; o[1] = (T)wod;
-        for (int c = 0; c < 3; c++) { o[2 + 2 * c] = (T)(u[c] * wev); o[3 + 2 * c] = (T)(u[c] * wod); }
+        if (wy) {   // the tap table of the CUDA-core y pass (not needed by the tensor-core one)
+            T *o = wy + (((size_t)s * nly + J) * ny + t) * 8;
+            o[0] = (T)wev; o[1] = (T)wod;
+            for (int c = 0; c < 3; c++) { o[2 + 2 * c] = (T)(u[c] * wev); o[3 + 2 * c] = (T)(u[c] * wod); }
+        }
     }
     __shared__ double part[9][YPT / 32];
     for (int k = 0; k < 9; k++) {
