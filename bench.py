@@ -4,9 +4,11 @@ Workload (default, the Re_tau ~ 550 precision form): DNS 512 x 257 x 384 in
 a 2 pi x 2 x pi box, tanh-stretched y, filtered with a Gaussian of constant
 width Delta = Lx / 64 (wall extension of Eq. 7) onto a 64 x 65 x 48 LES grid
 with split-BF16 tensor-core contractions; one step = ~bar(u_i), T_ij and the
-plane means of 8 seeded synthetic snapshots.  Inputs are 8 x 607 MB = 4.9 GB
-per step, far larger than the 129 MB L2, so no flush is needed between
-steps.  `--workload re550_d32` is the same with Delta = Lx / 32;
+plane means of 10 seeded synthetic snapshots.  Inputs are 10 x 607 MB = 6.1
+GB per step, far larger than the 129 MB L2, so no flush is needed between
+steps.  Ten snapshots are 2570 (snapshot, y-plane) items of the persistent
+x-z kernel, 16.9 per SM on 152 SMs, so its last wave is 90 % full (eight
+give 13.5 per SM and a last wave half full).  `--workload re550_d32` is the same with Delta = Lx / 32;
 `--workload re180` selects the 192 x 129 x 192 -> 32 x 33 x 32,
 Delta = Lx / 32 channel (10 snapshots per step).  `--precision` picks the
 split form (bf16x3, the default, or tf32x2) or fp32 / fp64.
@@ -58,8 +60,8 @@ UNIT = "DNS points/s"
 WORKLOADS = {
     # name: (nx, ny, nz, Lx, Lz, nlx, nly, nlz, delta/Lx, snapshots per step)
     "re180": (192, 129, 192, 4 * math.pi, 2 * math.pi, 32, 33, 32, 1 / 32, 10),
-    "re550_d64": (512, 257, 384, 2 * math.pi, math.pi, 64, 65, 48, 1 / 64, 8),
-    "re550_d32": (512, 257, 384, 2 * math.pi, math.pi, 64, 65, 48, 1 / 32, 8),
+    "re550_d64": (512, 257, 384, 2 * math.pi, math.pi, 64, 65, 48, 1 / 64, 10),
+    "re550_d32": (512, 257, 384, 2 * math.pi, math.pi, 64, 65, 48, 1 / 32, 10),
 }
 PREC = {"fp32": 1, "fp64": 0, "bf16x3": 3, "tf32x2": 2}
 L2_BYTES = 129e6
