@@ -316,6 +316,40 @@ __global__ void adam_step(float *w, float *Wq, const float *__restrict__ g, floa
     Wq[i] = bf16_round(wi);
 }
 
+// The captured training step's variants: the batch index *bt and the bias
+// corrections of that step come from device memory, so one captured step
+// serves every full batch of an epoch (same arithmetic as gather_batch and
+// adam_step).
+__global__ void gather_batch_at(const float *__restrict__ F, const float *__restrict__ tau, long n,
+                                const long *__restrict__ perm, const long *__restrict__ bt, int B,
+                                const double *fmu, const double *fsd, const double *tmu, const double *tsd, float *H0,
+                                float *T)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const long p = perm[*bt * B + b];
+    for (int k = 0; k < NIN; k++) H0[(long)b * NIN + k] = (float)((F[p * NIN + k] - fmu[k]) / fsd[k]);
+    for (int q = 0; q < NOUT; q++) T[(long)b * NOUT + q] = (float)((tau[(long)q * n + p] - tmu[q]) / tsd[q]);
+}
+
+__global__ void adam_step_at(float *w, float *Wq, const float *__restrict__ g, float *m, float *v, long n, float lr,
+                             float b1, float b2, float eps, const float *__restrict__ c12, const long *__restrict__ bt)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float c1 = c12[2 * *bt], c2 = c12[2 * *bt + 1];
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    Wq[i] = bf16_round(wi);
+}
+
+__global__ void next_batch(long *bt) { *bt += 1; }
+
 __global__ void round_copy(const float *w, float *Wq, long n)
 {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -611,15 +645,41 @@ int ef_closure_train(ef_closure *c, const float *feats, const float *tau, long n
     if (!c->fitted && (rc = ef_closure_fit_norm(c, feats, tau, n, stream))) return rc;
     const int B = c->cfg.batch;
     const long nbatch = (n + B - 1) / B;
+    const long nfull = n / B;            // full batches: one captured step replayed; a partial last one launched
+    const float b1 = 0.9f, b2 = 0.999f;
     std::vector<long> perm(n);
-    long *d_perm = nullptr;
+    std::vector<float> c12(2 * (size_t)nbatch);
+    long *d_perm = nullptr, *d_bt = nullptr;
+    float *d_c12 = nullptr;
     double *d_loss = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
     cudaError_t e = dev_malloc(&d_perm, sizeof(long) * (size_t)n);
     if (e == cudaSuccess) e = dev_malloc(&d_loss, sizeof(double));
+    if (e == cudaSuccess) e = dev_malloc(&d_bt, sizeof(long));
+    if (e == cudaSuccess) e = dev_malloc(&d_c12, sizeof(float) * c12.size());
     if (e == cudaSuccess) e = cudaMemsetAsync(d_loss, 0, sizeof(double), s);
-    if (e != cudaSuccess) {
-        cudaFree(d_perm);
-        return cuda_fail(e, "ef_closure_train buffers");
+    // one training step of a full batch, captured on a private stream: the
+    // batch index and the step's bias corrections are read on the device
+    if (e == cudaSuccess && nfull > 0 && epochs > 0) {
+        e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            gather_batch_at<<<grid1(B), 256, 0, cs>>>(feats, tau, n, d_perm, d_bt, B, c->stats, c->stats + 10,
+                                                        c->stats + 20, c->stats + 26, c->H[0], c->T);
+            forward(c, B, cs);
+            mse_grad<<<grid1(B), 256, 0, cs>>>(c->H[NLAYER], c->T, c->dA, c->rowloss, B);
+            backward(c, B, cs);
+            adam_step_at<<<grid1(c->nparam), 256, 0, cs>>>(c->w, c->wq, c->g, c->m, c->v, c->nparam, c->cfg.lr, b1,
+                                                             b2, 1e-8f, d_c12, d_bt);
+            sum_into<<<1, 256, 0, cs>>>(c->rowloss, B, d_loss);
+            next_batch<<<1, 1, 0, cs>>>(d_bt);
+            const cudaError_t el = cudaGetLastError();
+            e = cudaStreamEndCapture(cs, &graph);
+            if (e == cudaSuccess) e = el;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
     }
     for (int ep = 0; ep < epochs && e == cudaSuccess; ep++) {
         // deterministic order: sort points by a hash of (seed, epoch index,
@@ -631,30 +691,43 @@ int ef_closure_train(ef_closure *c, const float *feats, const float *tau, long n
             const long j = (long)(mix(key + (unsigned long long)i) % (unsigned long long)(i + 1));
             const long t = perm[i]; perm[i] = perm[j]; perm[j] = t;
         }
-        // the host buffer is refilled next epoch: the copy must have landed
+        for (long bt = 0; bt < nbatch; bt++) {   // Adam's bias corrections of the epoch's steps
+            const long st = c->step + 1 + bt;
+            c12[2 * bt] = 1.f - powf(b1, (float)st);
+            c12[2 * bt + 1] = 1.f - powf(b2, (float)st);
+        }
+        // the host buffers are refilled next epoch: the copies must have landed
         e = cudaMemcpyAsync(d_perm, perm.data(), sizeof(long) * (size_t)n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_c12, c12.data(), sizeof(float) * c12.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_bt, 0, sizeof(long), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_loss, 0, sizeof(double), s);   // the last epoch's loss is kept
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        for (long bt = 0; bt < nbatch && e == cudaSuccess; bt++) {
-            const int nb = (int)(bt + 1 < nbatch ? B : n - bt * B);
+        for (long bt = 0; bt < nfull && e == cudaSuccess; bt++) e = cudaGraphLaunch(exec, s);
+        for (long bt = nfull; bt < nbatch && e == cudaSuccess; bt++) {   // the partial last batch
+            const int nb = (int)(n - bt * B);
             gather_batch<<<grid1(nb), 256, 0, s>>>(feats, tau, n, d_perm + bt * B, nb, c->stats, c->stats + 10,
                                                    c->stats + 20, c->stats + 26, c->H[0], c->T);
             forward(c, nb, s);
             mse_grad<<<grid1(nb), 256, 0, s>>>(c->H[NLAYER], c->T, c->dA, c->rowloss, nb);
             backward(c, nb, s);
-            c->step++;
-            const float b1 = 0.9f, b2 = 0.999f;
-            const float c1 = 1.f - powf(b1, (float)c->step), c2 = 1.f - powf(b2, (float)c->step);
             adam_step<<<grid1(c->nparam), 256, 0, s>>>(c->w, c->wq, c->g, c->m, c->v, c->nparam, c->cfg.lr, b1, b2,
-                                                      1e-8f, c1, c2);
-            if (ep == epochs - 1) sum_into<<<1, 256, 0, s>>>(c->rowloss, nb, d_loss);
+                                                      1e-8f, c12[2 * bt], c12[2 * bt + 1]);
+            sum_into<<<1, 256, 0, s>>>(c->rowloss, nb, d_loss);
             e = cudaGetLastError();
         }
+        c->step += nbatch;
     }
     double loss_sum = 0.0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&loss_sum, d_loss, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
     cudaFree(d_perm);
     cudaFree(d_loss);
+    cudaFree(d_bt);
+    cudaFree(d_c12);
     if (e != cudaSuccess) return cuda_fail(e, "ef_closure_train");
     if (loss_out) *loss_out = epochs > 0 ? (float)(loss_sum / ((double)n * NOUT)) : 0.f;
     return EF_OK;
