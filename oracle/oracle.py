@@ -30,7 +30,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
-_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+# ORACLE_LIB names a library built elsewhere from a copy of oracle.c (the
+# planted-mistake tests run the pins against such copies); it is used as is.
+_LIB = os.environ.get("ORACLE_LIB") or os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -43,6 +45,8 @@ PAIRS = ((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))
 
 def build(force: bool = False) -> str:
     """Compile oracle.c with gcc into oracle/_build/liboracle.so."""
+    if os.environ.get("ORACLE_LIB"):
+        return _LIB
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
