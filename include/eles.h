@@ -468,8 +468,15 @@ int ef_closure_features_static(const ef_grid *les, const float *ubar, double re_
 int ef_closure_fit_norm(ef_closure *closure, const float *feats, const float *tau, long n, void *stream);
 
 /* Train for `epochs` passes over n points (fits the statistics first if not
- * yet done).  Synchronises the stream; *loss_out = mean loss of the last
- * epoch (standardised units). */
+ * yet done): mini-batches of cfg.batch points in a seeded order per epoch,
+ * MSE on the standardised outputs, Adam (Sec. 5's learned closure; the
+ * paper leaves the model open).  The call allocates its scratch (the epoch's
+ * permutation, Adam's per-step factors) and captures one full-batch step as
+ * a CUDA graph on a private stream, replayed for every full batch; all of it
+ * is released before it returns.  Results do not depend on the capture
+ * (bit-identical to launching each step).  Synchronises the stream;
+ * *loss_out = mean loss of the last epoch (standardised units).  Errors:
+ * EF_ERR_ARG, EF_ERR_OOM, EF_ERR_CUDA. */
 int ef_closure_train(ef_closure *closure, const float *feats, const float *tau, long n, int epochs,
                      void *stream, float *loss_out);
 
