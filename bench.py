@@ -570,7 +570,10 @@ def run_batch64(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     import __graft_entry__ as entry
-    entry.build()
+    if rank == 0:
+        entry.build()      # one rank builds; the others wait for the library
+    if world > 1:
+        dist.barrier()
     from paper_1902_02508_gb300 import eles
     from paper_1902_02508_gb300 import inputs as I
     prec = PREC[args.precision]
@@ -712,7 +715,10 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     import __graft_entry__ as entry
-    entry.build()
+    if rank == 0:
+        entry.build()      # one rank builds; the others wait for the library
+    if world > 1:
+        dist.barrier()
     from paper_1902_02508_gb300 import eles
 
     dns, les, delta, snaps = make_workload(args.workload, rank, args.snapshots)

@@ -58,13 +58,14 @@ def build(force: bool = False, verbose: bool = False, check: bool = False) -> st
 
     def compile_one(so):
         s, o = so
-        cmd = [nvcc(), *_flags(["-DELES_CHECK"] if check else []), "-c", s, "-o", o + ".tmp"]
+        tmp = o + f".{os.getpid()}.tmp"   # per process: concurrent builds never share a file
+        cmd = [nvcc(), *_flags(["-DELES_CHECK"] if check else []), "-c", s, "-o", tmp]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             raise RuntimeError(f"nvcc failed on {os.path.basename(s)}:\n{r.stderr}")
-        os.replace(o + ".tmp", o)
+        os.replace(tmp, o)
 
     if todo:
         with cf.ThreadPoolExecutor(max_workers=min(len(todo), os.cpu_count() or 4)) as ex:
