@@ -236,8 +236,10 @@ __device__ __forceinline__ void x_mma(float (&acc)[NF][4], const float2 (&v)[3][
 }
 
 // BF16X3 x contraction with the MMAs of two fields interleaved, so that the
-// dependent MMAs of one accumulator are issued apart: (u'1, u'1u'1),
-// (u'1u'2, u'1u'3), (u'2, u'2u'2), (u'3, u'2u'3), u'3u'3.
+// dependent MMAs of one accumulator are issued apart.  The x warps take the
+// pairs (u'1, u'1u'1), (u'2, u'1u'2), (u'3, u'2u'2), (u'2u'3, u'3u'3), then
+// u'1u'3 with u'1 reloaded, so that at most two velocity components are live
+// (the x-warp loop issues them).
 template <int F>
 __device__ __forceinline__ void vel_split(const float2 (&v)[3][2][2], unsigned (&ah)[4], unsigned (&al)[4])
 {
@@ -277,20 +279,10 @@ __device__ __forceinline__ void pp_pair(float (&acc)[NF][4], const float2 (&v)[3
     mma_f16(acc[F1], a[0], a[1], a[2], a[3], bp.x, bp.y);
     mma_f16(acc[F2], b[0], b[1], b[2], b[3], bp.x, bp.y);
 }
-__device__ __forceinline__ void x_mma_il(float (&acc)[NF][4], const float2 (&v)[3][2][2], const uint4 (&B)[2])
-{
-    vp_pair<0, 3>(acc, v, B[0], B[1]);
-    pp_pair<4, 5>(acc, v, B[1]);
-    vp_pair<1, 6>(acc, v, B[0], B[1]);
-    vp_pair<2, 7>(acc, v, B[0], B[1]);
-    unsigned a[4];
-    prod_pack<8>(v, a);
-    mma_f16(acc[8], a[0], a[1], a[2], a[3], B[1].z, B[1].w);
-    mma_f16(acc[8], a[0], a[1], a[2], a[3], B[1].x, B[1].y);
-}
 
 // TF32X2 x contraction with the first k-half of each velocity field
-// interleaved with the MMAs of a product field (same pairs as x_mma_il).
+// interleaved with the MMAs of a product field: (u'1, u'1u'1), (u'1u'2, u'1u'3),
+// (u'2, u'2u'2), (u'3, u'2u'3), u'3u'3 (all three components loaded).
 template <int FV>
 __device__ __forceinline__ void tf32_half(const float2 (&v)[3][2][2], int k2, unsigned (&h)[4], unsigned (&l)[4])
 {
@@ -602,19 +594,43 @@ __global__ void __launch_bounds__(Geo<NZ>::THREADS, 1) xz_ws(const __grid_consta
                 const float *buf = xrow + st * STGF;
 #pragma unroll
                 for (int m = 0; m < 2; m++) {
-                    float2 v[3][2][2];
+                    if constexpr (MODE == MODE_BF16X3) {
+                        // two components live at a time: (u1, u2), then (u2, u3), then (u1 reloaded, u3)
+                        float2 v[3][2][2];
+                        auto ld = [&](int c) {
+                            const float2 nU = make_float2(-U[c], -U[c]);
 #pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        const float2 nU = make_float2(-U[c], -U[c]);
+                            for (int h = 0; h < 2; h++) {
+                                const float4 x = *reinterpret_cast<const float4 *>(buf + (c * NZ + 16 * m + 8 * h) * CW);
+                                v[c][h][0] = __fadd2_rn(make_float2(x.x, x.y), nU);
+                                v[c][h][1] = __fadd2_rn(make_float2(x.z, x.w), nU);
+                            }
+                        };
+                        ld(0); ld(1);
+                        vp_pair<0, 3>(acc[m], v, B[0], B[1]);
+                        vp_pair<1, 4>(acc[m], v, B[0], B[1]);
+                        ld(2);
+                        vp_pair<2, 6>(acc[m], v, B[0], B[1]);
+                        pp_pair<7, 8>(acc[m], v, B[1]);
+                        ld(0);
+                        unsigned a5[4];
+                        prod_pack<5>(v, a5);
+                        mma_f16(acc[m][5], a5[0], a5[1], a5[2], a5[3], B[1].z, B[1].w);
+                        mma_f16(acc[m][5], a5[0], a5[1], a5[2], a5[3], B[1].x, B[1].y);
+                    } else {
+                        float2 v[3][2][2];
 #pragma unroll
-                        for (int h = 0; h < 2; h++) {
-                            const float4 x = *reinterpret_cast<const float4 *>(buf + (c * NZ + 16 * m + 8 * h) * CW);
-                            v[c][h][0] = __fadd2_rn(make_float2(x.x, x.y), nU);
-                            v[c][h][1] = __fadd2_rn(make_float2(x.z, x.w), nU);
+                        for (int c = 0; c < 3; c++) {
+                            const float2 nU = make_float2(-U[c], -U[c]);
+#pragma unroll
+                            for (int h = 0; h < 2; h++) {
+                                const float4 x = *reinterpret_cast<const float4 *>(buf + (c * NZ + 16 * m + 8 * h) * CW);
+                                v[c][h][0] = __fadd2_rn(make_float2(x.x, x.y), nU);
+                                v[c][h][1] = __fadd2_rn(make_float2(x.z, x.w), nU);
+                            }
                         }
+                        x_mma_il_tf32(acc[m], v, B);
                     }
-                    if constexpr (MODE == MODE_BF16X3) x_mma_il(acc[m], v, B);
-                    else x_mma_il_tf32(acc[m], v, B);
                 }
                 mbar_arrive(&empty[st]);
                 // the chunk completes phase outputs X0 + OP i, i < OPC (tile columns OPC q + i)
