@@ -151,7 +151,14 @@ __global__ void __launch_bounds__(YTW * 32, 5) ytc_kernel(const __grid_constant_
     }
     const int nplane = a.nplane;
     const size_t nl = (size_t)a.nly * nplane;
-    mbar_wait(&bar, 0, a.err);
+    const bool landed = mbar_wait(&bar, 0, a.err);
+    if (__syncthreads_or(!landed)) {
+        // the wait ran out (EF_ERR_TIMEOUT is recorded) and the copy may still
+        // be landing: skip the column and wait once more, with the same bound,
+        // so that no bulk copy outlives the CTA
+        mbar_wait(&bar, 0, nullptr);
+        return;
+    }
     // split the column once: (rows 2r, 2r + 1) -> (hi word, lo word)
     unsigned *hw = reinterpret_cast<unsigned *>(hs);
     for (int i = threadIdx.x; i < (rows / 2) * YTP; i += YTW * 32) {
