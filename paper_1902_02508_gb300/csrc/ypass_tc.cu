@@ -22,9 +22,10 @@
 //
 // One CTA per (32-point tile, snapshot, field) stages the field's h column
 // over the band rows with TMA (rows padded to 36 floats, which makes the B
-// fragment loads conflict-free).  Launches: fragments; the velocities (q_a,
-// d_a and C'_ab to the scratch, ~bar(u_a) out); the products (q_ab to the
-// scratch); the recovery of T_ab (elementwise).
+// fragment loads conflict-free).  Launches: fragments; all nine fields in
+// one launch (the velocities: q_a, d_a and C'_ab to the scratch, ~bar(u_a)
+// out; the products: q_ab to the scratch); the recovery of T_ab
+// (elementwise).
 #include <cuda_bf16.h>
 
 #include "eles_internal.h"
@@ -115,61 +116,19 @@ __global__ void yfrag_kernel(const YTcGeom g, const double *__restrict__ we, con
     o[32 + lane] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
 }
 
-// One field per CTA (blockIdx.z): NOPS 5, a velocity (q_f with A_y^{p_f},
-// d_f, and C'_cf for c = 1..3); NOPS 1, a product (q only).  After the TMA
-// load the CTA splits its h column once, in place: the fp32 pair of rows
-// (2r, 2r + 1) at a point becomes the two B fragment words (hi in row 2r's
-// slot, lo in row 2r + 1's).  Warp units are (LES row tile, operator, NG
-// column tiles of 8 points); a unit streams its k-steps with the next
-// k-step's operator fragment loaded ahead.
+// Warp units of one field's column (the h words split in place in hw):
+// (LES row tile, operator, NG column tiles of 8 points); a unit streams its
+// k-steps with the next k-step's operator fragment loaded ahead.  NOPS 5, a
+// velocity (q_F with A_y^{p_F}, d_F, and C'_cF for c = 1..3); NOPS 1, a
+// product (q only).  Returns whether a non-finite ~bar(u) was written.
 template <int NOPS, int NG>
-__global__ void __launch_bounds__(YTW * 32, 5) ytc_kernel(const __grid_constant__ YTcArgs a)
+__device__ __forceinline__ bool ytc_units(const YTcArgs &a, const unsigned *hw, int tile, int s, int F, int warp,
+                                          int lane)
 {
-    extern __shared__ float4 ysm4[];
-    float *hs;                                     // [2 box_rows][YTS], 128-B aligned for TMA
-    {
-        char *b = reinterpret_cast<char *>(ysm4);
-        const unsigned sa = smem_u32(b);
-        hs = reinterpret_cast<float *>(b + (((sa + 127u) & ~127u) - sa));
-    }
-    __shared__ alignas(8) unsigned long long bar;
     const YTcGeom &geo = a.geo;
-    const int tile = blockIdx.x, s = blockIdx.y, F = NOPS == 5 ? blockIdx.z : 3 + blockIdx.z;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    const int rows = 2 * geo.box_rows;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_expect_tx(&bar, 2u * geo.box_rows * YTS * 4u);
-        const int row0 = (s * 9 + F) * a.ny;
-        for (int hf = 0; hf < 2; hf++)
-            tma_load2(hs + (size_t)hf * geo.box_rows * YTS, &a.hmap, &bar, tile * YTP, row0 + hf * geo.box_rows);
-    }
     const int nplane = a.nplane;
     const size_t nl = (size_t)a.nly * nplane;
-    const bool landed = mbar_wait(&bar, 0, a.err);
-    if (__syncthreads_or(!landed)) {
-        // the wait ran out (EF_ERR_TIMEOUT is recorded) and the copy may still
-        // be landing: skip the column and wait once more, with the same bound,
-        // so that no bulk copy outlives the CTA
-        mbar_wait(&bar, 0, nullptr);
-        return;
-    }
-    // split the column once: (rows 2r, 2r + 1) -> (hi word, lo word)
-    unsigned *hw = reinterpret_cast<unsigned *>(hs);
-    for (int i = threadIdx.x; i < (rows / 2) * YTP; i += YTW * 32) {
-        const int r2 = i / YTP, pc = i - r2 * YTP;
-        unsigned hi, lo;
-        split_b(hs[(2 * r2) * YTS + pc], hs[(2 * r2 + 1) * YTS + pc], hi, lo);
-        hw[(2 * r2) * YTS + pc] = hi;
-        hw[(2 * r2 + 1) * YTS + pc] = lo;
-    }
-    __syncthreads();
-
     constexpr int NGRP = 4 / NG;                   // column groups per 32-point tile
     bool bad = false;
     for (int unit = warp; unit < geo.nmt * NOPS * NGRP; unit += YTW) {
@@ -198,14 +157,22 @@ __global__ void __launch_bounds__(YTW * 32, 5) ytc_kernel(const __grid_constant_
                 nal = __ldg(fo + 64 * (kk + 1) + 32);
             }
             const unsigned *x = bw + (size_t)16 * kk * YTS;
+            unsigned b0h[NG], b0l[NG], b1h[NG], b1l[NG];
 #pragma unroll
             for (int n = 0; n < NG; n++) {
-                const unsigned b0h = x[8 * n], b0l = x[YTS + 8 * n];                       // rows 2t, 2t + 1
-                const unsigned b1h = x[8 * YTS + 8 * n], b1l = x[9 * YTS + 8 * n];         // rows 2t + 8, 2t + 9
-                mma16816(acc[n], ah, b0h, b1h);
-                mma16816(acc[n], al, b0h, b1h);
-                mma16816(acc[n], ah, b0l, b1l);
+                b0h[n] = x[8 * n];                                                 // rows 2t, 2t + 1
+                b0l[n] = x[YTS + 8 * n];
+                b1h[n] = x[8 * YTS + 8 * n];                                       // rows 2t + 8, 2t + 9
+                b1l[n] = x[9 * YTS + 8 * n];
             }
+            // the three split products of one accumulator depend on each other:
+            // issue them NG apart (the order within an accumulator is unchanged)
+#pragma unroll
+            for (int n = 0; n < NG; n++) mma16816(acc[n], ah, b0h[n], b1h[n]);
+#pragma unroll
+            for (int n = 0; n < NG; n++) mma16816(acc[n], al, b0h[n], b1h[n]);
+#pragma unroll
+            for (int n = 0; n < NG; n++) mma16816(acc[n], ah, b0l[n], b1l[n]);
             ah = nah;
             al = nal;
         }
@@ -244,6 +211,59 @@ __global__ void __launch_bounds__(YTW * 32, 5) ytc_kernel(const __grid_constant_
                 }
         }
     }
+    return bad;
+}
+
+// One field per CTA (blockIdx.z = F: the velocities 0-2, the products 3-8
+// when the stress is wanted; one launch, the velocity CTAs first so that the
+// lighter product CTAs fill the tail).  After the TMA load the CTA splits its
+// h column once, in place: the fp32 pair of rows (2r, 2r + 1) at a point
+// becomes the two B fragment words (hi in row 2r's slot, lo in row 2r + 1's).
+__global__ void __launch_bounds__(YTW * 32, 5) ytc_kernel(const __grid_constant__ YTcArgs a)
+{
+    extern __shared__ float4 ysm4[];
+    float *hs;                                     // [2 box_rows][YTS], 128-B aligned for TMA
+    {
+        char *b = reinterpret_cast<char *>(ysm4);
+        const unsigned sa = smem_u32(b);
+        hs = reinterpret_cast<float *>(b + (((sa + 127u) & ~127u) - sa));
+    }
+    __shared__ alignas(8) unsigned long long bar;
+    const YTcGeom &geo = a.geo;
+    const int tile = blockIdx.x, s = blockIdx.y, F = blockIdx.z;
+    const int rows = 2 * geo.box_rows;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bar, 2u * geo.box_rows * YTS * 4u);
+        const int row0 = (s * 9 + F) * a.ny;
+        for (int hf = 0; hf < 2; hf++)
+            tma_load2(hs + (size_t)hf * geo.box_rows * YTS, &a.hmap, &bar, tile * YTP, row0 + hf * geo.box_rows);
+    }
+    const bool landed = mbar_wait(&bar, 0, a.err);
+    if (__syncthreads_or(!landed)) {
+        // the wait ran out (EF_ERR_TIMEOUT is recorded) and the copy may still
+        // be landing: skip the column and wait once more, with the same bound,
+        // so that no bulk copy outlives the CTA
+        mbar_wait(&bar, 0, nullptr);
+        return;
+    }
+    // split the column once: (rows 2r, 2r + 1) -> (hi word, lo word)
+    unsigned *hw = reinterpret_cast<unsigned *>(hs);
+    for (int i = threadIdx.x; i < (rows / 2) * YTP; i += YTW * 32) {
+        const int r2 = i / YTP, pc = i - r2 * YTP;
+        unsigned hi, lo;
+        split_b(hs[(2 * r2) * YTS + pc], hs[(2 * r2 + 1) * YTS + pc], hi, lo);
+        hw[(2 * r2) * YTS + pc] = hi;
+        hw[(2 * r2 + 1) * YTS + pc] = lo;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool bad = F < 3 ? ytc_units<5, 4>(a, hw, tile, s, F, warp, lane)
+                           : ytc_units<1, 2>(a, hw, tile, s, F, warp, lane);
     if (bad && a.err) atomicCAS(a.err, 0, (int)EF_ERR_NAN);
 }
 
@@ -340,17 +360,16 @@ __global__ void __launch_bounds__(256) yrecover_t_kernel(const __grid_constant__
     if (bad && a.err) atomicCAS(a.err, 0, (int)EF_ERR_NAN);
 }
 
-template <int NOPS, int NG>
-cudaError_t launch_part(const YTcArgs &a, int nsnap, int nz, cudaStream_t st)
+cudaError_t launch_fields(const YTcArgs &a, int nsnap, int nfields, cudaStream_t st)
 {
     const size_t smem = sizeof(float) * 2 * (size_t)a.geo.box_rows * YTS + 128;
     static size_t attr = 0;
     if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(ytc_kernel<NOPS, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(ytc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = smem;
     }
-    ytc_kernel<NOPS, NG><<<dim3((a.nplane + YTP - 1) / YTP, nsnap, nz), YTW * 32, smem, st>>>(a);
+    ytc_kernel<<<dim3((a.nplane + YTP - 1) / YTP, nsnap, nfields), YTW * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -432,9 +451,8 @@ cudaError_t launch_ytc(const YTcArgs &a, int nsnap, cudaStream_t st)
 {
     YTcArgs c = a;
     c.nsnap = nsnap;
-    cudaError_t e = launch_part<5, 4>(c, nsnap, 3, st);
+    cudaError_t e = launch_fields(c, nsnap, a.stress ? 9 : 3, st);
     if (e != cudaSuccess || !a.stress) return e;
-    if ((e = launch_part<1, 2>(c, nsnap, 6, st)) != cudaSuccess) return e;
     YTcArgs b = a;
     b.nsnap = nsnap;
     if (a.ptrans) {
