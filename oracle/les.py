@@ -14,7 +14,11 @@ counterpart, on the LES nodes where the filter samples ubar and T_ij.
 
 Readings (the paper gives no discretisation of its own beyond the above):
   * nodes: x_i = i Lx/nx, z_k = k Lz/nz (periodic), the given y nodes with
-    both walls; ubar = 0 at the walls (no slip);
+    both walls;
+  * wall values (Eq. 10 and Eq. 11): ubar_2 = 0 on the walls; ubar_1 and
+    ubar_3 take the filter-consistent value F(u_i) on the walls, which in the
+    loop of Fig. 2 is the filtered DNS of the same step (held over the step,
+    like T_ij); without a DNS field the walls are no-slip;
   * derivatives: second-order central differences,
       dx f = (f[i+1] - f[i-1]) / (2 hx)           (periodic; z alike),
       dy f = (f[j+1] - f[j-1]) / (y[j+1] - y[j-1])  (interior nodes);
@@ -28,7 +32,8 @@ Readings (the paper gives no discretisation of its own beyond the above):
     orthogonal projection of the interior velocities, in the inner product
     with weight (y[j+1] - y[j-1]) / 2 per node, onto the fields whose discrete
     divergence d_x u_1 + d_y u_2 + d_z u_3 is zero at every interior node, the
-    wall velocities held at zero;
+    wall velocities held fixed (the divergence at the interior nodes reads
+    only the wall value of u_2, which is zero);
   * time advance: the low-storage third-order Runge-Kutta scheme with
     gamma = (8/15, 5/12, 3/4), zeta = (0, -17/60, -5/12),
       u* = u_(k-1) + dt (gamma_k R(u_(k-1)) + zeta_k R(u_(k-2))),  u_k = P u*,
@@ -184,7 +189,7 @@ def project(u, grid):
             out[0, :, q, m] = v[:ni]
             out[1, :, q, m] = v[ni:2 * ni]
             out[2, :, q, m] = v[2 * ni:]
-    res = np.zeros_like(u)
+    res = np.array(u)
     res[:, 1:-1] = np.real(np.fft.ifft2(out, axes=(2, 3)))
     return res
 
@@ -230,16 +235,27 @@ def project_dense(u, grid):
     A = (D * Wi[None, :]) @ D.T
     lam = np.linalg.lstsq(A, D @ ustar, rcond=1e-13)[0]
     v = ustar - Wi * (D.T @ lam)
-    res = np.zeros_like(u)
+    res = np.array(u)
     res[:, 1:-1] = v.reshape(3, ny - 2, nz, nx)
     return res
 
 
-def step(u, tau, grid, nu: float, dt: float, forcing: float = 1.0, scheme: str = "rk3", projector=project):
-    """One time step of the LES (module docstring).  Returns the new field."""
+def wall_values(u, ubc=None):
+    """u with its wall rows set by Eq. 10 / Eq. 11: u_2 = 0, u_1 and u_3 from
+    ubc (the filtered DNS) or zero."""
     u = np.asarray(u, dtype=np.float64).copy()
-    u[:, 0] = 0.0
-    u[:, -1] = 0.0
+    for row in (0, -1):
+        u[1, row] = 0.0
+        for c in (0, 2):
+            u[c, row] = 0.0 if ubc is None else np.asarray(ubc[c][row], dtype=np.float64)
+    return u
+
+
+def step(u, tau, grid, nu: float, dt: float, forcing: float = 1.0, scheme: str = "rk3", projector=project,
+         ubc=None):
+    """One time step of the LES (module docstring) with the wall values taken
+    from ubc (None: no slip).  Returns the new field."""
+    u = wall_values(u, ubc)
     if scheme == "rk3":
         coefs = list(zip(RK3_GAMMA, RK3_ZETA))
     elif scheme == "euler":
@@ -259,14 +275,15 @@ def step(u, tau, grid, nu: float, dt: float, forcing: float = 1.0, scheme: str =
 
 def apost_run(dns, les, delta: float, snapshots, u0, nu: float, dt: float, forcing: float = 1.0,
               ext: int = 0, scheme: str = "rk3"):
-    """Fig. 2: for each DNS snapshot in turn, T_ij from the filter (Eq. 6,
-    oracle.subfilter_stress) and one LES step from the current LES field.
-    Returns the LES field after the last step and the list of T_ij."""
+    """Fig. 2: for each DNS snapshot in turn, ubar and T_ij from the filter
+    (Eq. 6, oracle.subfilter_stress) and one LES step from the current LES
+    field, its wall values those of that ubar (Eq. 10).  Returns the LES field
+    after the last step and the list of T_ij."""
     from . import oracle as O
     u = np.asarray(u0, dtype=np.float64)
     taus = []
     for snap in snapshots:
-        _, tau = O.subfilter_stress(dns, les, delta, snap, ext=ext)
+        ubar, tau = O.subfilter_stress(dns, les, delta, snap, ext=ext)
         taus.append(tau)
-        u = step(u, tau, les, nu, dt, forcing, scheme)
+        u = step(u, tau, les, nu, dt, forcing, scheme, ubc=ubar)
     return u, taus

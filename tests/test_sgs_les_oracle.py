@@ -7,7 +7,8 @@ advanced with the exact T_ij of Eq. 6).
     discrete gradients of potentials that vanish on the walls, and leaves
     zero divergence (the Hodge split it must perform);
   * laminar Poiseuille flow under the mean pressure gradient is a steady
-    state of the step (the stencils are exact for quadratics);
+    state of the step (the stencils are exact for quadratics), and so is a
+    Couette profile between wall values given by Eq. 10;
   * a single wall-bounded mode with no advection decays by the third-order
     Runge-Kutta amplification 1 + z + z^2/2 + z^3/6 (z = nu dt lambda, lambda
     the closed-form eigenvalue of the three-point operators), and by 1 + z
@@ -96,6 +97,27 @@ def test_projection_is_the_hodge_split(shape):
     pu = L.project(u, g)
     assert np.max(np.abs(L.divergence(pu, g))) < 1e-11 * np.max(np.abs(u))
     assert rel(L.project(pu, g), pu) < 1e-12
+
+
+@pytest.mark.parametrize("scheme", ["rk3", "euler"])
+def test_couette_with_wall_values_is_steady(scheme):
+    """Eq. 10: the wall rows of u_1 and u_3 come from the given field; a
+    linear profile between them is steady (no forcing)."""
+    g = grid(8, 13, 6)
+    y = np.asarray(g.y)
+    u = np.zeros((3, g.ny, g.nz, g.nx))
+    u[0] = (0.4 + 1.5 * y)[:, None, None]
+    u[2] = (-0.2 + 0.7 * y)[:, None, None]
+    u[1, 1:-1] = 0.0
+    start = np.array(u)
+    start[:, 0] = start[:, -1] = 0.0           # the step sets the walls itself
+    out = L.step(start, None, g, nu=0.02, dt=0.1, forcing=0.0, scheme=scheme, ubc=u)
+    assert rel(out, u) < 1e-13
+    # and u_2 on the walls is zero whatever the given field holds
+    bc = np.array(u)
+    bc[1] = 5.0
+    out = L.step(start, None, g, nu=0.02, dt=0.1, forcing=0.0, scheme=scheme, ubc=bc)
+    assert rel(out, u) < 1e-13
 
 
 @pytest.mark.parametrize("scheme", ["rk3", "euler"])

@@ -19,6 +19,8 @@ MUTANTS = {
     "forcing on the wrong component": ("        if i == 0:\n            acc += forcing",
                                        "        if i == 1:\n            acc += forcing"),
     "advective flux u_i u_i instead of u_i u_j": ("flux = u[i] * u[j]", "flux = u[i] * u[i]"),
+    "wall value of u_2 taken from the filtered field": ("        u[1, row] = 0.0\n        for c in (0, 2):",
+                                                         "        for c in (0, 1, 2):"),
     "difference symbol at half the wavenumber": ("s = np.sin(2.0 * np.pi * m / n) / h", "s = np.sin(np.pi * m / n) / h"),
 }
 
@@ -28,6 +30,7 @@ def _pin_calls():
         lambda: pins.test_projection_forms_agree(),
         lambda: pins.test_projection_is_the_hodge_split((16, 13, 12)),
         lambda: pins.test_poiseuille_is_steady("rk3"),
+        lambda: pins.test_couette_with_wall_values_is_steady("rk3"),
         lambda: pins.test_single_mode_decays_by_the_scheme_amplification(
             "rk3", lambda z: 1 + z + z * z / 2 + z ** 3 / 6),
         lambda: pins.test_rhs_closed_form_uniform_grid(),
