@@ -541,6 +541,74 @@ int ef_closure_set_params(ef_closure *closure, const float *params, const double
 int ef_closure_save(const ef_closure *closure, const char *path);
 int ef_closure_load(ef_closure *closure, const char *path);
 
+/* ------------------------------------------------------------------------
+ * The loop of Sec. 3 and Fig. 2: at every time step the DNS field is
+ * filtered, T_ij (Eq. 6) is formed from it, and the explicitly filtered LES
+ * equations (Eq. 5, with bar(u_i u_j) = ubar_i ubar_j + T_ij) are advanced
+ * one step with that T_ij.  The LES here is a minimal collocated solver on
+ * the LES nodes of the filter, FP64 throughout:
+ *   - second-order central differences (periodic in x and z, non-uniform in
+ *     y), the three-point Laplacian;
+ *   - R_i = -d_j (ubar_i ubar_j + T_ij) + nu lap ubar_i + forcing [i = 1] at
+ *     the interior nodes, `forcing` the imposed mean pressure gradient (Sec. 3
+ *     drives the channel with a constant one; 1 in units u_tau^2 / delta);
+ *   - wall rows by Eq. 10 and Eq. 11: ubar_2 = 0, ubar_1 and ubar_3 the
+ *     filter-consistent wall value F(u_i), taken from a filtered DNS field
+ *     of the step (no slip when none is given);
+ *   - third-order low-storage Runge-Kutta (the scheme family of Sec. 3) or
+ *     forward Euler, each substep followed by the projection below, with
+ *     T_ij and the wall values held over the step;
+ *   - projection (the pressure step of the fractional-step method): the
+ *     orthogonal projection, in the inner product weighted by
+ *     (y[j+1] - y[j-1]) / 2, onto velocities of zero discrete divergence at
+ *     every interior node, the wall values held; computed by discrete
+ *     Fourier transforms in x and z and two tridiagonal solves in y per mode.
+ * Fields are device [3][ny][nz][nx] FP64 with x fastest; tau is the
+ * [6][ny][nz][nx] output of ef_subfilter_stress in the precision of its
+ * plan (double for EF_PREC_FP64, float otherwise), as is the wall-value
+ * field ubar_bc.  The solver owns its scratch (about 12 doubles per node);
+ * calls on one solver must not overlap on the GPU.  Calls are asynchronous
+ * on `stream` and allocate nothing.
+ */
+enum { EF_LES_RK3 = 0, EF_LES_EULER = 1 };
+typedef struct {
+    double nu;          /* kinematic viscosity (1 / Re_tau in wall units), >= 0 */
+    double forcing;     /* mean pressure gradient driving u_1 */
+    int scheme;         /* EF_LES_RK3 or EF_LES_EULER */
+} ef_les_cfg;
+typedef struct ef_les ef_les;
+
+/* Set-up on the current device for the LES grid `les` (3 to 4096 nodes per
+ * direction).  Errors: EF_ERR_ARG, EF_ERR_SHAPE, EF_ERR_OOM, EF_ERR_CUDA. */
+int ef_les_create(const ef_grid *les, const ef_les_cfg *cfg, ef_les **out);
+void ef_les_destroy(ef_les *les);
+
+/* One time step of length dt, in place on ubar (device [3][ny][nz][nx]
+ * double).  tau (may be NULL: no subfilter term) and ubar_bc (may be NULL:
+ * no slip) in `precision` as above.  Its wall rows are set first. */
+int ef_les_step(ef_les *les, double *ubar, const void *tau, const void *ubar_bc, int precision, double dt,
+                void *stream);
+
+/* The projection alone: u = P ustar (u may equal ustar; wall rows copied). */
+int ef_les_project(ef_les *les, const double *ustar, double *u, void *stream);
+
+/* The discrete divergence of u at every node (zero on the wall rows). */
+int ef_les_divergence(ef_les *les, const double *u, double *div, void *stream);
+
+/* The right-hand side R (device [3][ny][nz][nx], zero on the wall rows) of
+ * u as given (its wall rows are used as they are). */
+int ef_les_rhs(ef_les *les, const double *u, const void *tau, int precision, double *rhs, void *stream);
+
+/*
+ * ef_apost_step -- one step of the loop of Fig. 2: ef_subfilter_stress of
+ * the DNS snapshot u_dns into ubar_dns and tau (device, the plan's LES grid
+ * and precision; the caller's scratch), then ef_les_step of ubar_les with
+ * that tau and the wall values of ubar_dns.  The plan's LES grid must be the
+ * solver's (EF_ERR_SHAPE otherwise).  Other errors as the two calls.
+ */
+int ef_apost_step(ef_plan *plan, ef_les *les, const void *u_dns, void *ubar_dns, void *tau, double *ubar_les,
+                  double dt, void *stream);
+
 /*
  * ef_debug_fail_alloc -- test hook: the n-th device allocation the library
  * makes from now on (n = 0: the next one) fails as if the device were out of

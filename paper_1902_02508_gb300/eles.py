@@ -21,6 +21,7 @@ LIB_PATH = (os.path.join(_HERE, "_lib_check", "libeles_check.so") if os.environ.
             else os.path.join(_HERE, "_lib", "libeles.so"))
 
 EF_OK = 0
+EF_ERR_ARG, EF_ERR_SHAPE = 1, 2
 STATUS = {0: "EF_OK", 1: "EF_ERR_ARG", 2: "EF_ERR_SHAPE", 3: "EF_ERR_CUDA", 4: "EF_ERR_NAN",
           5: "EF_ERR_TIMEOUT", 6: "EF_ERR_OOM", 7: "EF_ERR_UNSUPPORTED", 8: "EF_ERR_RANGE"}
 KERNEL_GAUSSIAN = 0
@@ -42,7 +43,8 @@ EXPORTED = ("ef_filter_setup", "ef_plan_destroy", "ef_filter_fields", "ef_subfil
             "ef_batch_captures", "ef_plan_autotune", "ef_plan_set_variant", "ef_closure_features_static", "ef_io_create",
             "ef_closure_check_device_error", "ef_differential_unfilter", "ef_selftest_wait",
             "ef_io_destroy", "ef_subfilter_stress_host", "ef_stats_create", "ef_stats_destroy", "ef_plane_stats",
-            "ef_error_field", "ef_error_profile")
+            "ef_error_field", "ef_error_profile", "ef_les_create", "ef_les_destroy", "ef_les_step",
+            "ef_les_project", "ef_les_divergence", "ef_les_rhs", "ef_apost_step")
 
 
 class EFError(RuntimeError):
@@ -60,6 +62,10 @@ class _Grid(ctypes.Structure):
 class _ClosureCfg(ctypes.Structure):
     _fields_ = [("hidden", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
                 ("guard_sigma", ctypes.c_float), ("seed", ctypes.c_ulonglong)]
+
+
+class _LesCfg(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double), ("forcing", ctypes.c_double), ("scheme", ctypes.c_int)]
 
 
 _lib = None
@@ -165,6 +171,20 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             lib.ef_error_field.restype = i
             lib.ef_error_profile.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, vp, vp]
             lib.ef_error_profile.restype = i
+            lib.ef_les_create.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_LesCfg), ctypes.POINTER(vp)]
+            lib.ef_les_create.restype = i
+            lib.ef_les_destroy.argtypes = [vp]
+            lib.ef_les_destroy.restype = None
+            lib.ef_les_step.argtypes = [vp, vp, vp, vp, i, d, vp]
+            lib.ef_les_step.restype = i
+            lib.ef_les_project.argtypes = [vp, vp, vp, vp]
+            lib.ef_les_project.restype = i
+            lib.ef_les_divergence.argtypes = [vp, vp, vp, vp]
+            lib.ef_les_divergence.restype = i
+            lib.ef_les_rhs.argtypes = [vp, vp, vp, i, vp, vp]
+            lib.ef_les_rhs.restype = i
+            lib.ef_apost_step.argtypes = [vp, vp, vp, vp, vp, vp, d, vp]
+            lib.ef_apost_step.restype = i
             lib.ef_last_error.restype = ctypes.c_char_p
             lib.ef_version.restype = ctypes.c_char_p
             _lib = lib
@@ -652,3 +672,93 @@ def error_profile(st: Stats, pa, pb, err, utau_a: float = 1.0, utau_b: float = 1
     b = _field(pb, (g.ny,), torch.float64, "pb")
     pe = _field(err, (1,), torch.float64, "err")
     _check(load().ef_error_profile(st.handle, a, b, float(utau_a), float(utau_b), pe, _stream(stream)))
+
+
+LES_RK3 = 0
+LES_EULER = 1
+
+
+class Les:
+    """Owns an ef_les*: the minimal LES solver of the loop of Fig. 2."""
+
+    def __init__(self, handle, grid, cfg):
+        self.handle, self.grid, self.cfg = handle, grid, cfg
+
+    def close(self):
+        if self.handle:
+            load().ef_les_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def les_create(grid, nu: float, forcing: float = 1.0, scheme: int = LES_RK3) -> Les:
+    g, y = _grid(grid)
+    cfg = _LesCfg(float(nu), float(forcing), int(scheme))
+    h = ctypes.c_void_p()
+    _check(load().ef_les_create(ctypes.byref(g), ctypes.byref(cfg), ctypes.byref(h)))
+    return Les(h, grid, cfg)
+
+
+def _les_shape(les: Les, ncomp: int):
+    g = les.grid
+    return (ncomp, g.ny, g.nz, g.nx)
+
+
+def _prec_of(*tensors):
+    import torch
+    dts = {t.dtype for t in tensors if t is not None}
+    if len(dts) > 1:
+        raise ValueError("tau and ubar_bc must share one dtype")
+    dt = dts.pop() if dts else torch.float64
+    return (PREC_FP64 if dt == torch.float64 else PREC_FP32), dt
+
+
+def les_step(les: Les, ubar, dt: float, tau=None, ubar_bc=None, stream=None) -> None:
+    """One step in place on ubar (device float64 [3][ny][nz][nx]); tau
+    [6][..] and ubar_bc [3][..] float64 or float32 (or None)."""
+    import torch
+    prec, tdt = _prec_of(tau, ubar_bc)
+    pu = _field(ubar, _les_shape(les, 3), torch.float64, "ubar")
+    pt = _field(tau, _les_shape(les, 6), tdt, "tau")
+    pb = _field(ubar_bc, _les_shape(les, 3), tdt, "ubar_bc")
+    _check(load().ef_les_step(les.handle, pu, pt, pb, prec, float(dt), _stream(stream)))
+
+
+def les_project(les: Les, ustar, u, stream=None) -> None:
+    import torch
+    a = _field(ustar, _les_shape(les, 3), torch.float64, "ustar")
+    b = _field(u, _les_shape(les, 3), torch.float64, "u")
+    _check(load().ef_les_project(les.handle, a, b, _stream(stream)))
+
+
+def les_divergence(les: Les, u, div, stream=None) -> None:
+    import torch
+    a = _field(u, _les_shape(les, 3), torch.float64, "u")
+    b = _field(div, _les_shape(les, 1)[1:], torch.float64, "div")
+    _check(load().ef_les_divergence(les.handle, a, b, _stream(stream)))
+
+
+def les_rhs(les: Les, u, rhs, tau=None, stream=None) -> None:
+    import torch
+    prec, tdt = _prec_of(tau)
+    a = _field(u, _les_shape(les, 3), torch.float64, "u")
+    pt = _field(tau, _les_shape(les, 6), tdt, "tau")
+    b = _field(rhs, _les_shape(les, 3), torch.float64, "rhs")
+    _check(load().ef_les_rhs(les.handle, a, pt, prec, b, _stream(stream)))
+
+
+def apost_step(plan: Plan, les: Les, u_dns, ubar_dns, tau, ubar_les, dt: float, stream=None) -> None:
+    """Fig. 2: the filter of the DNS snapshot u_dns (T_ij into tau, ubar into
+    ubar_dns; the plan's dtype), then one LES step of ubar_les (float64)."""
+    import torch
+    d, l = plan.dns, plan.les
+    pu = _field(u_dns, (3, d.ny, d.nz, d.nx), plan.dtype, "u_dns")
+    pb = _field(ubar_dns, (3, l.ny, l.nz, l.nx), plan.dtype, "ubar_dns")
+    pt = _field(tau, (6, l.ny, l.nz, l.nx), plan.dtype, "tau")
+    pl = _field(ubar_les, _les_shape(les, 3), torch.float64, "ubar_les")
+    _check(load().ef_apost_step(plan.handle, les.handle, pu, pb, pt, pl, float(dt), _stream(stream)))

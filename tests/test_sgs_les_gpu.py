@@ -1,0 +1,208 @@
+"""GPU parity of the LES step driven by the exact subfilter stress (the loop
+of Sec. 3 and Fig. 2; include/eles.h ef_les_*, ef_apost_step) against the
+FP64 oracle of oracle/les.py, through the C ABI.
+
+  * the projection, the divergence and the right-hand side (T_ij in FP64 and
+    in FP32) on random fields, odd and even node counts;
+  * whole RK3 and Euler steps with T_ij and Eq. 10 wall values;
+  * the loop itself: ef_apost_step (filter of the DNS snapshot, then the LES
+    step) against oracle.les.apost_run for an FP64 plan, and for split
+    precision plans (T_ij within 1e-4 u_tau^2 of the oracle's);
+  * at the 64 x 65 x 48 LES grid of the 512 x 257 x 384 channel: Poiseuille
+    flow stays steady and a projected random field has zero divergence.
+
+Tolerances: the GPU and the oracle evaluate the same FP64 stencils and the
+same projection (the GPU by Fourier transforms and tridiagonal chains, the
+oracle by per-mode least squares), so they agree to 1e-12 relative; a loop
+fed by a split-precision plan is compared within 1e-3 u_tau, seven times
+what the oracle's loop moves when its inputs are perturbed by the 1e-4
+accuracy of a split-precision plan.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import __graft_entry__ as entry
+from oracle import les as L
+from oracle import oracle as O
+from paper_1902_02508_gb300 import eles
+from paper_1902_02508_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+NU = 1.0 / 180.0
+SHAPES = [(32, 33, 24), (12, 10, 9), (16, 17, 12)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    entry.build()
+
+
+def dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(torch.device("cuda"), dtype)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def les_grid(nx, ny, nz):
+    return I.dns_grid(nx, ny, nz, 2 * math.pi, math.pi)
+
+
+def random_fields(g, seed):
+    rng = np.random.default_rng(seed)
+    u = rng.standard_normal((3, g.ny, g.nz, g.nx))
+    u[1, 0] = u[1, -1] = 0.0
+    tau = rng.standard_normal((6, g.ny, g.nz, g.nx)) * 0.1
+    bc = rng.standard_normal((3, g.ny, g.nz, g.nx))
+    return u, tau, bc
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_projection_and_divergence_match_oracle(shape):
+    g = les_grid(*shape)
+    u, _, _ = random_fields(g, 1)
+    les = eles.les_create(g, NU)
+    ud = dev(u)
+    out = torch.full_like(ud, float("nan"))
+    eles.les_project(les, ud, out)
+    ref = L.project(u, g)
+    got = host(out)
+    assert rel(got, ref) < 1e-12
+    div = torch.full(ud.shape[1:], float("nan"), device=ud.device, dtype=torch.float64)
+    eles.les_divergence(les, ud, div)
+    assert rel(host(div), L.divergence(u, g)) < 1e-13
+    eles.les_divergence(les, out, div)
+    assert np.abs(host(div)).max() < 1e-11 * np.abs(u).max() / min(g.Lx / g.nx, np.diff(g.y).min())
+    # in place
+    eles.les_project(les, ud, ud)
+    assert rel(host(ud), ref) < 1e-12
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("tdtype", [torch.float64, torch.float32])
+def test_rhs_matches_oracle(shape, tdtype):
+    g = les_grid(*shape)
+    u, tau, _ = random_fields(g, 2)
+    tau_d = dev(tau, tdtype)
+    les = eles.les_create(g, NU, forcing=1.3)
+    R = torch.full((3, g.ny, g.nz, g.nx), float("nan"), device="cuda", dtype=torch.float64)
+    eles.les_rhs(les, dev(u), R, tau=tau_d)
+    ref = L.rhs(u, host(tau_d), g, NU, 1.3)
+    assert rel(host(R), ref) < 1e-13
+    eles.les_rhs(les, dev(u), R)
+    assert rel(host(R), L.rhs(u, None, g, NU, 1.3)) < 1e-13
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("scheme,name", [(eles.LES_RK3, "rk3"), (eles.LES_EULER, "euler")])
+def test_steps_match_oracle(shape, scheme, name):
+    g = les_grid(*shape)
+    u, tau, bc = random_fields(g, 3)
+    u0 = L.project(u, g)
+    les = eles.les_create(g, NU, forcing=1.0, scheme=scheme)
+    ud = dev(u0)
+    ref = u0
+    for _ in range(2):
+        eles.les_step(les, ud, 0.01, tau=dev(tau), ubar_bc=dev(bc))
+        ref = L.step(ref, tau, g, NU, 0.01, 1.0, name, ubc=bc)
+    got = host(ud)
+    assert rel(got, ref) < 1e-12
+    # Eq. 10 / 11 wall rows
+    for row in (0, -1):
+        assert np.array_equal(got[0, row], bc[0, row]) and np.array_equal(got[2, row], bc[2, row])
+        assert np.all(got[1, row] == 0.0)
+    # no subfilter term, no slip
+    ud = dev(u0)
+    eles.les_step(les, ud, 0.01)
+    assert rel(host(ud), L.step(u0, None, g, NU, 0.01, 1.0, name)) < 1e-12
+
+
+APOST = {
+    # name: (DNS nx ny nz, Lx, Lz, LES nx ny nz, Delta, precision)
+    "fp64": ((32, 33, 32), 2 * math.pi, math.pi, (8, 9, 8), 2 * math.pi / 16, eles.PREC_FP64),
+    "fp64_s6": ((96, 49, 96), 4 * math.pi, 2 * math.pi, (16, 13, 16), 4 * math.pi / 16, eles.PREC_FP64),
+    "bf16x3": ((128, 65, 128), 2 * math.pi, math.pi, (16, 17, 16), 12 * math.pi / 128, eles.PREC_BF16X3),
+    "tf32x2": ((128, 65, 128), 2 * math.pi, math.pi, (16, 17, 16), 12 * math.pi / 128, eles.PREC_TF32X2),
+}
+
+
+@pytest.mark.parametrize("name", sorted(APOST))
+def test_apost_loop_matches_oracle(name):
+    """Three steps of Fig. 2 from the filtered first snapshot, each with the
+    T_ij and wall values of its own DNS snapshot."""
+    (nx, ny, nz), Lx, Lz, (nlx, nly, nlz), delta, prec = APOST[name]
+    dns = I.dns_grid(nx, ny, nz, Lx, Lz)
+    les = I.les_grid(dns, nlx, nly, nlz)
+    snaps = [I.channel_velocity(dns, 1000 + s) for s in range(4)]
+    dt = 0.002
+    ub0, _ = O.subfilter_stress(dns, les, delta, snaps[0])
+    ref, _ = L.apost_run(dns, les, delta, snaps[1:], ub0, NU, dt, forcing=1.0)
+    plan = eles.filter_setup(dns, les, delta, precision=prec)
+    solver = eles.les_create(les, NU, forcing=1.0)
+    cuda = torch.device("cuda")
+    ubar_dns = torch.empty((3, les.ny, les.nz, les.nx), device=cuda, dtype=plan.dtype)
+    tau = torch.empty((6, les.ny, les.nz, les.nx), device=cuda, dtype=plan.dtype)
+    u0 = dev(snaps[0], plan.dtype)
+    eles.filter_fields(plan, u0, ubar_dns)
+    ubar_les = ubar_dns.double().contiguous()
+    for s in snaps[1:]:
+        eles.apost_step(plan, solver, dev(s, plan.dtype), ubar_dns, tau, ubar_les, dt)
+    got = host(ubar_les)
+    assert eles.check_device_error(plan) == 0
+    if prec == eles.PREC_FP64:
+        assert rel(got, ref) < 1e-11
+    else:
+        # ubar, T_ij and the wall values within 1e-4 u_tau^2 (u_tau) of the
+        # oracle's: perturbed at random by that much, the oracle's own loop
+        # moves by 1.5e-4 here (u up to 18.4); the bound leaves a factor 7
+        assert np.abs(got - ref).max() < 1e-3
+
+
+def test_apost_refuses_another_grid():
+    dns = I.dns_grid(32, 33, 32, 2 * math.pi, math.pi)
+    plan = eles.filter_setup(dns, I.les_grid(dns, 8, 9, 8), 2 * math.pi / 16, precision=eles.PREC_FP64)
+    other = I.les_grid(dns, 16, 17, 16)
+    solver = eles.les_create(other, NU)
+    cuda = torch.device("cuda")
+    u = torch.zeros((3, 33, 32, 32), device=cuda, dtype=torch.float64)
+    ub = torch.zeros((3, 9, 8, 8), device=cuda, dtype=torch.float64)
+    tau = torch.zeros((6, 9, 8, 8), device=cuda, dtype=torch.float64)
+    with pytest.raises(eles.EFError) as e:
+        eles.apost_step(plan, solver, u, ub, tau, torch.zeros((3, 17, 16, 16), device=cuda, dtype=torch.float64),
+                        0.01)
+    assert e.value.code == eles.EF_ERR_SHAPE
+
+
+def test_full_les_grid_invariants():
+    """The 64 x 65 x 48 LES grid of the 512 x 257 x 384 channel."""
+    dns = I.dns_grid(512, 257, 384, 2 * math.pi, math.pi)
+    g = I.les_grid(dns, 64, 65, 48)
+    y = np.asarray(g.y)
+    solver = eles.les_create(g, NU, forcing=1.0)
+    u = np.zeros((3, g.ny, g.nz, g.nx))
+    u[0] = (1.0 / (2 * NU) * (1 - y * y))[:, None, None]
+    ud = dev(u)
+    for _ in range(5):
+        eles.les_step(solver, ud, 0.01)
+    assert rel(host(ud), u) < 1e-13
+    rng = np.random.default_rng(9)
+    r = rng.standard_normal((3, g.ny, g.nz, g.nx))
+    r[1, 0] = r[1, -1] = 0.0
+    rd = dev(r)
+    eles.les_project(solver, rd, rd)
+    div = torch.empty(rd.shape[1:], device=rd.device, dtype=torch.float64)
+    eles.les_divergence(solver, rd, div)
+    assert np.abs(host(div)).max() < 1e-11 * np.abs(r).max() / np.diff(y).min()
