@@ -552,7 +552,7 @@ def apost_measure(eles, torch, dns, les, plan, u, ub, tau, stream, timed, steps)
     ns = u.shape[0]
     ub1, tau1 = ub[0], tau[0]
     eles.filter_fields(plan, u[0], ub1, stream=stream)
-    ubar_les = ub1.double().contiguous()
+    ubar_les = ub1.to(torch.float64, copy=True)
     dt = 1e-3
     state = {"k": 0}
 

@@ -581,6 +581,10 @@ int ef_apost_step(ef_plan *plan, ef_les *s, const void *u_dns, void *ubar_dns, v
         set_error("ef_apost_step: the plan's LES grid is not the solver's");
         return EF_ERR_SHAPE;
     }
+    if (static_cast<const void *>(ubar_les) == ubar_dns || static_cast<const void *>(ubar_les) == tau) {
+        set_error("ef_apost_step: ubar_les must not be ubar_dns or tau");
+        return EF_ERR_ARG;
+    }
     int rc = ef_subfilter_stress(plan, u_dns, ubar_dns, tau, nullptr, stream);
     if (rc) return rc;
     return ef_les_step(s, ubar_les, tau, ubar_dns, plan->prec, dt, stream);

@@ -157,7 +157,7 @@ def test_apost_loop_matches_oracle(name):
     tau = torch.empty((6, les.ny, les.nz, les.nx), device=cuda, dtype=plan.dtype)
     u0 = dev(snaps[0], plan.dtype)
     eles.filter_fields(plan, u0, ubar_dns)
-    ubar_les = ubar_dns.double().contiguous()
+    ubar_les = ubar_dns.to(torch.float64, copy=True)
     for s in snaps[1:]:
         eles.apost_step(plan, solver, dev(s, plan.dtype), ubar_dns, tau, ubar_les, dt)
     got = host(ubar_les)
@@ -184,6 +184,11 @@ def test_apost_refuses_another_grid():
         eles.apost_step(plan, solver, u, ub, tau, torch.zeros((3, 17, 16, 16), device=cuda, dtype=torch.float64),
                         0.01)
     assert e.value.code == eles.EF_ERR_SHAPE
+    # the LES field may not be the filter's output buffer
+    same = eles.les_create(I.les_grid(dns, 8, 9, 8), NU)
+    with pytest.raises(eles.EFError) as e:
+        eles.apost_step(plan, same, u, ub, tau, ub, 0.01)
+    assert e.value.code == eles.EF_ERR_ARG
 
 
 def test_full_les_grid_invariants():
