@@ -37,11 +37,14 @@
 // its first unknown is set to zero (the right-hand side is consistent: the
 // divergence telescopes to the wall values of u_2, which are zero).
 //
-// All arithmetic is FP64.  The transforms are plain sums over tabulated
-// twiddles: the LES grids are small (the DNS filter dominates the loop).
+// All arithmetic is FP64.  The transforms are Stockham FFTs (radices 4, 2,
+// 3, 5, 7; one warp per line in shared memory, twiddles from host-built
+// tables) for lines of at most 1024 points with no other prime factor, and
+// plain sums over the same tables otherwise.
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "eles_internal.h"
@@ -50,6 +53,8 @@ namespace {
 
 constexpr int kLesThreads = 256;
 constexpr int kLesMaxN = 4096;          // largest nx, ny, nz of an LES grid
+constexpr int kLesMaxStages = 16;       // radix stages of one transform
+constexpr int kLesFftMaxN = 1024;       // longest line transformed by the FFT kernels (32 KB per warp)
 
 // Twiddle and per-row tables (device), and the sizes they are for.
 struct LesGeom {
@@ -61,6 +66,8 @@ struct LesGeom {
     const double *cosx, *sinx;           // [nx] cos, sin of 2 pi r / nx
     const double *cosz, *sinz;           // [nz]
     const double *k2x, *k2z;             // [nxh] s_x^2, [nz] s_z^2 (exact zeros where the symbol is zero)
+    int nfx, nfz;                        // Stockham stages of the x and z transforms (0: plain sums)
+    int fx[kLesMaxStages], fz[kLesMaxStages];   // their radices, in order (4, 2, 3, 5, 7)
 };
 
 __host__ __device__ inline int pair_of(int a, int b)
@@ -197,7 +204,8 @@ __host__ __device__ inline void dftz_point(const LesGeom &g, const double2 *src,
 // of even j (starting at j = 2), 1 for odd j (starting at j = 1).  In place
 // on C (right-hand side in, phi out); cw holds the eliminated coefficients.
 // The chain's wall rows of C are set to zero (phi = 0 on the walls).
-__host__ __device__ inline void chain_point(const LesGeom &g, double2 *C, double *cw, long t)
+__host__ __device__ inline void chain_point(const LesGeom &g, double2 *__restrict__ C, double *__restrict__ cw,
+                                            long t)
 {
     const int p = (int)(t & 1);
     const long mode = t >> 1;
@@ -284,6 +292,74 @@ __host__ __device__ inline void correct_point(const LesGeom &g, const double *us
     u[2 * N + idx] = us[2 * N + idx] - (phi[zp] - phi[zm]) / (2.0 * g.hz);
 }
 
+// One radix-R stage (R in 2, 3, 4, 5, 7) of a length-n Stockham transform
+// in natural order: butterfly j in [0, n / R), Ns the product of the radices
+// of the earlier stages.  Its R inputs in[j + r n / R] are turned by
+// exp(sgn 2 pi i r (j mod Ns) / (Ns R)), transformed by an R-point DFT and
+// written to out[(j / Ns) Ns R + (j mod Ns) + q Ns].  sgn = -1 forward,
+// +1 inverse (no scaling).  Twiddles from the length-n tables.
+template <int R>
+__host__ __device__ inline void stockham_stage_r(const double2 *in, double2 *out, int n, int Ns, int j, double sgn,
+                                                 const double *cs, const double *sn)
+{
+    double2 v[R];
+    const int k = j % Ns, span = n / R, tstep = n / (Ns * R);
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const double2 a = in[j + r * span];
+        const int t = (r * k * tstep) % n;
+        const double c = cs[t], si = sgn * sn[t];
+        v[r] = make_double2(a.x * c - a.y * si, a.x * si + a.y * c);
+    }
+    const int base = (j / Ns) * Ns * R + k;
+    if (R == 2) {
+        out[base] = make_double2(v[0].x + v[1].x, v[0].y + v[1].y);
+        out[base + Ns] = make_double2(v[0].x - v[1].x, v[0].y - v[1].y);
+    } else if (R == 4) {
+        const double2 t0 = make_double2(v[0].x + v[2 % R].x, v[0].y + v[2 % R].y);
+        const double2 t1 = make_double2(v[0].x - v[2 % R].x, v[0].y - v[2 % R].y);
+        const double2 t2 = make_double2(v[1].x + v[3 % R].x, v[1].y + v[3 % R].y);
+        const double2 t3 = make_double2(v[1].x - v[3 % R].x, v[1].y - v[3 % R].y);
+        const double2 wt3 = make_double2(-sgn * t3.y, sgn * t3.x);   // exp(sgn i pi / 2) t3
+        out[base] = make_double2(t0.x + t2.x, t0.y + t2.y);
+        out[base + Ns] = make_double2(t1.x + wt3.x, t1.y + wt3.y);
+        out[base + 2 * Ns] = make_double2(t0.x - t2.x, t0.y - t2.y);
+        out[base + 3 * Ns] = make_double2(t1.x - wt3.x, t1.y - wt3.y);
+    } else {
+        const int rstep = n / R;
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+            double re = v[0].x, im = v[0].y;
+#pragma unroll
+            for (int r = 1; r < R; r++) {
+                const int t = (r * q * rstep) % n;
+                const double c = cs[t], si = sgn * sn[t];
+                re += v[r].x * c - v[r].y * si;
+                im += v[r].x * si + v[r].y * c;
+            }
+            out[base + q * Ns] = make_double2(re, im);
+        }
+    }
+}
+
+// One radix-R stage (R in 2, 3, 4, 5, 7) of a length-n Stockham transform
+// in natural order: butterfly j in [0, n / R), Ns the product of the radices
+// of the earlier stages.  Its R inputs in[j + r n / R] are turned by
+// exp(sgn 2 pi i r (j mod Ns) / (Ns R)), transformed by an R-point DFT and
+// written to out[(j / Ns) Ns R + (j mod Ns) + q Ns].  sgn = -1 forward,
+// +1 inverse (no scaling).  Twiddles from the length-n tables.
+__host__ __device__ inline void stockham_stage(const double2 *in, double2 *out, int n, int Ns, int R, int j,
+                                               double sgn, const double *cs, const double *sn)
+{
+    switch (R) {
+    case 2: stockham_stage_r<2>(in, out, n, Ns, j, sgn, cs, sn); break;
+    case 3: stockham_stage_r<3>(in, out, n, Ns, j, sgn, cs, sn); break;
+    case 4: stockham_stage_r<4>(in, out, n, Ns, j, sgn, cs, sn); break;
+    case 5: stockham_stage_r<5>(in, out, n, Ns, j, sgn, cs, sn); break;
+    default: stockham_stage_r<7>(in, out, n, Ns, j, sgn, cs, sn); break;
+    }
+}
+
 // ---- kernels: grid-stride loops over the items of each point function ----
 
 #define LES_LOOP(n) for (long it = (long)blockIdx.x * blockDim.x + threadIdx.x; it < (n); it += (long)gridDim.x * blockDim.x)
@@ -335,6 +411,90 @@ __global__ void __launch_bounds__(kLesThreads) les_correct(LesGeom g, const doub
 
 #undef LES_LOOP
 
+// Transforms by Stockham FFTs, one warp per line, the line in two shared
+// buffers of n complex values per warp (lanes split each stage's butterflies;
+// __syncwarp between stages).  W warps per block, each walking lines
+// line0 = blockIdx.x W + warp, line0 + gridDim.x W, ...
+__device__ inline double2 *warp_fft(double2 *a, double2 *b, int n, int nf, const int *f, double sgn,
+                                    const double *cs, const double *sn, int lane)
+{
+    int Ns = 1;
+    for (int s = 0; s < nf; s++) {
+        const int R = f[s];
+        for (int j = lane; j < n / R; j += 32) stockham_stage(a, b, n, Ns, R, j, sgn, cs, sn);
+        __syncwarp();
+        double2 *t = a; a = b; b = t;
+        Ns *= R;
+    }
+    return a;
+}
+
+// Forward x: real rows b[line][0..nx) -> B[line][0..nxh).
+__global__ void __launch_bounds__(128) les_fftx_fwd(LesGeom g, const double *b, double2 *B)
+{
+    extern __shared__ double2 fsm[];
+    const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, n = g.nx;
+    double2 *a0 = fsm + (size_t)warp * 2 * n, *b0 = a0 + n;
+    const long lines = (long)g.ny * g.nz;
+    for (long line = (long)blockIdx.x * W + warp; line < lines; line += (long)gridDim.x * W) {
+        const double *row = b + line * n;
+        for (int i = lane; i < n; i += 32) a0[i] = make_double2(row[i], 0.0);
+        __syncwarp();
+        const double2 *res = warp_fft(a0, b0, n, g.nfx, g.fx, -1.0, g.cosx, g.sinx, lane);
+        double2 *dst = B + line * g.nxh;
+        for (int m = lane; m < g.nxh; m += 32) dst[m] = res[m];
+        __syncwarp();
+    }
+}
+
+// Inverse x: B[line][0..nxh) (the Hermitian half) -> real rows phi[line][0..nx), scale 1 / nx.
+__global__ void __launch_bounds__(128) les_fftx_inv(LesGeom g, const double2 *B, double *phi)
+{
+    extern __shared__ double2 fsm[];
+    const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, n = g.nx;
+    double2 *a0 = fsm + (size_t)warp * 2 * n, *b0 = a0 + n;
+    const long lines = (long)g.ny * g.nz;
+    const double inv = 1.0 / n;
+    for (long line = (long)blockIdx.x * W + warp; line < lines; line += (long)gridDim.x * W) {
+        const double2 *src = B + line * g.nxh;
+        for (int m = lane; m < n; m += 32) {
+            if (m < g.nxh) {
+                a0[m] = src[m];
+            } else {
+                const double2 c = src[n - m];
+                a0[m] = make_double2(c.x, -c.y);
+            }
+        }
+        __syncwarp();
+        const double2 *res = warp_fft(a0, b0, n, g.nfx, g.fx, 1.0, g.cosx, g.sinx, lane);
+        double *dst = phi + line * n;
+        for (int i = lane; i < n; i += 32) dst[i] = res[i].x * inv;
+        __syncwarp();
+    }
+}
+
+// z transform of the columns (j, m): src[j][k][m] -> dst[j][q][m], sign sgn, scale.
+__global__ void __launch_bounds__(128) les_fftz(LesGeom g, const double2 *src, double2 *dst, double sgn,
+                                                double scale)
+{
+    extern __shared__ double2 fsm[];
+    const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, n = g.nz;
+    double2 *a0 = fsm + (size_t)warp * 2 * n, *b0 = a0 + n;
+    const long lines = (long)g.ny * g.nxh;
+    for (long line = (long)blockIdx.x * W + warp; line < lines; line += (long)gridDim.x * W) {
+        const long j = line / g.nxh, m = line % g.nxh;
+        const double2 *col = src + j * (long)n * g.nxh + m;
+        for (int k = lane; k < n; k += 32) a0[k] = col[(long)k * g.nxh];
+        __syncwarp();
+        const double2 *res = warp_fft(a0, b0, n, g.nfz, g.fz, sgn, g.cosz, g.sinz, lane);
+        double2 *out = dst + j * (long)n * g.nxh + m;
+        for (int q = lane; q < n; q += 32) out[(long)q * g.nxh] = make_double2(res[q].x * scale, res[q].y * scale);
+        __syncwarp();
+    }
+}
+
+inline int fft_warps(int n) { int w = 49152 / (32 * n); return w < 1 ? 1 : (w > 4 ? 4 : w); }
+
 inline int blocks_for(long n)
 {
     long b = (n + kLesThreads - 1) / kLesThreads;
@@ -377,6 +537,19 @@ void les_tables(int nx, int ny, int nz, double Lx, double Lz, const double *y, s
     }
 }
 
+// Radices of a Stockham transform of length n (4 first, then 2, 3, 5, 7);
+// 0 if n is longer than kLesFftMaxN or has another prime factor.
+int les_radices(int n, int *f)
+{
+    if (n > kLesFftMaxN) return 0;
+    int nf = 0, m = n;
+    while (m % 4 == 0) { f[nf++] = 4; m /= 4; }
+    while (m % 2 == 0) { f[nf++] = 2; m /= 2; }
+    for (int p : {3, 5, 7})
+        while (m % p == 0) { f[nf++] = p; m /= p; }
+    return m == 1 ? nf : 0;
+}
+
 // Point g at tables packed as by les_tables at `base`.
 void les_bind(int nx, int ny, int nz, double Lx, double Lz, const double *base, LesGeom *g)
 {
@@ -385,6 +558,8 @@ void les_bind(int nx, int ny, int nz, double Lx, double Lz, const double *base, 
     g->dlinv = base; g->lapm = base + ny; g->lapp = base + 2 * ny; g->cm = base + 3 * ny; g->cp = base + 4 * ny;
     g->cosx = base + 5 * ny; g->sinx = g->cosx + nx; g->cosz = g->sinx + nx; g->sinz = g->cosz + nz;
     g->k2x = g->sinz + nz; g->k2z = g->k2x + nxh;
+    g->nfx = les_radices(nx, g->fx);
+    g->nfz = les_radices(nz, g->fz);
 }
 
 }  // namespace
@@ -416,12 +591,21 @@ cudaError_t launch_projection(ef_les *s, const double *ustar, double *u, cudaStr
 {
     const LesGeom &g = s->g;
     const long N = les_points(s), NH = (long)g.nxh * g.ny * g.nz;
+    const long xlines = (long)g.ny * g.nz, zlines = (long)g.ny * g.nxh;
+    const int wx = fft_warps(g.nx), wz = fft_warps(g.nz);
+    const int bx = (int)std::min<long>((xlines + wx - 1) / wx, 152L * 16);
+    const int bz = (int)std::min<long>((zlines + wz - 1) / wz, 152L * 16);
+    const size_t shx = sizeof(double2) * 2 * g.nx * wx, shz = sizeof(double2) * 2 * g.nz * wz;
     les_div<<<blocks_for(N), kLesThreads, 0, st>>>(g, ustar, s->d_b);
-    les_dftx_fwd<<<blocks_for(NH), kLesThreads, 0, st>>>(g, s->d_b, s->d_B);
-    les_dftz<<<blocks_for(NH), kLesThreads, 0, st>>>(g, s->d_B, s->d_C, -1.0, 1.0);
+    if (g.nfx) les_fftx_fwd<<<bx, 32 * wx, shx, st>>>(g, s->d_b, s->d_B);
+    else les_dftx_fwd<<<blocks_for(NH), kLesThreads, 0, st>>>(g, s->d_b, s->d_B);
+    if (g.nfz) les_fftz<<<bz, 32 * wz, shz, st>>>(g, s->d_B, s->d_C, -1.0, 1.0);
+    else les_dftz<<<blocks_for(NH), kLesThreads, 0, st>>>(g, s->d_B, s->d_C, -1.0, 1.0);
     les_chain<<<blocks_for(2L * g.nxh * g.nz), kLesThreads, 0, st>>>(g, s->d_C, s->d_cw);
-    les_dftz<<<blocks_for(NH), kLesThreads, 0, st>>>(g, s->d_C, s->d_B, 1.0, 1.0 / g.nz);
-    les_dftx_inv<<<blocks_for(N), kLesThreads, 0, st>>>(g, s->d_B, s->d_b);
+    if (g.nfz) les_fftz<<<bz, 32 * wz, shz, st>>>(g, s->d_C, s->d_B, 1.0, 1.0 / g.nz);
+    else les_dftz<<<blocks_for(NH), kLesThreads, 0, st>>>(g, s->d_C, s->d_B, 1.0, 1.0 / g.nz);
+    if (g.nfx) les_fftx_inv<<<bx, 32 * wx, shx, st>>>(g, s->d_B, s->d_b);
+    else les_dftx_inv<<<blocks_for(N), kLesThreads, 0, st>>>(g, s->d_B, s->d_b);
     les_correct<<<blocks_for(N), kLesThreads, 0, st>>>(g, ustar, s->d_b, u);
     return cudaGetLastError();
 }

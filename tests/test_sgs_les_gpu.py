@@ -34,7 +34,9 @@ from paper_1902_02508_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 NU = 1.0 / 180.0
-SHAPES = [(32, 33, 24), (12, 10, 9), (16, 17, 12)]
+# transforms: Stockham radices 4 2 3 (first three), 2 7 in x with plain sums in
+# z (22 = 2 x 11), 4 5 in x and 2 3 5 in z
+SHAPES = [(32, 33, 24), (12, 10, 9), (16, 17, 12), (14, 9, 22), (20, 11, 30)]
 
 
 @pytest.fixture(scope="module", autouse=True)
