@@ -562,7 +562,9 @@ int ef_closure_load(ef_closure *closure, const char *path);
  *     orthogonal projection, in the inner product weighted by
  *     (y[j+1] - y[j-1]) / 2, onto velocities of zero discrete divergence at
  *     every interior node, the wall values held; computed by discrete
- *     Fourier transforms in x and z and two tridiagonal solves in y per mode.
+ *     Fourier transforms in x and z (mixed-radix FFTs for lines of at most
+ *     1024 points with prime factors 2, 3, 5, 7; plain sums otherwise) and
+ *     two tridiagonal solves in y per mode.
  * Fields are device [3][ny][nz][nx] FP64 with x fastest; tau is the
  * [6][ny][nz][nx] output of ef_subfilter_stress in the precision of its
  * plan (double for EF_PREC_FP64, float otherwise), as is the wall-value
