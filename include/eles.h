@@ -568,7 +568,7 @@ int ef_closure_load(ef_closure *closure, const char *path);
  * Fields are device [3][ny][nz][nx] FP64 with x fastest; tau is the
  * [6][ny][nz][nx] output of ef_subfilter_stress in the precision of its
  * plan (double for EF_PREC_FP64, float otherwise), as is the wall-value
- * field ubar_bc.  The solver owns its scratch (about 12 doubles per node);
+ * field ubar_bc.  The solver owns its scratch (about 13 doubles per node);
  * calls on one solver must not overlap on the GPU.  Calls are asynchronous
  * on `stream` and allocate nothing.
  */
@@ -581,7 +581,8 @@ typedef struct {
 typedef struct ef_les ef_les;
 
 /* Set-up on the current device for the LES grid `les` (3 to 4096 nodes per
- * direction).  Errors: EF_ERR_ARG, EF_ERR_SHAPE, EF_ERR_OOM, EF_ERR_CUDA. */
+ * direction, at most 2^28 in all).  Errors: EF_ERR_ARG, EF_ERR_SHAPE,
+ * EF_ERR_OOM, EF_ERR_CUDA. */
 int ef_les_create(const ef_grid *les, const ef_les_cfg *cfg, ef_les **out);
 void ef_les_destroy(ef_les *les);
 

@@ -55,11 +55,13 @@ constexpr int kLesThreads = 256;
 constexpr int kLesMaxN = 4096;          // largest nx, ny, nz of an LES grid
 constexpr int kLesMaxStages = 16;       // radix stages of one transform
 constexpr int kLesFftMaxN = 1024;       // longest line transformed by the FFT kernels (32 KB per warp)
+constexpr long kLesMaxPoints = 1L << 28; // largest LES grid (node indices fit 32-bit arithmetic)
 
 // Twiddle and per-row tables (device), and the sizes they are for.
 struct LesGeom {
     int nx, ny, nz, nxh;                 // nxh = nx / 2 + 1 x modes kept
     double hx, hz;
+    double ix2, iz2, ixx, izz;           // 1 / (2 hx), 1 / (2 hz), 1 / hx^2, 1 / hz^2
     const double *dlinv;                 // [ny] 1 / (y[j+1] - y[j-1]) (interior rows)
     const double *lapm, *lapp;           // [ny] y-Laplacian weights of f[j-1] and f[j+1]
     const double *cm, *cp;               // [ny] chain couplings (above)
@@ -88,9 +90,10 @@ __host__ __device__ inline double tau_at(const TT *tau, long N, int pair, long i
 template <typename TT>
 __host__ __device__ inline void walls_point(const LesGeom &g, double *u, const TT *bc, long w)
 {
-    const long nxz = (long)g.nz * g.nx, N = nxz * g.ny;
-    const long row = (w / nxz) ? (long)(g.ny - 1) : 0;
-    const long idx = row * nxz + w % nxz;
+    const int nxz = g.nz * g.nx;
+    const long N = (long)nxz * g.ny;
+    const int wi = (int)w;
+    const long idx = (long)((wi / nxz) ? g.ny - 1 : 0) * nxz + wi % nxz;
     u[N + idx] = 0.0;
     u[idx] = bc ? (double)bc[idx] : 0.0;
     u[2 * N + idx] = bc ? (double)bc[2 * N + idx] : 0.0;
@@ -105,7 +108,8 @@ __host__ __device__ inline void rhs_point(const LesGeom &g, const double *u, con
 {
     const int nx = g.nx, nz = g.nz, ny = g.ny;
     const long nxz = (long)nx * nz, N = nxz * ny;
-    const int i = (int)(idx % nx), k = (int)((idx / nx) % nz), j = (int)(idx / nxz);
+    const int id = (int)idx, row = id / nx;
+    const int i = id - row * nx, j = row / nz, k = row - j * nz;
     if (j == 0 || j == ny - 1) {
         for (int c = 0; c < 3; c++) {
             ustar[c * N + idx] = u[c * N + idx];
@@ -118,8 +122,7 @@ __host__ __device__ inline void rhs_point(const LesGeom &g, const double *u, con
     const long zrow = (long)j * nxz + i;
     const long zp = zrow + (long)(k + 1 == nz ? 0 : k + 1) * nx, zm = zrow + (long)(k == 0 ? nz - 1 : k - 1) * nx;
     const long yp = idx + nxz, ym = idx - nxz;
-    const double ix2 = 1.0 / (2.0 * g.hx), iz2 = 1.0 / (2.0 * g.hz);
-    const double ixx = 1.0 / (g.hx * g.hx), izz = 1.0 / (g.hz * g.hz);
+    const double ix2 = g.ix2, iz2 = g.iz2, ixx = g.ixx, izz = g.izz;
     const double dl = g.dlinv[j], wm = g.lapm[j], wp = g.lapp[j];
     for (int c = 0; c < 3; c++) {
         const double *uc = u + c * N;
@@ -148,7 +151,8 @@ __host__ __device__ inline void div_point(const LesGeom &g, const double *us, do
 {
     const int nx = g.nx, nz = g.nz, ny = g.ny;
     const long nxz = (long)nx * nz, N = nxz * ny;
-    const int i = (int)(idx % nx), k = (int)((idx / nx) % nz), j = (int)(idx / nxz);
+    const int id = (int)idx, row = id / nx;
+    const int i = id - row * nx, j = row / nz, k = row - j * nz;
     if (j == 0 || j == ny - 1) {
         b[idx] = 0.0;
         return;
@@ -157,8 +161,8 @@ __host__ __device__ inline void div_point(const LesGeom &g, const double *us, do
     const long xp = base + (i + 1 == nx ? 0 : i + 1), xm = base + (i == 0 ? nx - 1 : i - 1);
     const long zrow = (long)j * nxz + i;
     const long zp = zrow + (long)(k + 1 == nz ? 0 : k + 1) * nx, zm = zrow + (long)(k == 0 ? nz - 1 : k - 1) * nx;
-    b[idx] = (us[xp] - us[xm]) / (2.0 * g.hx) + (us[N + idx + nxz] - us[N + idx - nxz]) * g.dlinv[j] +
-             (us[2 * N + zp] - us[2 * N + zm]) / (2.0 * g.hz);
+    b[idx] = (us[xp] - us[xm]) * g.ix2 + (us[N + idx + nxz] - us[N + idx - nxz]) * g.dlinv[j] +
+             (us[2 * N + zp] - us[2 * N + zm]) * g.iz2;
 }
 
 // Forward x transform: B[j][k][m] = sum_i b[j][k][i] exp(-2 pi i m i / nx).
@@ -200,57 +204,86 @@ __host__ __device__ inline void dftz_point(const LesGeom &g, const double2 *src,
     dst[o] = make_double2(re * scale, im * scale);
 }
 
+// The eliminated coefficients of every chain, which depend only on the mode:
+// for chain row j, cw = c'_j and cinv = 1 / (b_j - a_j c'_{j-2}) of the Thomas
+// forward sweep (host, at set-up).  The singular chain's first row is
+// replaced by phi = 0: cinv = 0 there makes its eliminated right-hand side
+// zero.  Layout [j][q][m] as C; wall rows unused.
+void les_chain_tables(const LesGeom &g, std::vector<double> &cw, std::vector<double> &cinv)
+{
+    const int ny = g.ny, nz = g.nz, nxh = g.nxh;
+    const long stride = (long)nz * nxh;
+    cw.assign((size_t)ny * stride, 0.0);
+    cinv.assign((size_t)ny * stride, 0.0);
+    for (int q = 0; q < nz; q++)
+        for (int m = 0; m < nxh; m++)
+            for (int p = 0; p < 2; p++) {
+                const int j0 = p ? 1 : 2;
+                if (j0 > ny - 2) continue;
+                int jl = ny - 2;
+                if ((jl & 1) != p) jl--;
+                const double k2 = g.k2x[m] + g.k2z[q];
+                const bool singular = (k2 == 0.0) && (j0 == 1) && (jl == ny - 2);
+                double cprev = 0.0;
+                for (int j = j0; j <= jl; j += 2) {
+                    const long o = (long)j * stride + (long)q * nxh + m;
+                    const double a = (j - 2 >= 1) ? g.cm[j] : 0.0;
+                    const double c = (j + 2 <= ny - 2) ? g.cp[j] : 0.0;
+                    if (singular && j == j0) {
+                        cw[o] = 0.0;
+                        cinv[o] = 0.0;
+                        cprev = 0.0;
+                        continue;
+                    }
+                    const double den = (-g.cm[j] - g.cp[j] - k2) - a * cprev;
+                    cw[o] = c / den;
+                    cinv[o] = 1.0 / den;
+                    cprev = cw[o];
+                }
+            }
+}
+
 // One chain of one mode: item t = (q nxh + m) * 2 + p, p = 0 for the chain
 // of even j (starting at j = 2), 1 for odd j (starting at j = 1).  In place
-// on C (right-hand side in, phi out); cw holds the eliminated coefficients.
-// The chain's wall rows of C are set to zero (phi = 0 on the walls).
-__host__ __device__ inline void chain_point(const LesGeom &g, double2 *__restrict__ C, double *__restrict__ cw,
+// on C (right-hand side in, phi out) with the eliminated coefficients of
+// les_chain_tables.  The chain's wall rows of C are set to zero (phi = 0 on
+// the walls).
+__host__ __device__ inline void chain_point(const LesGeom &g, double2 *__restrict__ C,
+                                            const double *__restrict__ cw, const double *__restrict__ cinv,
                                             long t)
 {
     const int p = (int)(t & 1);
-    const long mode = t >> 1;
-    const int m = (int)(mode % g.nxh), q = (int)(mode / g.nxh);
+    const int mode = (int)(t >> 1);
+    const int q = mode / g.nxh, m = mode - q * g.nxh;
     const int ny = g.ny;
     const long stride = (long)g.nz * g.nxh;            // between rows j of one mode
-    double2 *col = C + (long)q * g.nxh + m;
-    double *cwc = cw + (long)q * g.nxh + m;
+    const long off = (long)q * g.nxh + m;
+    double2 *col = C + off;
     if (p == 0) col[0] = make_double2(0.0, 0.0);
     if (((ny - 1) & 1) == p) col[(long)(ny - 1) * stride] = make_double2(0.0, 0.0);
     const int j0 = p ? 1 : 2;
     if (j0 > ny - 2) return;
     int jl = ny - 2;
     if ((jl & 1) != p) jl--;
-    const double k2 = g.k2x[m] + g.k2z[q];
-    const bool singular = (k2 == 0.0) && (j0 == 1) && (jl == ny - 2);
     // forward elimination
-    double cprev = 0.0;
     double2 dprev = make_double2(0.0, 0.0);
     for (int j = j0; j <= jl; j += 2) {
+        const long o = (long)j * stride;
         const double a = (j - 2 >= 1) ? g.cm[j] : 0.0;
-        const double c = (j + 2 <= ny - 2) ? g.cp[j] : 0.0;
-        double bd = -g.cm[j] - g.cp[j] - k2;
-        double2 rhs = col[(long)j * stride];
-        double cc = c;
-        if (singular && j == j0) {
-            bd = 1.0;
-            cc = 0.0;
-            rhs = make_double2(0.0, 0.0);
-        }
-        const double den = bd - a * cprev;
-        const double cn = cc / den;
-        const double2 dn = make_double2((rhs.x - a * dprev.x) / den, (rhs.y - a * dprev.y) / den);
-        cwc[(long)j * stride] = cn;
-        col[(long)j * stride] = dn;
-        cprev = cn;
+        const double2 rhs = col[o];
+        const double inv = cinv[off + o];
+        const double2 dn = make_double2((rhs.x - a * dprev.x) * inv, (rhs.y - a * dprev.y) * inv);
+        col[o] = dn;
         dprev = dn;
     }
     // back substitution
     double2 next = col[(long)jl * stride];
     for (int j = jl - 2; j >= j0; j -= 2) {
-        const double cn = cwc[(long)j * stride];
-        const double2 d = col[(long)j * stride];
+        const long o = (long)j * stride;
+        const double cn = cw[off + o];
+        const double2 d = col[o];
         next = make_double2(d.x - cn * next.x, d.y - cn * next.y);
-        col[(long)j * stride] = next;
+        col[o] = next;
     }
 }
 
@@ -278,7 +311,8 @@ __host__ __device__ inline void correct_point(const LesGeom &g, const double *us
 {
     const int nx = g.nx, nz = g.nz, ny = g.ny;
     const long nxz = (long)nx * nz, N = nxz * ny;
-    const int i = (int)(idx % nx), k = (int)((idx / nx) % nz), j = (int)(idx / nxz);
+    const int id = (int)idx, row = id / nx;
+    const int i = id - row * nx, j = row / nz, k = row - j * nz;
     if (j == 0 || j == ny - 1) {
         for (int c = 0; c < 3; c++) u[c * N + idx] = us[c * N + idx];
         return;
@@ -287,9 +321,9 @@ __host__ __device__ inline void correct_point(const LesGeom &g, const double *us
     const long xp = base + (i + 1 == nx ? 0 : i + 1), xm = base + (i == 0 ? nx - 1 : i - 1);
     const long zrow = (long)j * nxz + i;
     const long zp = zrow + (long)(k + 1 == nz ? 0 : k + 1) * nx, zm = zrow + (long)(k == 0 ? nz - 1 : k - 1) * nx;
-    u[idx] = us[idx] - (phi[xp] - phi[xm]) / (2.0 * g.hx);
+    u[idx] = us[idx] - (phi[xp] - phi[xm]) * g.ix2;
     u[N + idx] = us[N + idx] - (phi[idx + nxz] - phi[idx - nxz]) * g.dlinv[j];
-    u[2 * N + idx] = us[2 * N + idx] - (phi[zp] - phi[zm]) / (2.0 * g.hz);
+    u[2 * N + idx] = us[2 * N + idx] - (phi[zp] - phi[zm]) * g.iz2;
 }
 
 // One radix-R stage (R in 2, 3, 4, 5, 7) of a length-n Stockham transform
@@ -394,9 +428,9 @@ __global__ void __launch_bounds__(kLesThreads) les_dftz(LesGeom g, const double2
     LES_LOOP((long)g.nxh * g.ny * g.nz) dftz_point(g, src, dst, sgn, scale, it);
 }
 
-__global__ void __launch_bounds__(kLesThreads) les_chain(LesGeom g, double2 *C, double *cw)
+__global__ void __launch_bounds__(kLesThreads) les_chain(LesGeom g, double2 *C, const double *cw, const double *cinv)
 {
-    LES_LOOP(2L * g.nxh * g.nz) chain_point(g, C, cw, it);
+    LES_LOOP(2L * g.nxh * g.nz) chain_point(g, C, cw, cinv, it);
 }
 
 __global__ void __launch_bounds__(kLesThreads) les_dftx_inv(LesGeom g, const double2 *B, double *phi)
@@ -555,6 +589,8 @@ void les_bind(int nx, int ny, int nz, double Lx, double Lz, const double *base, 
 {
     const int nxh = nx / 2 + 1;
     g->nx = nx; g->ny = ny; g->nz = nz; g->nxh = nxh; g->hx = Lx / nx; g->hz = Lz / nz;
+    g->ix2 = 1.0 / (2.0 * g->hx); g->iz2 = 1.0 / (2.0 * g->hz);
+    g->ixx = 1.0 / (g->hx * g->hx); g->izz = 1.0 / (g->hz * g->hz);
     g->dlinv = base; g->lapm = base + ny; g->lapp = base + 2 * ny; g->cm = base + 3 * ny; g->cp = base + 4 * ny;
     g->cosx = base + 5 * ny; g->sinx = g->cosx + nx; g->cosz = g->sinx + nx; g->sinz = g->cosz + nz;
     g->k2x = g->sinz + nz; g->k2z = g->k2x + nxh;
@@ -574,7 +610,8 @@ struct ef_les {
     double *d_ustar = nullptr;      // [3][N]
     double *d_r = nullptr;          // [3][N] R of the previous substep
     double *d_b = nullptr;          // [N] divergence, then phi
-    double *d_cw = nullptr;         // [ny][nz][nxh] chain elimination coefficients
+    double *d_cw = nullptr;         // [ny][nz][nxh] chain elimination coefficients c'
+    double *d_cinv = nullptr;       // [ny][nz][nxh] their reciprocal pivots
     double2 *d_B = nullptr;         // [ny][nz][nxh] x-transformed
     double2 *d_C = nullptr;         // [ny][nz][nxh] x- and z-transformed
     LesGeom g{};
@@ -601,7 +638,7 @@ cudaError_t launch_projection(ef_les *s, const double *ustar, double *u, cudaStr
     else les_dftx_fwd<<<blocks_for(NH), kLesThreads, 0, st>>>(g, s->d_b, s->d_B);
     if (g.nfz) les_fftz<<<bz, 32 * wz, shz, st>>>(g, s->d_B, s->d_C, -1.0, 1.0);
     else les_dftz<<<blocks_for(NH), kLesThreads, 0, st>>>(g, s->d_B, s->d_C, -1.0, 1.0);
-    les_chain<<<blocks_for(2L * g.nxh * g.nz), kLesThreads, 0, st>>>(g, s->d_C, s->d_cw);
+    les_chain<<<blocks_for(2L * g.nxh * g.nz), kLesThreads, 0, st>>>(g, s->d_C, s->d_cw, s->d_cinv);
     if (g.nfz) les_fftz<<<bz, 32 * wz, shz, st>>>(g, s->d_C, s->d_B, 1.0, 1.0 / g.nz);
     else les_dftz<<<blocks_for(NH), kLesThreads, 0, st>>>(g, s->d_C, s->d_B, 1.0, 1.0 / g.nz);
     if (g.nfx) les_fftx_inv<<<bx, 32 * wx, shx, st>>>(g, s->d_B, s->d_b);
@@ -648,6 +685,10 @@ int ef_les_create(const ef_grid *les, const ef_les_cfg *cfg, ef_les **out)
         set_error("ef_les_create: grid %dx%dx%d outside 3..%d per direction", nx, ny, nz, kLesMaxN);
         return EF_ERR_SHAPE;
     }
+    if ((long)nx * ny * nz > kLesMaxPoints) {
+        set_error("ef_les_create: more than %ld nodes", kLesMaxPoints);
+        return EF_ERR_SHAPE;
+    }
     if (!(les->Lx > 0) || !(les->Lz > 0)) { set_error("ef_les_create: Lx and Lz must be > 0"); return EF_ERR_ARG; }
     for (int j = 1; j < ny; j++)
         if (!(les->y[j] > les->y[j - 1])) { set_error("ef_les_create: y nodes must ascend"); return EF_ERR_ARG; }
@@ -666,17 +707,25 @@ int ef_les_create(const ef_grid *les, const ef_les_cfg *cfg, ef_les **out)
     s->cfg = *cfg;
     s->y.assign(les->y, les->y + ny);
     const int nxh = s->nxh;
-    std::vector<double> tab;
+    std::vector<double> tab, cwh, cinvh;
     les_tables(nx, ny, nz, les->Lx, les->Lz, les->y, tab);
+    {
+        LesGeom hg{};
+        les_bind(nx, ny, nz, les->Lx, les->Lz, tab.data(), &hg);
+        les_chain_tables(hg, cwh, cinvh);
+    }
     const long N = (long)nx * ny * nz, NH = (long)nxh * ny * nz;
     cudaError_t e = dev_malloc(&s->d_tab, sizeof(double) * tab.size());
     if (e == cudaSuccess) e = dev_malloc(&s->d_ustar, sizeof(double) * 3 * N);
     if (e == cudaSuccess) e = dev_malloc(&s->d_r, sizeof(double) * 3 * N);
     if (e == cudaSuccess) e = dev_malloc(&s->d_b, sizeof(double) * N);
     if (e == cudaSuccess) e = dev_malloc(&s->d_cw, sizeof(double) * NH);
+    if (e == cudaSuccess) e = dev_malloc(&s->d_cinv, sizeof(double) * NH);
     if (e == cudaSuccess) e = dev_malloc(&s->d_B, sizeof(double2) * NH);
     if (e == cudaSuccess) e = dev_malloc(&s->d_C, sizeof(double2) * NH);
     if (e == cudaSuccess) e = cudaMemcpy(s->d_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_cw, cwh.data(), sizeof(double) * NH, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_cinv, cinvh.data(), sizeof(double) * NH, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         ef_les_destroy(s);
         return cuda_fail(e, "ef_les_create");
@@ -694,6 +743,7 @@ void ef_les_destroy(ef_les *s)
     cudaFree(s->d_r);
     cudaFree(s->d_b);
     cudaFree(s->d_cw);
+    cudaFree(s->d_cinv);
     cudaFree(s->d_B);
     cudaFree(s->d_C);
     delete s;
