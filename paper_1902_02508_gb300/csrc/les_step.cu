@@ -790,6 +790,11 @@ int ef_les_divergence(ef_les *s, const double *u, double *div, void *stream)
 int ef_les_rhs(ef_les *s, const double *u, const void *tau, int precision, double *rhs, void *stream)
 {
     if (!s || !u || !rhs) { set_error("ef_les_rhs: NULL argument"); return EF_ERR_ARG; }
+    if (precision != EF_PREC_FP64 && precision != EF_PREC_FP32 && precision != EF_PREC_TF32X2 &&
+        precision != EF_PREC_BF16X3) {
+        set_error("ef_les_rhs: unknown precision %d", precision);
+        return EF_ERR_ARG;
+    }
     if (!same_device(s)) { set_error("ef_les_rhs: the current device is not the solver's"); return EF_ERR_ARG; }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const long N = les_points(s);

@@ -80,3 +80,29 @@ def test_hot_calls_reject_null(lib):
     v = ctypes.c_long()
     assert lib.ef_plan_info(None, 0, ctypes.byref(v)) == 1
     lib.ef_plan_destroy(None)
+
+
+def test_les_calls_check_arguments_on_host(lib):
+    """The LES step's entry points (the loop of Fig. 2) refuse bad arguments
+    before touching a device."""
+    y = np.linspace(-1.0, 1.0, 9)
+    cfg = eles._LesCfg(0.01, 1.0, eles.LES_RK3)
+    h = ctypes.c_void_p()
+
+    def create(nx, ny, nz, Lx=1.0, c=cfg, yy=y):
+        g = eles._Grid(nx, ny, nz, Lx, 1.0, yy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return lib.ef_les_create(ctypes.byref(g), ctypes.byref(c), ctypes.byref(h))
+
+    assert create(2, 9, 8) == eles.EF_ERR_SHAPE                 # fewer than 3 nodes in x
+    assert create(8, 9, 5000) == eles.EF_ERR_SHAPE              # more than 4096 in z
+    assert create(8, 9, 8, Lx=0.0) == eles.EF_ERR_ARG
+    assert create(8, 9, 8, yy=y[::-1].copy()) == eles.EF_ERR_ARG   # y nodes must ascend
+    assert create(8, 9, 8, c=eles._LesCfg(-1.0, 1.0, 0)) == eles.EF_ERR_ARG
+    assert create(8, 9, 8, c=eles._LesCfg(0.01, 1.0, 7)) == eles.EF_ERR_ARG
+    assert lib.ef_les_create(None, None, None) == eles.EF_ERR_ARG
+    assert lib.ef_les_step(None, None, None, None, 0, 0.01, None) == eles.EF_ERR_ARG
+    assert lib.ef_les_project(None, None, None, None) == eles.EF_ERR_ARG
+    assert lib.ef_les_divergence(None, None, None, None) == eles.EF_ERR_ARG
+    assert lib.ef_les_rhs(None, None, None, 0, None, None) == eles.EF_ERR_ARG
+    assert lib.ef_apost_step(None, None, None, None, None, None, 0.01, None) == eles.EF_ERR_ARG
+    lib.ef_les_destroy(None)
