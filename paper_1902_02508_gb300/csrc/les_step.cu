@@ -752,6 +752,7 @@ void ef_les_destroy(ef_les *s)
 int ef_les_step(ef_les *s, double *ubar, const void *tau, const void *ubar_bc, int precision, double dt,
                 void *stream)
 {
+    NvtxRange nv("ef_les_step");
     if (!s || !ubar) { set_error("ef_les_step: NULL argument"); return EF_ERR_ARG; }
     if (!(dt > 0) || !isfinite(dt)) { set_error("ef_les_step: dt must be finite and > 0"); return EF_ERR_ARG; }
     if (precision != EF_PREC_FP64 && precision != EF_PREC_FP32 && precision != EF_PREC_TF32X2 &&
@@ -811,6 +812,7 @@ int ef_les_rhs(ef_les *s, const double *u, const void *tau, int precision, doubl
 int ef_apost_step(ef_plan *plan, ef_les *s, const void *u_dns, void *ubar_dns, void *tau, double *ubar_les,
                   double dt, void *stream)
 {
+    NvtxRange nv("ef_apost_step");
     if (!plan || !s || !u_dns || !ubar_dns || !tau || !ubar_les) {
         set_error("ef_apost_step: NULL argument");
         return EF_ERR_ARG;

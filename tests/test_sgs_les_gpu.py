@@ -215,3 +215,47 @@ def test_full_les_grid_invariants():
     div = torch.empty(rd.shape[1:], device=rd.device, dtype=torch.float64)
     eles.les_divergence(solver, rd, div)
     assert np.abs(host(div)).max() < 1e-11 * np.abs(r).max() / np.diff(y).min()
+
+
+PAD = 256                  # guard elements on each side of an output
+CANARY = -1.2345e30
+
+
+def guarded(shape):
+    n = int(np.prod(shape))
+    buf = torch.full((PAD + n + PAD,), CANARY, dtype=torch.float64, device="cuda")
+    return buf, buf[PAD:PAD + n].view(*shape)
+
+
+def untouched(buf, shape, what):
+    n = int(np.prod(shape))
+    torch.cuda.synchronize()
+    b = buf.cpu()
+    assert torch.all(b[:PAD] == CANARY) and torch.all(b[PAD + n:] == CANARY), f"{what}: guard band written"
+    assert not torch.any(b[PAD:PAD + n] == CANARY), f"{what}: output not fully written"
+
+
+@pytest.mark.parametrize("shape", [(20, 11, 30), (14, 9, 22)])
+def test_outputs_stay_inside_their_buffers(shape):
+    """Guard bands of a canary pattern around every output of the LES entry
+    points (FFT and plain-sum transforms): the margins stay untouched, the
+    outputs are written in full, and the inputs are left as they were."""
+    g = les_grid(*shape)
+    u, tau, bc = random_fields(g, 4)
+    les = eles.les_create(g, NU)
+    f3, f1 = (3, g.ny, g.nz, g.nx), (g.ny, g.nz, g.nx)
+    ud, tau_d, bc_d = dev(u), dev(tau), dev(bc)
+    buf, out = guarded(f3)
+    eles.les_project(les, ud, out)
+    untouched(buf, f3, "les_project")
+    buf, out = guarded(f1)
+    eles.les_divergence(les, ud, out)
+    untouched(buf, f1, "les_divergence")
+    buf, out = guarded(f3)
+    eles.les_rhs(les, ud, out, tau=tau_d)
+    untouched(buf, f3, "les_rhs")
+    buf, out = guarded(f3)
+    out.copy_(dev(L.project(u, g)))
+    eles.les_step(les, out, 0.01, tau=tau_d, ubar_bc=bc_d)
+    untouched(buf, f3, "les_step")
+    assert np.array_equal(host(ud), u) and np.array_equal(host(tau_d), tau) and np.array_equal(host(bc_d), bc)
