@@ -607,7 +607,9 @@ int ef_les_rhs(ef_les *les, const double *u, const void *tau, int precision, dou
  * the DNS snapshot u_dns into ubar_dns and tau (device, the plan's LES grid
  * and precision; the caller's scratch), then ef_les_step of ubar_les with
  * that tau and the wall values of ubar_dns.  The plan's LES grid must be the
- * solver's (EF_ERR_SHAPE otherwise); ubar_les must be a buffer of its own
+ * solver's: the call compares the node counts and box lengths (EF_ERR_SHAPE
+ * if they differ); the y nodes are the caller's to keep equal (both set-up
+ * calls take them).  ubar_les must be a buffer of its own
  * (EF_ERR_ARG if it is ubar_dns or tau).  Other errors as the two calls.
  */
 int ef_apost_step(ef_plan *plan, ef_les *les, const void *u_dns, void *ubar_dns, void *tau, double *ubar_les,

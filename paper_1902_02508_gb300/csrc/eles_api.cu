@@ -251,7 +251,6 @@ int ef_filter_setup(const ef_grid *dns, const ef_grid *les, double delta, int ke
     cudaGetDevice(&p->device);
     p->nx = dns->nx; p->ny = dns->ny; p->nz = dns->nz;
     p->nlx = les->nx; p->nly = les->ny; p->nlz = les->nz;
-    p->les_y.assign(les->y, les->y + les->ny);
     p->Lx = dns->Lx; p->Lz = dns->Lz; p->delta = delta;
     p->ext = extension; p->prec = precision;
     p->yquad = kernel == EF_KERNEL_GAUSSIAN_HAT ? 1 : 0;

@@ -166,7 +166,6 @@ struct ef_plan {
     int device = 0;
     int nx = 0, ny = 0, nz = 0, nlx = 0, nly = 0, nlz = 0;
     double Lx = 0, Lz = 0, delta = 0;
-    std::vector<double> les_y;    // LES y nodes (host copy)
     int ext = 0, prec = 0;
     int yquad = 0;                // y quadrature: 0 trapezoid, 1 hat (EF_KERNEL_GAUSSIAN_HAT)
     eles::DiffPlan *diff = nullptr;   // EF_KERNEL_DIFFERENTIAL: its transforms and scratch

@@ -817,8 +817,7 @@ int ef_apost_step(ef_plan *plan, ef_les *s, const void *u_dns, void *ubar_dns, v
         set_error("ef_apost_step: NULL argument");
         return EF_ERR_ARG;
     }
-    if (plan->nlx != s->nx || plan->nly != s->ny || plan->nlz != s->nz || plan->Lx != s->Lx || plan->Lz != s->Lz ||
-        plan->les_y != s->y) {
+    if (plan->nlx != s->nx || plan->nly != s->ny || plan->nlz != s->nz || plan->Lx != s->Lx || plan->Lz != s->Lz) {
         set_error("ef_apost_step: the plan's LES grid is not the solver's");
         return EF_ERR_SHAPE;
     }
