@@ -8,8 +8,10 @@ FP64 oracle of oracle/les.py, through the C ABI.
   * the loop itself: ef_apost_step (filter of the DNS snapshot, then the LES
     step) against oracle.les.apost_run for an FP64 plan, and for split
     precision plans (T_ij within 1e-4 u_tau^2 of the oracle's);
-  * at the 64 x 65 x 48 LES grid of the 512 x 257 x 384 channel: Poiseuille
-    flow stays steady and a projected random field has zero divergence.
+  * at the 64 x 65 x 48 LES grid of the 512 x 257 x 384 channel: one RK3
+    step node by node against the oracle, Poiseuille flow stays steady and a
+    projected random field has zero divergence;
+  * guard bands around every output.
 
 Tolerances: the GPU and the oracle evaluate the same FP64 stencils and the
 same projection (the GPU by Fourier transforms and tridiagonal chains, the
@@ -215,6 +217,24 @@ def test_full_les_grid_invariants():
     div = torch.empty(rd.shape[1:], device=rd.device, dtype=torch.float64)
     eles.les_divergence(solver, rd, div)
     assert np.abs(host(div)).max() < 1e-11 * np.abs(r).max() / np.diff(y).min()
+
+
+def test_full_les_grid_step_matches_oracle():
+    """One RK3 step on the 64 x 65 x 48 LES grid of the 512 x 257 x 384
+    channel, every node against the oracle (random T_ij and wall values)."""
+    dns = I.dns_grid(512, 257, 384, 2 * math.pi, math.pi)
+    g = I.les_grid(dns, 64, 65, 48)
+    rng = np.random.default_rng(12)
+    u = rng.standard_normal((3, g.ny, g.nz, g.nx))
+    u[1, 0] = u[1, -1] = 0.0
+    tau = rng.standard_normal((6, g.ny, g.nz, g.nx)) * 0.1
+    bc = rng.standard_normal((3, g.ny, g.nz, g.nx))
+    u0 = L.project(u, g)
+    ref = L.step(u0, tau, g, NU, 1e-4, 1.0, "rk3", ubc=bc)
+    solver = eles.les_create(g, NU, forcing=1.0)
+    ud = dev(u0)
+    eles.les_step(solver, ud, 1e-4, tau=dev(tau), ubar_bc=dev(bc))
+    assert rel(host(ud), ref) < 1e-12
 
 
 PAD = 256                  # guard elements on each side of an output
