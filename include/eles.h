@@ -544,8 +544,8 @@ int ef_closure_load(ef_closure *closure, const char *path);
 /* ------------------------------------------------------------------------
  * The loop of Sec. 3 and Fig. 2: at every time step the DNS field is
  * filtered, T_ij (Eq. 6) is formed from it, and the explicitly filtered LES
- * equations (Eq. 5, with bar(u_i u_j) = ubar_i ubar_j + T_ij) are advanced
- * one step with that T_ij.  The LES here is a minimal collocated solver on
+ * equations (Eq. 6: Eq. 5 with bar(u_i u_j) = ubar_i ubar_j + T_ij) are
+ * advanced one step with that T_ij.  The LES here is a minimal collocated solver on
  * the LES nodes of the filter, FP64 throughout:
  *   - second-order central differences (periodic in x and z, non-uniform in
  *     y), the three-point Laplacian;

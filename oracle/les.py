@@ -5,7 +5,7 @@ Only the tests use this module; the CUDA library never calls it.
 
 Sec. 3 and Fig. 2 of the paper couple the two computations: at every time
 step the DNS field is filtered, T_ij of Eq. 6 is formed from it (Sec. 2.1),
-and the explicitly filtered LES equations (Eq. 5 with
+and the explicitly filtered LES equations (Eq. 6: Eq. 5 with
 bar(u_i u_j) = ubar_i ubar_j + T_ij) are advanced with that T_ij.  The
 paper's LES is a staggered second-order finite-difference code with a
 fractional-step method and a third-order Runge-Kutta scheme, driven by a

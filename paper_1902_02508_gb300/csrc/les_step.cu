@@ -1,7 +1,7 @@
 // A minimal explicitly filtered LES step driven by the exact subfilter stress
 // (Sec. 3, Fig. 2): at every step the DNS field is filtered, T_ij of Eq. 6 is
-// formed, and the filtered equations (Eq. 5, with bar(u_i u_j) written as
-// ubar_i ubar_j + T_ij) are advanced on the LES nodes with that T_ij.
+// formed, and the discrete filtered equations (Eq. 6: Eq. 5 with bar(u_i u_j)
+// written as ubar_i ubar_j + T_ij) are advanced on the LES nodes with it.
 //
 // Discretisation (the paper's LES is a staggered second-order code with a
 // fractional-step method and a third-order Runge-Kutta scheme; this is its
