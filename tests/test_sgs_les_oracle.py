@@ -18,7 +18,9 @@ advanced with the exact T_ij of Eq. 6).
   * the subfilter term: a wall-normal gradient of T_12 (T_23) drives u_1
     (u_3) alone, by the central difference of the profile; a T_22 profile
     that vanishes on the walls is balanced by the pressure entirely; a
-    constant T_ij does nothing.
+    constant T_ij does nothing;
+  * the loop of Fig. 2: two steps are one step twice (no hidden state), each
+    step takes its own snapshot's T_ij and wall values.
 """
 import math
 
@@ -206,3 +208,26 @@ def test_subfilter_term_enters_by_its_divergence():
     a = L.step(u0, tau, g, nu=0.01, dt=0.01, forcing=1.0, scheme="rk3")
     b = L.step(u0, None, g, nu=0.01, dt=0.01, forcing=1.0, scheme="rk3")
     assert rel(a, b) < 1e-13
+
+
+def test_loop_takes_each_snapshot_at_its_own_step():
+    """Fig. 2: the loop over snapshots A, B is the loop over A followed by the
+    loop over B (no state beyond the LES field), each step uses its own
+    snapshot's T_ij and wall values (the order matters), and a one-snapshot
+    loop is one step with that snapshot's filter output."""
+    from oracle import oracle as O
+    dns = I.dns_grid(32, 33, 32, 2 * math.pi, math.pi)
+    les = I.les_grid(dns, 8, 9, 8)
+    delta = 2 * math.pi / 16
+    A, B, C = (I.channel_velocity(dns, 1000 + s) for s in range(3))
+    u0, _ = O.subfilter_stress(dns, les, delta, C)
+    nu, dt = 1.0 / 180.0, 0.002
+    ab, taus = L.apost_run(dns, les, delta, [A, B], u0, nu, dt)
+    a, _ = L.apost_run(dns, les, delta, [A], u0, nu, dt)
+    a_b, _ = L.apost_run(dns, les, delta, [B], a, nu, dt)
+    assert rel(ab, a_b) < 1e-15
+    ba, _ = L.apost_run(dns, les, delta, [B, A], u0, nu, dt)
+    assert rel(ba, ab) > 1e-6
+    ubar_a, tau_a = O.subfilter_stress(dns, les, delta, A)
+    assert np.array_equal(taus[0], tau_a)
+    assert rel(a, L.step(u0, tau_a, les, nu, dt, ubc=ubar_a)) < 1e-15
