@@ -545,8 +545,8 @@ int ef_closure_load(ef_closure *closure, const char *path);
  * The loop of Sec. 3 and Fig. 2: at every time step the DNS field is
  * filtered, T_ij (Eq. 6) is formed from it, and the explicitly filtered LES
  * equations (Eq. 6: Eq. 5 with bar(u_i u_j) = ubar_i ubar_j + T_ij) are
- * advanced one step with that T_ij.  The LES here is a minimal collocated solver on
- * the LES nodes of the filter, FP64 throughout:
+ * advanced one step with that T_ij.  The LES here is a minimal collocated
+ * solver on the LES nodes of the filter, FP64 throughout:
  *   - second-order central differences (periodic in x and z, non-uniform in
  *     y), the three-point Laplacian;
  *   - R_i = -d_j (ubar_i ubar_j + T_ij) + nu lap ubar_i + forcing [i = 1] at
@@ -568,9 +568,12 @@ int ef_closure_load(ef_closure *closure, const char *path);
  * Fields are device [3][ny][nz][nx] FP64 with x fastest; tau is the
  * [6][ny][nz][nx] output of ef_subfilter_stress in the precision of its
  * plan (double for EF_PREC_FP64, float otherwise), as is the wall-value
- * field ubar_bc.  The solver owns its scratch (about 13 doubles per node);
- * calls on one solver must not overlap on the GPU.  Calls are asynchronous
- * on `stream` and allocate nothing.
+ * field ubar_bc.  The solver owns its scratch (about 13 doubles per node,
+ * allocated by ef_les_create); calls on one solver must not overlap on the
+ * GPU.  The other calls are asynchronous on `stream` and allocate nothing;
+ * they return EF_ERR_ARG for a NULL pointer, a non-positive dt, an unknown
+ * precision or a current device other than the solver's, and EF_ERR_CUDA if
+ * a launch fails.
  */
 enum { EF_LES_RK3 = 0, EF_LES_EULER = 1 };
 typedef struct {
